@@ -1,0 +1,177 @@
+"""CPU oracle of the Huffman hot path (TEST INFRASTRUCTURE ONLY).
+
+Only ``tests/``, ``__graft_entry__.smoke()`` and ``bench.py``'s CPU-baseline
+and reference legs may import this package.  The CUDA library shares no code
+with it.  The arithmetic lives in plain C (``huff_oracle.c``), compiled with
+gcc into ``libhuff_oracle.so`` beside it; this module only marshals numpy
+arrays.  Each function follows the paper's Huffman Method 1 and Method 2
+(Section III-A); see the C file's header for the readings taken where the
+paper is silent.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "huff_oracle.c")
+_HDR = os.path.join(_HERE, "huff_oracle.h")
+_LIB = os.path.join(_HERE, "libhuff_oracle.so")
+_lib = None
+
+OK = 0
+ERR_INVALID_ARG = -1
+ERR_CODE_TOO_LONG = -2
+ERR_CAPACITY = -3
+ERR_CORRUPT = -4
+
+HEADER_BYTES = 272
+MAX_CODE_LEN = 32
+DEFAULT_CHUNK = 16384
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (-O2, no FP contraction; integer code)."""
+    newest = max(os.path.getmtime(_SRC), os.path.getmtime(_HDR))
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < newest:
+        tmp = f"{_LIB}.tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-O2", "-std=c99", "-fPIC", "-shared",
+                               "-ffp-contract=off", "-o", tmp, _SRC])
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+def _load():
+    global _lib
+    if _lib is None:
+        lib = ctypes.CDLL(build())
+        u8p = ctypes.POINTER(ctypes.c_uint8)
+        u32p = ctypes.POINTER(ctypes.c_uint32)
+        u64p = ctypes.POINTER(ctypes.c_uint64)
+        u64 = ctypes.c_uint64
+        u32 = ctypes.c_uint32
+        lib.oracle_histogram.restype = None
+        lib.oracle_histogram.argtypes = [u8p, u64, u64p]
+        lib.oracle_code_lengths.restype = ctypes.c_int
+        lib.oracle_code_lengths.argtypes = [u64p, u8p]
+        lib.oracle_canonical_codes.restype = None
+        lib.oracle_canonical_codes.argtypes = [u8p, u32p]
+        lib.oracle_max_stream_size.restype = u64
+        lib.oracle_max_stream_size.argtypes = [u64, u32]
+        lib.oracle_chunk_offsets.restype = ctypes.c_int
+        lib.oracle_chunk_offsets.argtypes = [u8p, u64, u32, u8p, u64p, u64p]
+        lib.oracle_pack_bits.restype = ctypes.c_int
+        lib.oracle_pack_bits.argtypes = [u8p, u64, u8p, u32p, u64, u64p]
+        lib.oracle_encode.restype = ctypes.c_int
+        lib.oracle_encode.argtypes = [u8p, u64, u32, u8p, u8p, u64, u64p]
+        lib.oracle_compress.restype = ctypes.c_int
+        lib.oracle_compress.argtypes = [u8p, u64, u32, u8p, u64, u64p]
+        lib.oracle_decode.restype = ctypes.c_int
+        lib.oracle_decode.argtypes = [u8p, u64, u8p, u64, u64p]
+        _lib = lib
+    return _lib
+
+
+def _p(a: np.ndarray, ct):
+    return a.ctypes.data_as(ctypes.POINTER(ct))
+
+
+def _bytes(x) -> np.ndarray:
+    a = np.ascontiguousarray(np.asarray(x, dtype=np.uint8)).reshape(-1)
+    return a if a.size else np.zeros(1, dtype=np.uint8)[:0]
+
+
+def histogram(x) -> np.ndarray:
+    """Byte counts, u64[256] (Method 1's probability-of-occurrence step)."""
+    a = _bytes(x)
+    h = np.zeros(256, dtype=np.uint64)
+    _load().oracle_histogram(_p(a, ctypes.c_uint8), a.size, _p(h, ctypes.c_uint64))
+    return h
+
+
+def code_lengths(hist):
+    """(status, len u8[256]) from the (weight, id)-ordered merge tree."""
+    h = np.ascontiguousarray(np.asarray(hist, dtype=np.uint64))
+    assert h.size == 256
+    ln = np.zeros(256, dtype=np.uint8)
+    st = _load().oracle_code_lengths(_p(h, ctypes.c_uint64), _p(ln, ctypes.c_uint8))
+    return st, ln
+
+
+def canonical_codes(lengths) -> np.ndarray:
+    ln = np.ascontiguousarray(np.asarray(lengths, dtype=np.uint8))
+    code = np.zeros(256, dtype=np.uint32)
+    _load().oracle_canonical_codes(_p(ln, ctypes.c_uint8), _p(code, ctypes.c_uint32))
+    return code
+
+
+def max_stream_size(n: int, cs: int = DEFAULT_CHUNK) -> int:
+    return int(_load().oracle_max_stream_size(n, cs))
+
+
+def chunk_offsets(x, lengths, cs: int = DEFAULT_CHUNK):
+    """(status, off u64[C], total_bits) of the concatenated codes."""
+    a = _bytes(x)
+    ln = np.ascontiguousarray(np.asarray(lengths, dtype=np.uint8))
+    chunks = (a.size + cs - 1) // cs if cs else 0
+    off = np.zeros(max(chunks, 1), dtype=np.uint64)
+    tb = ctypes.c_uint64(0)
+    st = _load().oracle_chunk_offsets(_p(a, ctypes.c_uint8), a.size, cs, _p(ln, ctypes.c_uint8),
+                                      _p(off, ctypes.c_uint64), ctypes.byref(tb))
+    return st, off[:chunks], int(tb.value)
+
+
+def pack_bits(x, lengths):
+    """(status, u32 words, bits): the codes of x concatenated MSB first from bit 0."""
+    a = _bytes(x)
+    ln = np.ascontiguousarray(np.asarray(lengths, dtype=np.uint8))
+    nwords = (a.size * MAX_CODE_LEN + 31) // 32
+    words = np.zeros(max(nwords, 1), dtype=np.uint32)
+    bits = ctypes.c_uint64(0)
+    st = _load().oracle_pack_bits(_p(a, ctypes.c_uint8), a.size, _p(ln, ctypes.c_uint8),
+                                  _p(words, ctypes.c_uint32), words.size, ctypes.byref(bits))
+    nb = int(bits.value)
+    return st, words[:(nb + 31) // 32], nb
+
+
+def encode(x, lengths, cs: int = DEFAULT_CHUNK, cap: int | None = None):
+    """(status, stream bytes, needed bytes) for a given codebook (lengths)."""
+    a = _bytes(x)
+    ln = np.ascontiguousarray(np.asarray(lengths, dtype=np.uint8))
+    if cap is None:
+        cap = max_stream_size(a.size, cs) if cs else HEADER_BYTES
+    out = np.zeros(max(cap, 1), dtype=np.uint8)
+    ob = ctypes.c_uint64(0)
+    st = _load().oracle_encode(_p(a, ctypes.c_uint8), a.size, cs, _p(ln, ctypes.c_uint8),
+                               _p(out, ctypes.c_uint8), cap, ctypes.byref(ob))
+    need = int(ob.value)
+    return st, (out[:need] if st == OK else out[:0]), need
+
+
+def compress(x, cs: int = DEFAULT_CHUNK, cap: int | None = None):
+    """(status, stream bytes): histogram + lengths + canonical codes + encode."""
+    a = _bytes(x)
+    if cap is None:
+        cap = max_stream_size(a.size, cs) if cs else HEADER_BYTES
+    out = np.zeros(max(cap, 1), dtype=np.uint8)
+    ob = ctypes.c_uint64(0)
+    st = _load().oracle_compress(_p(a, ctypes.c_uint8), a.size, cs, _p(out, ctypes.c_uint8),
+                                 cap, ctypes.byref(ob))
+    return st, (out[:int(ob.value)] if st == OK else out[:0])
+
+
+def decode(stream, cap: int | None = None):
+    """(status, decoded bytes, n from the header)."""
+    s = _bytes(stream)
+    if cap is None:
+        cap = int.from_bytes(bytes(s[256:264]), "little") if s.size >= 264 else 0
+        cap = min(cap, 1 << 34)
+    out = np.zeros(max(cap, 1), dtype=np.uint8)
+    n = ctypes.c_uint64(0)
+    st = _load().oracle_decode(_p(s, ctypes.c_uint8), s.size, _p(out, ctypes.c_uint8), cap,
+                               ctypes.byref(n))
+    nn = int(n.value)
+    return st, (out[:nn] if st == OK else out[:0]), nn

@@ -1,0 +1,434 @@
+/*
+ * huff_oracle.c -- plain, slow CPU oracle of the Huffman hot path.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only the tests, the smoke check and the
+ * benchmark's CPU-baseline / reference arm may load this file.  It shares no
+ * code, header, table or constant generator with the CUDA library, and the
+ * library never calls it.
+ *
+ * What it computes (paper: "Parallel Data Compression Techniques",
+ * Section III-A, Huffman Method 1 and Method 2):
+ *   1. Method 1 counts how often each byte occurs (its "probability of
+ *      occurrence").                                        oracle_histogram
+ *   2. Method 1 builds an extended weighted binary tree: the two lightest
+ *      nodes are replaced by one internal node whose weight is the sum of
+ *      theirs, repeated until one root is left.  A leaf's depth is the length
+ *      of its code.                                      oracle_code_lengths
+ *   3. Codes are assigned canonically from the lengths.
+ *                                                     oracle_canonical_codes
+ *   4. Encoding concatenates the codes of the input bytes.  Method 2's
+ *      segments with ids become fixed-size chunks of `cs` symbols whose
+ *      starting bit offsets are recorded, so each chunk can be decoded on
+ *      its own and the output reassembled in chunk order.     oracle_encode
+ *   5. Decoding ("lossless") reverses 4 chunk by chunk.       oracle_decode
+ *
+ * Readings of points the paper leaves open:
+ *   R1 tie-break: nodes are ordered by (weight, id); leaf id = byte value,
+ *      internal ids are 256, 257, ... in creation order.
+ *   R2 "replacing two external nodes" is read as the standard step: any two
+ *      lowest-(weight, id) nodes, leaves or internal.
+ *   R3 empty input: all lengths 0.  Exactly one distinct byte: length 1,
+ *      code "0".
+ *   R4 a code longer than 32 bits is an error (no length limiting).
+ *   R5 canonical order: symbols sorted by (length, byte value); the code
+ *      starts at 0 and is shifted left by the length increase before each
+ *      assignment, then incremented.
+ *   R6 stream: [0,256) lengths u8; [256,264) n u64 LE; [264,268) chunk
+ *      symbols u32 LE; [268,272) longest length u32 LE; then ceil(n/cs) u64
+ *      LE bit offsets; then the payload as u32 LE words, stream bit j being
+ *      bit (31 - j%32) of word j/32 (MSB first), zero padded.
+ *   R7 decode validation: see oracle_decode.
+ *
+ * Parity: pinned (worked examples, Kraft equality, brute-force optimality,
+ * Shannon bounds, Fibonacci length boundary, independent offset sums, round
+ * trip; see tests/test_oracle_*.py).
+ */
+#include "huff_oracle.h"
+
+#include <stdlib.h>
+#include <string.h>
+
+/* ---- little-endian field access (independent of the host's byte order) */
+static void put_u32le(uint8_t *p, uint32_t v)
+{
+    for (int k = 0; k < 4; ++k)
+        p[k] = (uint8_t)(v >> (8 * k));
+}
+static void put_u64le(uint8_t *p, uint64_t v)
+{
+    for (int k = 0; k < 8; ++k)
+        p[k] = (uint8_t)(v >> (8 * k));
+}
+static uint32_t get_u32le(const uint8_t *p)
+{
+    uint32_t v = 0;
+    for (int k = 0; k < 4; ++k)
+        v |= (uint32_t)p[k] << (8 * k);
+    return v;
+}
+static uint64_t get_u64le(const uint8_t *p)
+{
+    uint64_t v = 0;
+    for (int k = 0; k < 8; ++k)
+        v |= (uint64_t)p[k] << (8 * k);
+    return v;
+}
+
+static int chunk_symbols_ok(uint32_t cs)
+{
+    return cs >= ORACLE_MIN_CHUNK && cs <= ORACLE_MAX_CHUNK && cs % 16 == 0;
+}
+
+/* ---- step 1: byte counts ------------------------------------------------ */
+void oracle_histogram(const uint8_t *x, uint64_t n, uint64_t hist[256])
+{
+    memset(hist, 0, 256 * sizeof(uint64_t));
+    for (uint64_t i = 0; i < n; ++i)
+        hist[x[i]] += 1;
+}
+
+/* ---- step 2: the weighted tree, with a binary min-heap on (weight, id) --- */
+typedef struct {
+    uint64_t w;
+    uint32_t id;
+} node_t;
+
+static int node_before(node_t a, node_t b)
+{
+    return a.w < b.w || (a.w == b.w && a.id < b.id);
+}
+
+static void heap_push(node_t *h, int *size, node_t v)
+{
+    int i = (*size)++;
+    h[i] = v;
+    while (i > 0) {
+        int up = (i - 1) / 2;
+        if (!node_before(h[i], h[up]))
+            break;
+        node_t t = h[i];
+        h[i] = h[up];
+        h[up] = t;
+        i = up;
+    }
+}
+
+static node_t heap_pop(node_t *h, int *size)
+{
+    node_t top = h[0];
+    h[0] = h[--(*size)];
+    int i = 0;
+    for (;;) {
+        int l = 2 * i + 1, r = l + 1, m = i;
+        if (l < *size && node_before(h[l], h[m]))
+            m = l;
+        if (r < *size && node_before(h[r], h[m]))
+            m = r;
+        if (m == i)
+            break;
+        node_t t = h[i];
+        h[i] = h[m];
+        h[m] = t;
+        i = m;
+    }
+    return top;
+}
+
+int oracle_code_lengths(const uint64_t hist[256], uint8_t len[256])
+{
+    node_t heap[512];
+    int size = 0, parent[511], leaves = 0, last_leaf = -1;
+
+    memset(len, 0, 256);
+    for (int s = 0; s < 256; ++s) {
+        parent[s] = -1;
+        if (hist[s] > 0) {
+            node_t leaf = {hist[s], (uint32_t)s};
+            heap_push(heap, &size, leaf);
+            ++leaves;
+            last_leaf = s;
+        }
+    }
+    if (leaves == 0)
+        return ORACLE_OK; /* R3: empty input */
+    if (leaves == 1) {
+        len[last_leaf] = 1; /* R3: one distinct byte */
+        return ORACLE_OK;
+    }
+    /* R1/R2: replace the two lightest nodes by their sum, until one is left */
+    uint32_t next_id = 256;
+    while (size > 1) {
+        node_t a = heap_pop(heap, &size);
+        node_t b = heap_pop(heap, &size);
+        node_t inner = {a.w + b.w, next_id++};
+        parent[a.id] = (int)inner.id;
+        parent[b.id] = (int)inner.id;
+        parent[inner.id] = -1;
+        heap_push(heap, &size, inner);
+    }
+    /* code length = depth of the leaf = number of edges up to the root */
+    int too_long = 0;
+    for (int s = 0; s < 256; ++s) {
+        if (hist[s] == 0)
+            continue;
+        int depth = 0;
+        for (int v = s; parent[v] != -1; v = parent[v])
+            ++depth;
+        if (depth > ORACLE_MAX_CODE_LEN)
+            too_long = 1;
+        len[s] = (uint8_t)(depth > 255 ? 255 : depth);
+    }
+    if (too_long) {
+        memset(len, 0, 256);
+        return ORACLE_ERR_CODE_TOO_LONG; /* R4 */
+    }
+    return ORACLE_OK;
+}
+
+/* ---- step 3: canonical codes (R5) ---------------------------------------- */
+void oracle_canonical_codes(const uint8_t len[256], uint32_t code[256])
+{
+    uint64_t next = 0;
+    int prev = -1;
+    memset(code, 0, 256 * sizeof(uint32_t));
+    for (int L = 1; L <= ORACLE_MAX_CODE_LEN; ++L) {
+        for (int s = 0; s < 256; ++s) {
+            if (len[s] != L)
+                continue;
+            if (prev < 0)
+                next = 0;
+            else
+                next <<= (L - prev);
+            prev = L;
+            code[s] = (uint32_t)next;
+            next += 1;
+        }
+    }
+}
+
+uint64_t oracle_max_stream_size(uint64_t n, uint32_t cs)
+{
+    uint64_t chunks = cs ? (n + cs - 1) / cs : 0;
+    return ORACLE_HEADER_BYTES + 8 * chunks + 4 * ((n + 3) / 4) + 4;
+}
+
+/* ---- step 4: encode ------------------------------------------------------ */
+int oracle_chunk_offsets(const uint8_t *x, uint64_t n, uint32_t cs,
+                         const uint8_t len[256], uint64_t *off, uint64_t *total_bits)
+{
+    uint64_t pos = 0;
+    if (!chunk_symbols_ok(cs))
+        return ORACLE_ERR_INVALID_ARG;
+    for (uint64_t i = 0; i < n; ++i) {
+        if (i % cs == 0)
+            off[i / cs] = pos;
+        if (len[x[i]] == 0)
+            return ORACLE_ERR_INVALID_ARG; /* byte missing from the codebook */
+        pos += len[x[i]];
+    }
+    *total_bits = pos;
+    return ORACLE_OK;
+}
+
+int oracle_pack_bits(const uint8_t *x, uint64_t m, const uint8_t len[256],
+                     uint32_t *words, uint64_t nwords, uint64_t *bits)
+{
+    uint32_t code[256];
+    uint64_t pos = 0;
+    oracle_canonical_codes(len, code);
+    memset(words, 0, nwords * sizeof(uint32_t));
+    for (uint64_t i = 0; i < m; ++i) {
+        int L = len[x[i]];
+        if (L == 0)
+            return ORACLE_ERR_INVALID_ARG;
+        for (int b = L - 1; b >= 0; --b) { /* most significant bit first */
+            if ((pos >> 5) >= nwords)
+                return ORACLE_ERR_CAPACITY;
+            if ((code[x[i]] >> b) & 1u)
+                words[pos >> 5] |= 1u << (31 - (pos & 31));
+            ++pos;
+        }
+    }
+    *bits = pos;
+    return ORACLE_OK;
+}
+
+int oracle_encode(const uint8_t *x, uint64_t n, uint32_t cs, const uint8_t len[256],
+                  uint8_t *out, uint64_t cap, uint64_t *out_bytes)
+{
+    uint64_t chunks, total_bits = 0, nwords, need, bits;
+    uint32_t max_len = 0;
+    int st;
+
+    *out_bytes = 0;
+    if (!chunk_symbols_ok(cs))
+        return ORACLE_ERR_INVALID_ARG;
+    chunks = (n + cs - 1) / cs;
+    uint64_t *off = (uint64_t *)malloc(sizeof(uint64_t) * (chunks ? chunks : 1));
+    if (!off)
+        return ORACLE_ERR_INVALID_ARG;
+    st = oracle_chunk_offsets(x, n, cs, len, off, &total_bits);
+    if (st != ORACLE_OK) {
+        free(off);
+        return st;
+    }
+    nwords = (total_bits + 31) / 32;
+    need = ORACLE_HEADER_BYTES + 8 * chunks + 4 * nwords;
+    *out_bytes = need;
+    if (need > cap) {
+        free(off);
+        return ORACLE_ERR_CAPACITY;
+    }
+    for (int s = 0; s < 256; ++s)
+        if (len[s] > max_len)
+            max_len = len[s];
+    memcpy(out, len, 256);
+    put_u64le(out + 256, n);
+    put_u32le(out + 264, cs);
+    put_u32le(out + 268, max_len);
+    for (uint64_t c = 0; c < chunks; ++c)
+        put_u64le(out + ORACLE_HEADER_BYTES + 8 * c, off[c]);
+    free(off);
+
+    uint32_t *words = (uint32_t *)malloc(sizeof(uint32_t) * (nwords ? nwords : 1));
+    if (!words)
+        return ORACLE_ERR_INVALID_ARG;
+    st = oracle_pack_bits(x, n, len, words, nwords, &bits);
+    if (st == ORACLE_OK) {
+        uint8_t *pay = out + ORACLE_HEADER_BYTES + 8 * chunks;
+        for (uint64_t j = 0; j < nwords; ++j)
+            put_u32le(pay + 4 * j, words[j]);
+    }
+    free(words);
+    return st;
+}
+
+int oracle_compress(const uint8_t *x, uint64_t n, uint32_t cs, uint8_t *out, uint64_t cap,
+                    uint64_t *out_bytes)
+{
+    uint64_t hist[256];
+    uint8_t len[256];
+    int st;
+    *out_bytes = 0;
+    oracle_histogram(x, n, hist);
+    st = oracle_code_lengths(hist, len);
+    if (st != ORACLE_OK)
+        return st;
+    return oracle_encode(x, n, cs, len, out, cap, out_bytes);
+}
+
+/* ---- step 5: decode -------------------------------------------------------
+ * Validation (R7), in this order; every failure is "corrupt" except (c):
+ *  (a) at least 272 bytes; chunk symbols a multiple of 16 in range; the
+ *      offset table fits; every length <= 32 and the largest equals the
+ *      header's field; n > 0 needs at least one code; one code must have
+ *      length 1; two or more codes must fill the code space exactly
+ *      (sum of 2^-len == 1).
+ *  (b) *n_out = n.
+ *  (c) n larger than the output capacity -> capacity error.
+ *  (d) off[0] == 0, offsets non-decreasing and <= payload bits P, where P is
+ *      32 * (whole u32 words after the offset table).
+ *  (e) chunk c reads only bits below off[c+1] (below P for the last chunk),
+ *      every code is found within the longest length, and a chunk that is
+ *      not the last one ends exactly at off[c+1].
+ */
+int oracle_decode(const uint8_t *s, uint64_t bytes, uint8_t *out, uint64_t cap, uint64_t *n_out)
+{
+    uint8_t len[256];
+    uint32_t code[256];
+    uint64_t n, chunks;
+    uint32_t cs, max_field, max_len = 0, nsym = 0;
+
+    *n_out = 0;
+    if (bytes < ORACLE_HEADER_BYTES)
+        return ORACLE_ERR_CORRUPT;
+    memcpy(len, s, 256);
+    n = get_u64le(s + 256);
+    cs = get_u32le(s + 264);
+    max_field = get_u32le(s + 268);
+    if (!chunk_symbols_ok(cs))
+        return ORACLE_ERR_CORRUPT;
+    chunks = n / cs + (n % cs != 0);
+    if (chunks > (bytes - ORACLE_HEADER_BYTES) / 8)
+        return ORACLE_ERR_CORRUPT;
+    for (int k = 0; k < 256; ++k) {
+        if (len[k] > ORACLE_MAX_CODE_LEN)
+            return ORACLE_ERR_CORRUPT;
+        if (len[k] > max_len)
+            max_len = len[k];
+        nsym += len[k] > 0;
+    }
+    if (max_len != max_field)
+        return ORACLE_ERR_CORRUPT;
+    if (n > 0 && nsym == 0)
+        return ORACLE_ERR_CORRUPT;
+    if (nsym == 1 && max_len != 1)
+        return ORACLE_ERR_CORRUPT;
+    if (nsym >= 2) {
+        uint64_t kraft = 0; /* sum of 2^(32 - len): 2^32 means sum 2^-len = 1 */
+        for (int k = 0; k < 256; ++k)
+            if (len[k])
+                kraft += (uint64_t)1 << (32 - len[k]);
+        if (kraft != ((uint64_t)1 << 32))
+            return ORACLE_ERR_CORRUPT;
+    }
+    *n_out = n;
+    if (n > cap)
+        return ORACLE_ERR_CAPACITY;
+
+    const uint8_t *offp = s + ORACLE_HEADER_BYTES;
+    const uint8_t *pay = offp + 8 * chunks;
+    uint64_t pbits = 32 * ((bytes - ORACLE_HEADER_BYTES - 8 * chunks) / 4);
+    for (uint64_t c = 0; c < chunks; ++c) {
+        uint64_t o = get_u64le(offp + 8 * c);
+        if (c == 0 && o != 0)
+            return ORACLE_ERR_CORRUPT;
+        if (c > 0 && o < get_u64le(offp + 8 * (c - 1)))
+            return ORACLE_ERR_CORRUPT;
+        if (o > pbits)
+            return ORACLE_ERR_CORRUPT;
+    }
+
+    /* canonical codes of each length are consecutive integers: decode by
+     * the first code and the symbols of each length in byte order */
+    uint32_t first[ORACLE_MAX_CODE_LEN + 1], count[ORACLE_MAX_CODE_LEN + 1];
+    uint8_t syms[ORACLE_MAX_CODE_LEN + 1][256];
+    oracle_canonical_codes(len, code);
+    memset(count, 0, sizeof(count));
+    memset(first, 0, sizeof(first));
+    for (int L = 1; L <= ORACLE_MAX_CODE_LEN; ++L)
+        for (int k = 0; k < 256; ++k)
+            if (len[k] == L) {
+                if (count[L] == 0)
+                    first[L] = code[k];
+                syms[L][count[L]++] = (uint8_t)k;
+            }
+
+    for (uint64_t c = 0; c < chunks; ++c) {
+        uint64_t pos = get_u64le(offp + 8 * c);
+        uint64_t limit = c + 1 < chunks ? get_u64le(offp + 8 * (c + 1)) : pbits;
+        uint64_t base = c * cs;
+        uint64_t m = n - base < cs ? n - base : cs;
+        for (uint64_t i = 0; i < m; ++i) {
+            uint32_t v = 0;
+            int L = 0, found = 0;
+            while (!found) {
+                if (pos >= limit)
+                    return ORACLE_ERR_CORRUPT;
+                uint32_t word = get_u32le(pay + 4 * (pos >> 5));
+                v = (v << 1) | ((word >> (31 - (pos & 31))) & 1u);
+                ++pos;
+                ++L;
+                if (count[L] && v >= first[L] && v - first[L] < count[L]) {
+                    out[base + i] = syms[L][v - first[L]];
+                    found = 1;
+                } else if ((uint32_t)L >= max_len) {
+                    return ORACLE_ERR_CORRUPT;
+                }
+            }
+        }
+        if (c + 1 < chunks && pos != limit)
+            return ORACLE_ERR_CORRUPT;
+    }
+    return ORACLE_OK;
+}

@@ -1,0 +1,35 @@
+/*
+ * huff_oracle.h -- plain CPU oracle of the Huffman hot path.
+ * TEST INFRASTRUCTURE ONLY: tests, the smoke check and the benchmark's CPU
+ * baseline use it; the CUDA library neither includes nor links it.
+ */
+#ifndef HUFF_ORACLE_H
+#define HUFF_ORACLE_H
+#include <stdint.h>
+
+#define ORACLE_OK 0
+#define ORACLE_ERR_INVALID_ARG (-1)
+#define ORACLE_ERR_CODE_TOO_LONG (-2)
+#define ORACLE_ERR_CAPACITY (-3)
+#define ORACLE_ERR_CORRUPT (-4)
+
+#define ORACLE_HEADER_BYTES 272
+#define ORACLE_MAX_CODE_LEN 32
+#define ORACLE_MIN_CHUNK 16
+#define ORACLE_MAX_CHUNK (1u << 24)
+
+void oracle_histogram(const uint8_t *x, uint64_t n, uint64_t hist[256]);
+int oracle_code_lengths(const uint64_t hist[256], uint8_t len[256]);
+void oracle_canonical_codes(const uint8_t len[256], uint32_t code[256]);
+uint64_t oracle_max_stream_size(uint64_t n, uint32_t cs);
+int oracle_chunk_offsets(const uint8_t *x, uint64_t n, uint32_t cs, const uint8_t len[256],
+                         uint64_t *off, uint64_t *total_bits);
+int oracle_pack_bits(const uint8_t *x, uint64_t m, const uint8_t len[256], uint32_t *words,
+                     uint64_t nwords, uint64_t *bits);
+int oracle_encode(const uint8_t *x, uint64_t n, uint32_t cs, const uint8_t len[256],
+                  uint8_t *out, uint64_t cap, uint64_t *out_bytes);
+int oracle_compress(const uint8_t *x, uint64_t n, uint32_t cs, uint8_t *out, uint64_t cap,
+                    uint64_t *out_bytes);
+int oracle_decode(const uint8_t *s, uint64_t bytes, uint8_t *out, uint64_t cap,
+                  uint64_t *n_out);
+#endif

@@ -1,0 +1,205 @@
+/*
+ * Seeded synthetic inputs shared by the CPU oracle tests, the GPU parity
+ * tests and the benchmark.  This file holds no Huffman arithmetic: it only
+ * draws bytes, sizes and arrival times.
+ *
+ * Every stream comes from splitmix64 (Steele, Lea and Flood, "Fast
+ * splittable pseudorandom number generators", OOPSLA 2014), so the inputs are
+ * reproducible from a seed without depending on any library's RNG.
+ *
+ * The paper's Huffman corpus (a ~45 MB concatenation of English books,
+ * Section III-A) is not available, so gen_text() produces text of the same
+ * scale and a text-like symbol distribution: words from a random vocabulary
+ * with Zipf frequencies, spaces, punctuation and line breaks.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+static inline uint64_t sm64(uint64_t *state)
+{
+    uint64_t z = (*state += 0x9E3779B97F4A7C15ull);
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+/* uniform double in [0, 1) with 53 random bits */
+static inline double u01(uint64_t *state)
+{
+    return (double)(sm64(state) >> 11) * (1.0 / 9007199254740992.0);
+}
+
+/* uniform integer in [0, m) by multiply-shift of the top 32 bits */
+static inline uint32_t below(uint64_t *state, uint32_t m)
+{
+    return (uint32_t)(((sm64(state) >> 32) * (uint64_t)m) >> 32);
+}
+
+/* Cumulative Zipf(s) table over ranks 1..v, normalised to end at 1. */
+static double *zipf_cdf(uint32_t v, double s)
+{
+    double *cdf = (double *)malloc(sizeof(double) * v);
+    if (!cdf)
+        return NULL;
+    double acc = 0.0;
+    for (uint32_t k = 0; k < v; ++k) {
+        acc += pow((double)(k + 1), -s);
+        cdf[k] = acc;
+    }
+    for (uint32_t k = 0; k < v; ++k)
+        cdf[k] /= acc;
+    cdf[v - 1] = 1.0;
+    return cdf;
+}
+
+/* smallest rank index k with u < cdf[k] */
+static inline uint32_t zipf_draw(const double *cdf, uint32_t v, double u)
+{
+    uint32_t lo = 0, hi = v - 1;
+    while (lo < hi) {
+        uint32_t mid = (lo + hi) >> 1;
+        if (u < cdf[mid])
+            hi = mid;
+        else
+            lo = mid + 1;
+    }
+    return lo;
+}
+
+uint64_t synth_splitmix64(uint64_t state) { return sm64(&state); }
+
+/* Bytes i.i.d. Zipf(s) over 96 consecutive codes starting at the space
+ * (rank k = 1..96 -> byte 31 + k). */
+int synth_zipf_ascii(uint8_t *out, uint64_t n, uint64_t seed, double s)
+{
+    double *cdf = zipf_cdf(96, s);
+    if (!cdf)
+        return -1;
+    uint64_t st = seed;
+    for (uint64_t i = 0; i < n; ++i)
+        out[i] = (uint8_t)(32 + zipf_draw(cdf, 96, u01(&st)));
+    free(cdf);
+    return 0;
+}
+
+/* Text: a vocabulary of `vocab` random lowercase words (length geometric
+ * with p = 0.3 on {1, 2, ...}, capped at 12), word choice Zipf(1.0) by
+ * vocabulary index, 5% of words followed by one of ".,;:!?", then a newline
+ * when the line has reached 80 characters and a space otherwise.  The stream
+ * is cut at exactly n bytes. */
+int synth_text(uint8_t *out, uint64_t n, uint64_t seed)
+{
+    enum { VOCAB = 50000, MAXW = 12 };
+    static const char punct[6] = {'.', ',', ';', ':', '!', '?'};
+    uint64_t st = seed;
+    uint8_t *words = (uint8_t *)malloc((size_t)VOCAB * MAXW);
+    uint8_t *wlen = (uint8_t *)malloc(VOCAB);
+    double *cdf = zipf_cdf(VOCAB, 1.0);
+    if (!words || !wlen || !cdf) {
+        free(words);
+        free(wlen);
+        free(cdf);
+        return -1;
+    }
+    for (uint32_t w = 0; w < VOCAB; ++w) {
+        uint32_t len = 1;
+        while (len < MAXW && !(u01(&st) < 0.3))
+            ++len;
+        wlen[w] = (uint8_t)len;
+        for (uint32_t j = 0; j < len; ++j)
+            words[(size_t)w * MAXW + j] = (uint8_t)('a' + below(&st, 26));
+    }
+    uint64_t pos = 0;
+    uint32_t line = 0;
+    while (pos < n) {
+        uint32_t w = zipf_draw(cdf, VOCAB, u01(&st));
+        for (uint32_t j = 0; j < wlen[w] && pos < n; ++j)
+            out[pos++] = words[(size_t)w * MAXW + j];
+        line += wlen[w];
+        if (u01(&st) < 0.05) {
+            uint8_t p = (uint8_t)punct[below(&st, 6)];
+            if (pos < n)
+                out[pos++] = p;
+            line += 1;
+        }
+        if (pos < n) {
+            if (line >= 80) {
+                out[pos++] = '\n';
+                line = 0;
+            } else {
+                out[pos++] = ' ';
+                line += 1;
+            }
+        }
+    }
+    free(words);
+    free(wlen);
+    free(cdf);
+    return 0;
+}
+
+/* Uniform bytes: the low byte of each draw. */
+void synth_uniform(uint8_t *out, uint64_t n, uint64_t seed)
+{
+    uint64_t st = seed;
+    for (uint64_t i = 0; i < n; ++i)
+        out[i] = (uint8_t)sm64(&st);
+}
+
+/* Geometric bytes: the number of trailing zero bits of a draw, capped at
+ * 255, so P(k) = 2^-(k+1). */
+void synth_geometric(uint8_t *out, uint64_t n, uint64_t seed)
+{
+    uint64_t st = seed;
+    for (uint64_t i = 0; i < n; ++i) {
+        uint64_t d = sm64(&st);
+        unsigned k = d ? (unsigned)__builtin_ctzll(d) : 64u;
+        out[i] = (uint8_t)(k > 255 ? 255 : k);
+    }
+}
+
+/* Geometric symbol with success probability p over {0..255}: used for small
+ * skewed alphabets in tests. */
+void synth_geometric_p(uint8_t *out, uint64_t n, uint64_t seed, double p)
+{
+    uint64_t st = seed;
+    for (uint64_t i = 0; i < n; ++i) {
+        unsigned k = 0;
+        while (k < 255 && !(u01(&st) < p))
+            ++k;
+        out[i] = (uint8_t)k;
+    }
+}
+
+/* Log-uniform sizes in [lo, hi]: floor(exp(U(ln lo, ln hi))). */
+void synth_log_uniform_sizes(uint64_t *sizes, uint32_t count, uint64_t seed,
+                             uint64_t lo, uint64_t hi)
+{
+    uint64_t st = seed;
+    double a = log((double)lo), b = log((double)hi);
+    for (uint32_t i = 0; i < count; ++i) {
+        uint64_t v = (uint64_t)floor(exp(a + (b - a) * u01(&st)));
+        sizes[i] = v < lo ? lo : (v > hi ? hi : v);
+    }
+}
+
+/* Open-loop Poisson arrival trace: exponential gaps with rate `lambda` per
+ * second, an operation bit (0 = compress, 1 = decompress) with probability
+ * 1/2 each, and log-uniform sizes in [lo, hi]. */
+void synth_poisson_trace(double *t_arrive, uint8_t *op, uint64_t *sizes,
+                         uint32_t count, uint64_t seed, double lambda,
+                         uint64_t lo, uint64_t hi)
+{
+    uint64_t st = seed;
+    double t = 0.0, a = log((double)lo), b = log((double)hi);
+    for (uint32_t i = 0; i < count; ++i) {
+        double u = u01(&st);
+        t += -log(1.0 - u) / lambda;
+        t_arrive[i] = t;
+        op[i] = (uint8_t)(sm64(&st) >> 63);
+        uint64_t v = (uint64_t)floor(exp(a + (b - a) * u01(&st)));
+        sizes[i] = v < lo ? lo : (v > hi ? hi : v);
+    }
+}
