@@ -1,0 +1,163 @@
+/*
+ * huff.h -- C ABI of the GB300 Huffman library (libhuff.so).
+ *
+ * The library runs the data-parallel hot path of the Huffman scheme of
+ * "Parallel Data Compression Techniques" (Noel, Graham, Liu), Section III-A:
+ *
+ *   Method 1: count how often each byte occurs, build the weighted binary
+ *   tree by repeatedly replacing the two lightest nodes with one internal
+ *   node whose weight is their sum, and code each byte by its leaf's path.
+ *   Method 2: cut the data into segments with ids, code them independently
+ *   and reassemble them by id.
+ *
+ * Here the segments are fixed chunks of `chunk_symbols` bytes whose starting
+ * bit offsets are stored in the stream, so every chunk decodes on its own.
+ *
+ * Conventions shared by every call:
+ *  - Pointers named d_* are DEVICE pointers, owned by the caller.  The plain
+ *    calls never allocate; scratch comes from the caller (d_ws).
+ *  - d_in, d_out and d_stream must be 16-byte aligned (cudaMalloc and torch
+ *    allocations are); otherwise HUFF_ERR_INVALID_ARG is returned.
+ *  - Calls are asynchronous on `stream` (0 = the legacy default stream).
+ *    The RETURN VALUE reports argument and launch errors only.
+ *  - Errors found on the device (code too long, corrupt stream, capacity,
+ *    wait timeout) are written to *d_status with "first error wins".  The
+ *    caller sets *d_status = 0 before the first call of a chain (for example
+ *    build_codebook -> encode); every kernel reads it first and does nothing
+ *    if it is already non-zero, so a failed step stops the rest of the chain.
+ *    huff_compress clears *d_status itself.  Read it after synchronising.
+ *
+ * Stream layout (all integers little-endian):
+ *   [0, 256)            code length of each byte value, u8 (0 = absent)
+ *   [256, 264)          n, the number of symbols, u64
+ *   [264, 268)          chunk_symbols, u32
+ *   [268, 272)          longest code length, u32
+ *   [272, 272 + 8C)     bit offset of each chunk in the payload, u64,
+ *                       C = ceil(n / chunk_symbols)
+ *   then                payload as u32 words; payload bit j is bit
+ *                       (31 - j % 32) of word j / 32 (most significant bit
+ *                       first), the last word zero padded.
+ *
+ * Codes: lengths from the merge tree with ties broken by (weight, id), leaf
+ * id = byte value and merged nodes numbered 256, 257, ... in creation order;
+ * canonical codes in (length, byte value) order.  One distinct byte gets the
+ * 1-bit code "0".  A code longer than 32 bits is an error, not limited.
+ */
+#ifndef HUFF_H
+#define HUFF_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int32_t huff_status_t;
+
+#define HUFF_OK 0
+#define HUFF_ERR_INVALID_ARG (-1)    /* bad argument (host) / symbol or size (device) */
+#define HUFF_ERR_CODE_TOO_LONG (-2)  /* a code would need more than 32 bits           */
+#define HUFF_ERR_CAPACITY (-3)       /* output buffer too small                       */
+#define HUFF_ERR_CORRUPT_STREAM (-4) /* stream fails validation                       */
+#define HUFF_ERR_CUDA (-5)           /* a CUDA call or launch failed                  */
+#define HUFF_ERR_TIMEOUT (-6)        /* a bounded device wait gave up                 */
+#define HUFF_ERR_BUDGET (-7)         /* request can never fit the memory budget       */
+#define HUFF_ERR_UNSUPPORTED (-8)    /* no usable device / unsupported configuration  */
+
+#define HUFF_HEADER_BYTES 272u
+#define HUFF_DEFAULT_CHUNK_SYMBOLS 16384u
+#define HUFF_MIN_CHUNK_SYMBOLS 16u
+#define HUFF_MAX_CHUNK_SYMBOLS (1u << 24)
+#define HUFF_MAX_CODE_LEN 32u
+
+/* The CUDA stream type, declared without including cuda_runtime.h. */
+typedef struct CUstream_st *huff_stream_t;
+
+/* Codebook, plain data, 1288 bytes; lives in device memory for the calls. */
+typedef struct huff_codebook {
+    uint8_t len[256];   /* code length of each byte value, 0 = absent      */
+    uint32_t code[256]; /* canonical code, right-aligned in the low bits   */
+    uint32_t nsym;      /* number of byte values with a code               */
+    uint32_t max_len;   /* longest code length                             */
+} huff_codebook_t;
+
+/* Text of a status code; never NULL. */
+const char *huff_status_str(huff_status_t status);
+
+/* Library version, major * 10000 + minor * 100 + patch. */
+int huff_version(void);
+
+/* Upper bound on the stream size of n input bytes coded with a codebook from
+ * huff_build_codebook: header + 8 * ceil(n / chunk_symbols) + 4 * ceil(n / 4)
+ * + 4.  It holds because an optimal code never spends more than 8 bits per
+ * byte on average (and 1 bit per byte with one distinct byte), so no read
+ * back is needed to size the output.  Returns 0 for an invalid
+ * chunk_symbols. */
+uint64_t huff_max_stream_size(uint64_t n, uint32_t chunk_symbols);
+
+/* Bytes of scratch (d_ws) that huff_encode and huff_compress need for n
+ * bytes.  Returns 0 for an invalid chunk_symbols. */
+uint64_t huff_workspace_size(uint64_t n, uint32_t chunk_symbols);
+
+/* Method 1, first step (Section III-A): d_hist[b] = number of bytes equal to
+ * b in d_in[0, n).  d_hist is u64[256]; the call clears it first.
+ * Errors: HUFF_ERR_INVALID_ARG (null or misaligned pointers),
+ * HUFF_ERR_CUDA. */
+huff_status_t huff_histogram(const uint8_t *d_in, uint64_t n, uint64_t *d_hist,
+                             huff_stream_t stream);
+
+/* Method 1, tree step (Section III-A): from d_hist (u64[256]) build the code
+ * lengths with the (weight, id) merge tree, then the canonical codes, into
+ * *d_cb.  One CTA; no host synchronisation.  Device errors in *d_status:
+ * HUFF_ERR_CODE_TOO_LONG (then *d_cb is all zero).  Returns
+ * HUFF_ERR_INVALID_ARG for null pointers, HUFF_ERR_CUDA on launch failure. */
+huff_status_t huff_build_codebook(const uint64_t *d_hist, huff_codebook_t *d_cb,
+                                  int32_t *d_status, huff_stream_t stream);
+
+/* Encode d_in[0, n) with *d_cb into the stream layout above at d_out.
+ * Method 1's coding step with Method 2's segments as chunks of
+ * chunk_symbols bytes (a multiple of 16 in [16, 2^24]).
+ *  - *d_out_bytes receives the exact stream size (also on a capacity
+ *    error, so the caller can retry with a larger buffer).
+ *  - out_cap: bytes available at d_out; huff_max_stream_size(n,
+ *    chunk_symbols) always suffices for a codebook built from d_in.
+ *  - d_ws / ws_bytes: scratch of at least huff_workspace_size(n,
+ *    chunk_symbols) bytes, 16-byte aligned; its contents are clobbered.
+ *  - Precondition: every byte value present in d_in has a code in *d_cb
+ *    (always true for a codebook built from d_in's histogram); otherwise
+ *    the stream is unspecified.
+ * Device errors: HUFF_ERR_CAPACITY, HUFF_ERR_TIMEOUT.  Host errors:
+ * HUFF_ERR_INVALID_ARG, HUFF_ERR_CUDA.  Calls sharing one d_ws must not
+ * overlap on the GPU. */
+huff_status_t huff_encode(const uint8_t *d_in, uint64_t n, const huff_codebook_t *d_cb,
+                          uint32_t chunk_symbols, uint8_t *d_out, uint64_t out_cap,
+                          uint64_t *d_out_bytes, void *d_ws, uint64_t ws_bytes,
+                          int32_t *d_status, huff_stream_t stream);
+
+/* Decode the stream d_stream[0, stream_bytes) into d_out[0, n) (Method 2's
+ * reassembly by chunk id; the code is lossless).  The stream is validated:
+ * header fields, a complete code (sum of 2^-len == 1, or one code of length
+ * 1), off[0] == 0, non-decreasing offsets within the payload, no chunk
+ * reading past the next chunk's offset and every chunk but the last ending
+ * exactly on it.  Any failure -> HUFF_ERR_CORRUPT_STREAM in *d_status; n
+ * larger than out_cap -> HUFF_ERR_CAPACITY.  *d_n receives n once the header
+ * is valid.  Trailing bytes after the payload are ignored.
+ * Host errors: HUFF_ERR_INVALID_ARG, HUFF_ERR_CUDA. */
+huff_status_t huff_decode(const uint8_t *d_stream, uint64_t stream_bytes, uint8_t *d_out,
+                          uint64_t out_cap, uint64_t *d_n, int32_t *d_status,
+                          huff_stream_t stream);
+
+/* Method 1 end to end on one stream, no host synchronisation: clear
+ * *d_status, huff_histogram, huff_build_codebook and huff_encode, with the
+ * histogram and codebook kept in d_ws (ws_bytes >= huff_workspace_size).
+ * Same arguments and errors as huff_encode. */
+huff_status_t huff_compress(const uint8_t *d_in, uint64_t n, uint32_t chunk_symbols,
+                            uint8_t *d_out, uint64_t out_cap, uint64_t *d_out_bytes,
+                            void *d_ws, uint64_t ws_bytes, int32_t *d_status,
+                            huff_stream_t stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HUFF_H */

@@ -1,0 +1,254 @@
+"""GB300 Huffman codec: Python binding of libhuff.so.
+
+Argument marshalling only: every step of the path runs in the library's CUDA
+kernels.  PyTorch supplies device memory and the current CUDA stream.  The
+functions named ``huff_*`` mirror the C ABI in ``include/huff.h`` one to one;
+``compress`` / ``decompress`` are conveniences that size the buffers,
+synchronise once and raise on a non-zero status.
+
+The library must have been built (``python -m paper_2306_11070_gb300.build``
+or ``__graft_entry__.build()``); there is no fallback of any kind, and every
+call raises if ``libhuff.so`` is missing.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import torch
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libhuff.so")
+
+HUFF_OK = 0
+HUFF_ERR_INVALID_ARG = -1
+HUFF_ERR_CODE_TOO_LONG = -2
+HUFF_ERR_CAPACITY = -3
+HUFF_ERR_CORRUPT_STREAM = -4
+HUFF_ERR_CUDA = -5
+HUFF_ERR_TIMEOUT = -6
+HUFF_ERR_BUDGET = -7
+HUFF_ERR_UNSUPPORTED = -8
+
+HEADER_BYTES = 272
+DEFAULT_CHUNK_SYMBOLS = 16384
+CODEBOOK_BYTES = 1288  # sizeof(huff_codebook_t)
+
+_lib = None
+
+
+class HuffError(RuntimeError):
+    def __init__(self, status: int, where: str = ""):
+        self.status = int(status)
+        super().__init__(f"{where}: {huff_status_str(status)} ({status})" if where else
+                         f"{huff_status_str(status)} ({status})")
+
+
+def lib() -> ctypes.CDLL:
+    """The loaded libhuff.so; raises if it has not been built."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with "
+                               "`python -m paper_2306_11070_gb300.build` (needs nvcc)")
+        L = ctypes.CDLL(LIB_PATH)
+        vp, u64, u32, i32 = ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_int32
+        L.huff_status_str.restype = ctypes.c_char_p
+        L.huff_status_str.argtypes = [i32]
+        L.huff_version.restype = ctypes.c_int
+        L.huff_version.argtypes = []
+        L.huff_max_stream_size.restype = u64
+        L.huff_max_stream_size.argtypes = [u64, u32]
+        L.huff_workspace_size.restype = u64
+        L.huff_workspace_size.argtypes = [u64, u32]
+        L.huff_histogram.restype = i32
+        L.huff_histogram.argtypes = [vp, u64, vp, vp]
+        L.huff_build_codebook.restype = i32
+        L.huff_build_codebook.argtypes = [vp, vp, vp, vp]
+        L.huff_encode.restype = i32
+        L.huff_encode.argtypes = [vp, u64, vp, u32, vp, u64, vp, vp, u64, vp, vp]
+        L.huff_decode.restype = i32
+        L.huff_decode.argtypes = [vp, u64, vp, u64, vp, vp, vp]
+        L.huff_compress.restype = i32
+        L.huff_compress.argtypes = [vp, u64, u32, vp, u64, vp, vp, u64, vp, vp]
+        _lib = L
+    return _lib
+
+
+# ---------------------------------------------------------------- helpers
+def _stream(stream) -> ctypes.c_void_p:
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    if isinstance(stream, torch.cuda.Stream):
+        return ctypes.c_void_p(stream.cuda_stream)
+    return ctypes.c_void_p(int(stream))
+
+
+def _ptr(t) -> ctypes.c_void_p:
+    if t is None:
+        return ctypes.c_void_p(0)
+    if isinstance(t, torch.Tensor):
+        if not t.is_cuda:
+            raise ValueError("device tensor expected")
+        if not t.is_contiguous():
+            raise ValueError("contiguous tensor expected")
+        return ctypes.c_void_p(t.data_ptr())
+    return ctypes.c_void_p(int(t))
+
+
+def _check(st: int, where: str):
+    if st != HUFF_OK:
+        raise HuffError(st, where)
+
+
+def _u8(t: torch.Tensor) -> torch.Tensor:
+    if t.dtype != torch.uint8:
+        raise TypeError("uint8 tensor expected")
+    return t.reshape(-1)
+
+
+def huff_status_str(status: int) -> str:
+    return lib().huff_status_str(int(status)).decode()
+
+
+def huff_version() -> int:
+    return int(lib().huff_version())
+
+
+def huff_max_stream_size(n: int, chunk_symbols: int = DEFAULT_CHUNK_SYMBOLS) -> int:
+    return int(lib().huff_max_stream_size(int(n), int(chunk_symbols)))
+
+
+def huff_workspace_size(n: int, chunk_symbols: int = DEFAULT_CHUNK_SYMBOLS) -> int:
+    return int(lib().huff_workspace_size(int(n), int(chunk_symbols)))
+
+
+def new_status(device=None) -> torch.Tensor:
+    """A zeroed int32 device status word."""
+    return torch.zeros(1, dtype=torch.int32, device=device or "cuda")
+
+
+# ---------------------------------------------------------------- C ABI mirror
+def huff_histogram(d_in: torch.Tensor, d_hist: torch.Tensor | None = None, stream=None):
+    """u64[256] byte counts (returned as int64 tensor bits)."""
+    x = _u8(d_in)
+    if d_hist is None:
+        d_hist = torch.empty(256, dtype=torch.int64, device=x.device)
+    _check(lib().huff_histogram(_ptr(x), x.numel(), _ptr(d_hist), _stream(stream)),
+           "huff_histogram")
+    return d_hist
+
+
+def huff_build_codebook(d_hist: torch.Tensor, d_cb: torch.Tensor | None = None,
+                        d_status: torch.Tensor | None = None, stream=None):
+    """(codebook bytes uint8[1288], status int32[1])."""
+    if d_cb is None:
+        d_cb = torch.empty(CODEBOOK_BYTES, dtype=torch.uint8, device=d_hist.device)
+    if d_status is None:
+        d_status = new_status(d_hist.device)
+    _check(lib().huff_build_codebook(_ptr(d_hist), _ptr(d_cb), _ptr(d_status), _stream(stream)),
+           "huff_build_codebook")
+    return d_cb, d_status
+
+
+def huff_encode(d_in: torch.Tensor, d_cb: torch.Tensor, chunk_symbols: int = DEFAULT_CHUNK_SYMBOLS,
+                d_out: torch.Tensor | None = None, d_out_bytes: torch.Tensor | None = None,
+                d_ws: torch.Tensor | None = None, d_status: torch.Tensor | None = None,
+                stream=None, out_cap: int | None = None):
+    """(stream buffer, out_bytes int64[1], status int32[1]); sizes not read back."""
+    x = _u8(d_in)
+    n = x.numel()
+    dev = x.device
+    if d_out is None:
+        d_out = torch.empty(huff_max_stream_size(n, chunk_symbols), dtype=torch.uint8, device=dev)
+    if d_out_bytes is None:
+        d_out_bytes = torch.zeros(1, dtype=torch.int64, device=dev)
+    if d_ws is None:
+        d_ws = torch.empty(max(huff_workspace_size(n, chunk_symbols), 256), dtype=torch.uint8,
+                           device=dev)
+    if d_status is None:
+        d_status = new_status(dev)
+    cap = d_out.numel() if out_cap is None else int(out_cap)
+    _check(lib().huff_encode(_ptr(x), n, _ptr(d_cb), int(chunk_symbols), _ptr(d_out), cap,
+                             _ptr(d_out_bytes), _ptr(d_ws), d_ws.numel(), _ptr(d_status),
+                             _stream(stream)), "huff_encode")
+    return d_out, d_out_bytes, d_status
+
+
+def huff_decode(d_stream: torch.Tensor, stream_bytes: int | None = None,
+                d_out: torch.Tensor | None = None, out_cap: int | None = None,
+                d_n: torch.Tensor | None = None, d_status: torch.Tensor | None = None,
+                stream=None):
+    """(output buffer, n int64[1], status int32[1]).  Without d_out the
+    header's n is read back once to size the output."""
+    s = _u8(d_stream)
+    nbytes = s.numel() if stream_bytes is None else int(stream_bytes)
+    dev = s.device
+    if d_out is None:
+        n = int.from_bytes(bytes(s[256:264].cpu().numpy()), "little") if s.numel() >= 264 else 0
+        d_out = torch.empty(max(n, 1), dtype=torch.uint8, device=dev)
+        out_cap = n if out_cap is None else out_cap
+    if out_cap is None:
+        out_cap = d_out.numel()
+    if d_n is None:
+        d_n = torch.zeros(1, dtype=torch.int64, device=dev)
+    if d_status is None:
+        d_status = new_status(dev)
+    _check(lib().huff_decode(_ptr(s), nbytes, _ptr(d_out), int(out_cap), _ptr(d_n),
+                             _ptr(d_status), _stream(stream)), "huff_decode")
+    return d_out, d_n, d_status
+
+
+def huff_compress(d_in: torch.Tensor, chunk_symbols: int = DEFAULT_CHUNK_SYMBOLS,
+                  d_out: torch.Tensor | None = None, d_out_bytes: torch.Tensor | None = None,
+                  d_ws: torch.Tensor | None = None, d_status: torch.Tensor | None = None,
+                  stream=None, out_cap: int | None = None):
+    """(stream buffer, out_bytes int64[1], status int32[1]), no host sync."""
+    x = _u8(d_in)
+    n = x.numel()
+    dev = x.device
+    if d_out is None:
+        d_out = torch.empty(huff_max_stream_size(n, chunk_symbols), dtype=torch.uint8, device=dev)
+    if d_out_bytes is None:
+        d_out_bytes = torch.zeros(1, dtype=torch.int64, device=dev)
+    if d_ws is None:
+        d_ws = torch.empty(huff_workspace_size(n, chunk_symbols), dtype=torch.uint8, device=dev)
+    if d_status is None:
+        d_status = torch.empty(1, dtype=torch.int32, device=dev)
+    cap = d_out.numel() if out_cap is None else int(out_cap)
+    _check(lib().huff_compress(_ptr(x), n, int(chunk_symbols), _ptr(d_out), cap,
+                               _ptr(d_out_bytes), _ptr(d_ws), d_ws.numel(), _ptr(d_status),
+                               _stream(stream)), "huff_compress")
+    return d_out, d_out_bytes, d_status
+
+
+# ---------------------------------------------------------------- conveniences
+def parse_codebook(d_cb: torch.Tensor):
+    """(len u8[256], code u32[256], nsym, max_len) as numpy, from a device codebook."""
+    import numpy as np
+    raw = d_cb.cpu().numpy().tobytes()
+    ln = np.frombuffer(raw[:256], dtype=np.uint8).copy()
+    code = np.frombuffer(raw[256:1280], dtype="<u4").copy()
+    nsym, max_len = np.frombuffer(raw[1280:1288], dtype="<u4")
+    return ln, code, int(nsym), int(max_len)
+
+
+def compress(x: torch.Tensor, chunk_symbols: int = DEFAULT_CHUNK_SYMBOLS, stream=None) -> torch.Tensor:
+    """Compress a uint8 CUDA tensor; returns the stream trimmed to its size."""
+    out, ob, st = huff_compress(x, chunk_symbols, stream=stream)
+    torch.cuda.current_stream().synchronize() if stream is None else torch.cuda.synchronize()
+    _check(int(st.item()), "compress")
+    return out[:int(ob.item())]
+
+
+def decompress(stream_t: torch.Tensor, stream=None) -> torch.Tensor:
+    """Decompress a stream held in a uint8 CUDA tensor."""
+    out, n, st = huff_decode(stream_t, stream=stream)
+    torch.cuda.current_stream().synchronize() if stream is None else torch.cuda.synchronize()
+    _check(int(st.item()), "decompress")
+    return out[:int(n.item())]
+
+
+__all__ = [name for name in dir() if name.startswith("huff_")] + [
+    "compress", "decompress", "parse_codebook", "new_status", "HuffError", "lib", "LIB_PATH",
+]

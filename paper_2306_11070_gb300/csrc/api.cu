@@ -1,0 +1,153 @@
+// C ABI of libhuff: argument checks, workspace layout and kernel launches.
+// Every step of the path runs in this library's kernels; nothing here
+// touches the data on the host.
+#include <cstdint>
+
+#include "huff_internal.cuh"
+
+namespace huff {
+
+int device_sm_count()
+{
+    static int cached[16] = {0};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 16)
+        dev = 0;
+    if (cached[dev] == 0) {
+        int v = 0;
+        if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v < 1)
+            v = 1;
+        cached[dev] = v;
+    }
+    return cached[dev];
+}
+
+namespace {
+
+// huff_compress workspace: histogram, codebook, then the encoder's part.
+constexpr uint64_t kWsHistOffset = 0;
+constexpr uint64_t kWsCodebookOffset = 2048;
+constexpr uint64_t kWsEncodeOffset = 4096;
+
+inline bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
+inline huff_status_t cuda_status(cudaError_t e) { return e == cudaSuccess ? HUFF_OK : HUFF_ERR_CUDA; }
+
+}  // namespace
+}  // namespace huff
+
+using namespace huff;
+
+extern "C" {
+
+const char *huff_status_str(huff_status_t status)
+{
+    switch (status) {
+    case HUFF_OK:
+        return "ok";
+    case HUFF_ERR_INVALID_ARG:
+        return "invalid argument";
+    case HUFF_ERR_CODE_TOO_LONG:
+        return "a code would be longer than 32 bits";
+    case HUFF_ERR_CAPACITY:
+        return "output buffer too small";
+    case HUFF_ERR_CORRUPT_STREAM:
+        return "corrupt stream";
+    case HUFF_ERR_CUDA:
+        return "CUDA error";
+    case HUFF_ERR_TIMEOUT:
+        return "device wait timed out";
+    case HUFF_ERR_BUDGET:
+        return "request exceeds the memory budget";
+    case HUFF_ERR_UNSUPPORTED:
+        return "unsupported";
+    default:
+        return "unknown status";
+    }
+}
+
+int huff_version(void) { return 100; }
+
+uint64_t huff_max_stream_size(uint64_t n, uint32_t chunk_symbols)
+{
+    if (!chunk_symbols_valid(chunk_symbols))
+        return 0;
+    return kHeaderBytes + 8 * ceil_div_u64(n, chunk_symbols) + 4 * ceil_div_u64(n, 4) + 4;
+}
+
+uint64_t huff_workspace_size(uint64_t n, uint32_t chunk_symbols)
+{
+    if (!chunk_symbols_valid(chunk_symbols))
+        return 0;
+    const uint64_t b = kWsEncodeOffset + encode_workspace_bytes(n);
+    return (b + 255) & ~uint64_t(255);
+}
+
+huff_status_t huff_histogram(const uint8_t *d_in, uint64_t n, uint64_t *d_hist, huff_stream_t stream)
+{
+    if (!d_hist || (n && !d_in) || (d_in && !aligned16(d_in)))
+        return HUFF_ERR_INVALID_ARG;
+    return cuda_status(launch_histogram(d_in, n, reinterpret_cast<unsigned long long *>(d_hist),
+                                        reinterpret_cast<cudaStream_t>(stream)));
+}
+
+huff_status_t huff_build_codebook(const uint64_t *d_hist, huff_codebook_t *d_cb, int32_t *d_status,
+                                  huff_stream_t stream)
+{
+    if (!d_hist || !d_cb || !d_status)
+        return HUFF_ERR_INVALID_ARG;
+    return cuda_status(launch_build_codebook(reinterpret_cast<const unsigned long long *>(d_hist),
+                                             d_cb, d_status,
+                                             reinterpret_cast<cudaStream_t>(stream)));
+}
+
+huff_status_t huff_encode(const uint8_t *d_in, uint64_t n, const huff_codebook_t *d_cb,
+                          uint32_t chunk_symbols, uint8_t *d_out, uint64_t out_cap,
+                          uint64_t *d_out_bytes, void *d_ws, uint64_t ws_bytes, int32_t *d_status,
+                          huff_stream_t stream)
+{
+    if (!chunk_symbols_valid(chunk_symbols) || !d_cb || !d_out || !d_out_bytes || !d_ws ||
+        !d_status || (n && !d_in) || (d_in && !aligned16(d_in)) || !aligned16(d_out) ||
+        !aligned16(d_ws) || ws_bytes < encode_workspace_bytes(n) ||
+        n > (uint64_t)UINT32_MAX * 4096u)
+        return HUFF_ERR_INVALID_ARG;
+    return cuda_status(launch_encode(d_in, n, d_cb, chunk_symbols, d_out, out_cap,
+                                     reinterpret_cast<unsigned long long *>(d_out_bytes), d_ws,
+                                     d_status, reinterpret_cast<cudaStream_t>(stream)));
+}
+
+huff_status_t huff_decode(const uint8_t *d_stream, uint64_t stream_bytes, uint8_t *d_out,
+                          uint64_t out_cap, uint64_t *d_n, int32_t *d_status, huff_stream_t stream)
+{
+    if (!d_stream || !d_n || !d_status || !aligned16(d_stream) || (d_out && !aligned16(d_out)) ||
+        (!d_out && out_cap))
+        return HUFF_ERR_INVALID_ARG;
+    return cuda_status(launch_decode(d_stream, stream_bytes, d_out, out_cap,
+                                     reinterpret_cast<unsigned long long *>(d_n), d_status,
+                                     reinterpret_cast<cudaStream_t>(stream)));
+}
+
+huff_status_t huff_compress(const uint8_t *d_in, uint64_t n, uint32_t chunk_symbols, uint8_t *d_out,
+                            uint64_t out_cap, uint64_t *d_out_bytes, void *d_ws, uint64_t ws_bytes,
+                            int32_t *d_status, huff_stream_t stream)
+{
+    if (!chunk_symbols_valid(chunk_symbols) || !d_ws || !aligned16(d_ws) || !d_status ||
+        ws_bytes < huff_workspace_size(n, chunk_symbols))
+        return HUFF_ERR_INVALID_ARG;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    uint8_t *ws = static_cast<uint8_t *>(d_ws);
+    uint64_t *hist = reinterpret_cast<uint64_t *>(ws + kWsHistOffset);
+    huff_codebook_t *cb = reinterpret_cast<huff_codebook_t *>(ws + kWsCodebookOffset);
+    if (cudaMemsetAsync(d_status, 0, sizeof(int32_t), s) != cudaSuccess)
+        return HUFF_ERR_CUDA;
+    huff_status_t st = huff_histogram(d_in, n, hist, stream);
+    if (st != HUFF_OK)
+        return st;
+    st = huff_build_codebook(hist, cb, d_status, stream);
+    if (st != HUFF_OK)
+        return st;
+    return huff_encode(d_in, n, cb, chunk_symbols, d_out, out_cap, d_out_bytes,
+                       ws + kWsEncodeOffset, ws_bytes - kWsEncodeOffset, d_status, stream);
+}
+
+}  // extern "C"

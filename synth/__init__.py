@@ -65,6 +65,8 @@ def _load():
             fn.argtypes = [u8p, ctypes.c_uint64, ctypes.c_uint64]
         lib.synth_geometric_p.restype = None
         lib.synth_geometric_p.argtypes = [u8p, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_double]
+        lib.synth_shuffle.restype = None
+        lib.synth_shuffle.argtypes = [u8p, ctypes.c_uint64, ctypes.c_uint64]
         lib.synth_log_uniform_sizes.restype = None
         lib.synth_log_uniform_sizes.argtypes = [u64p, ctypes.c_uint32, ctypes.c_uint64,
                                                 ctypes.c_uint64, ctypes.c_uint64]
@@ -127,6 +129,21 @@ def single(n: int, byte: int = 0x61, out=None) -> np.ndarray:
     a = _out(n, out)
     a[:n] = byte
     return a[:n]
+
+
+def shuffle(a: np.ndarray, seed: int) -> np.ndarray:
+    """Seeded Fisher-Yates shuffle of a uint8 array, in place."""
+    assert a.dtype == np.uint8 and a.flags.c_contiguous
+    _load().synth_shuffle(_ptr(a, ctypes.c_uint8), a.size, seed)
+    return a
+
+
+def counted(counts, seed: int) -> np.ndarray:
+    """Bytes with exactly counts[b] copies of byte b, in seeded random order
+    (for example Fibonacci counts, the deepest possible code tree)."""
+    counts = [int(c) for c in counts]
+    a = np.repeat(np.arange(len(counts), dtype=np.uint8), counts)
+    return shuffle(np.ascontiguousarray(a), seed)
 
 
 def log_uniform_sizes(count: int, seed: int = 3, lo: int = 1024, hi: int = 4 * MiB) -> np.ndarray:

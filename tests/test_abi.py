@@ -1,0 +1,77 @@
+"""The C-ABI library builds, loads without a GPU and exports every entry point
+that include/*.h declares; host-only calls agree with the oracle's sizes."""
+import glob
+import os
+import re
+
+import pytest
+
+import oracle
+import paper_2306_11070_gb300 as hg
+from paper_2306_11070_gb300 import build as nvbuild
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    names = set()
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        text = open(h).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        text = re.sub(r"//[^\n]*", "", text)
+        for m in re.finditer(r"\b(huff_[a-z0-9_]+)\s*\(", text):
+            names.add(m.group(1))
+    return sorted(names)
+
+
+@pytest.fixture(scope="module")
+def lib():
+    nvbuild.build()
+    return hg.lib()
+
+
+def test_header_declares_the_boundary():
+    names = _declared()
+    for must in ("huff_histogram", "huff_build_codebook", "huff_encode", "huff_decode",
+                 "huff_compress", "huff_max_stream_size", "huff_workspace_size",
+                 "huff_status_str"):
+        assert must in names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    missing = [n for n in _declared() if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+@pytest.mark.parametrize("n", [0, 1, 15, 16, 17, 4095, 4096, 16384, 16385, 10**9, 1 << 30])
+@pytest.mark.parametrize("cs", [16, 1024, 16384, 1 << 24])
+def test_max_stream_size_matches_oracle(lib, n, cs):
+    assert hg.huff_max_stream_size(n, cs) == oracle.max_stream_size(n, cs)
+
+
+@pytest.mark.parametrize("cs", [0, 8, 17, 100, (1 << 24) + 16])
+def test_invalid_chunk_sizes(lib, cs):
+    assert hg.huff_max_stream_size(100, cs) == 0
+    assert hg.huff_workspace_size(100, cs) == 0
+
+
+def test_workspace_grows_with_n(lib):
+    a = hg.huff_workspace_size(1 << 20)
+    b = hg.huff_workspace_size(1 << 30)
+    assert 0 < a < b and b % 256 == 0
+
+
+def test_status_strings(lib):
+    for st in range(-8, 1):
+        assert hg.huff_status_str(st)
+    assert hg.huff_status_str(-4) == "corrupt stream"
+
+
+def test_product_never_touches_the_oracle():
+    pkg = os.path.join(ROOT, "paper_2306_11070_gb300")
+    files = glob.glob(os.path.join(pkg, "**", "*.*"), recursive=True)
+    for f in files:
+        if f.endswith((".py", ".cu", ".cuh", ".h", ".cpp")):
+            text = open(f).read()
+            assert "import oracle" not in text and "huff_oracle" not in text, f
+            assert "from oracle" not in text, f

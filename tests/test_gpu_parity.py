@@ -1,0 +1,340 @@
+"""GPU parity: the CUDA path through the C ABI against the CPU oracle.
+
+Integer work, so the bar is bit-exact everywhere: histogram, code lengths and
+codes, the whole stream (header, chunk offsets, payload), decoded bytes and
+the device status of every error path.  Sizes span several 4096-symbol
+encode tiles, several chunks and ragged tails; the full-size workloads are
+checked on their whole histogram, codebook and offset table, on sampled
+chunk payloads, and by the round trip.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import synth
+import paper_2306_11070_gb300 as hg
+from paper_2306_11070_gb300 import build as nvbuild
+
+pytestmark = pytest.mark.gpu
+MiB = 1 << 20
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    nvbuild.build()
+    hg.lib()
+    torch.cuda.init()
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def gpu_codebook(x_np):
+    d = dev(x_np) if x_np.size else torch.empty(0, dtype=torch.uint8, device="cuda")
+    h = hg.huff_histogram(d)
+    cb, st = hg.huff_build_codebook(h)
+    torch.cuda.synchronize()
+    return d, h, cb, int(st.item())
+
+
+def gpu_encode(d, cb, cs=16384, cap=None):
+    n = d.numel()
+    out_cap = hg.huff_max_stream_size(n, cs) if cap is None else cap
+    out = torch.zeros(max(out_cap, 16), dtype=torch.uint8, device="cuda")
+    o, ob, st = hg.huff_encode(d, cb, cs, d_out=out, out_cap=out_cap)
+    torch.cuda.synchronize()
+    return o, int(ob.item()), int(st.item())
+
+
+def gpu_decode(stream_np_or_t, cap=None):
+    s = stream_np_or_t if isinstance(stream_np_or_t, torch.Tensor) else dev(stream_np_or_t)
+    if s.numel() == 0:
+        s = torch.zeros(16, dtype=torch.uint8, device="cuda")[:0]
+    nbytes = s.numel()
+    buf = torch.zeros(max(nbytes, 16), dtype=torch.uint8, device="cuda")
+    buf[:nbytes] = s
+    n_hdr = int.from_bytes(bytes(s[256:264].cpu().numpy()), "little") if nbytes >= 264 else 0
+    out_cap = min(n_hdr, 1 << 33) if cap is None else cap
+    out = torch.zeros(max(out_cap, 16), dtype=torch.uint8, device="cuda")
+    o, n, st = hg.huff_decode(buf, nbytes, d_out=out, out_cap=out_cap)
+    torch.cuda.synchronize()
+    return o, int(n.item()), int(st.item())
+
+
+# ------------------------------------------------------------------ inputs
+GENS = {
+    "zipf": lambda n, s: synth.zipf_ascii(n, s),
+    "text": lambda n, s: synth.text(n, s),
+    "uniform": lambda n, s: synth.uniform(n, s),
+    "geometric": lambda n, s: synth.geometric(n, s),
+    "single": lambda n, s: synth.single(n, 0x61),
+    "skew4": lambda n, s: synth.geometric_p(n, s, 0.75),
+}
+SIZES = [1, 2, 15, 16, 17, 31, 32, 33, 4095, 4096, 4097, 16383, 16384, 16385,
+         3 * 16384 + 4096 * 2 + 123, 100003, MiB + 7]
+
+
+# ------------------------------------------------------------------ histogram
+@pytest.mark.parametrize("gen", list(GENS))
+@pytest.mark.parametrize("n", [0, 1, 15, 16, 17, 4096 * 16 + 5, 3 * MiB + 11])
+def test_histogram(gen, n):
+    x = GENS[gen](n, 7)
+    d = dev(x) if n else torch.empty(0, dtype=torch.uint8, device="cuda")
+    h = hg.huff_histogram(d).cpu().numpy().view(np.uint64)
+    assert np.array_equal(h, oracle.histogram(x))
+
+
+# ------------------------------------------------------------------ codebook
+def _hists(count, seed):
+    rng = np.random.default_rng(seed)
+    for _ in range(count):
+        k = int(rng.integers(1, 257))
+        syms = rng.choice(256, size=k, replace=False)
+        kind = int(rng.integers(0, 3))
+        if kind == 0:
+            w = rng.integers(1, 4, size=k)
+        elif kind == 1:
+            w = rng.integers(1, 1 << 40, size=k)
+        else:
+            w = np.floor(1e5 * rng.pareto(1.1, size=k)).astype(np.int64) + 1
+        h = np.zeros(256, dtype=np.uint64)
+        h[syms] = w.astype(np.uint64)
+        yield h
+
+
+def _gpu_cb_from_hist(h):
+    dh = torch.from_numpy(h.view(np.int64)).cuda()
+    cb, st = hg.huff_build_codebook(dh)
+    torch.cuda.synchronize()
+    return hg.parse_codebook(cb), int(st.item())
+
+
+def test_codebook_random_histograms():
+    for h in _hists(400, 3):
+        (ln, code, nsym, mx), st = _gpu_cb_from_hist(h)
+        ost, oln = oracle.code_lengths(h)
+        assert st == ost
+        if ost != oracle.OK:
+            continue
+        assert np.array_equal(ln, oln)
+        assert np.array_equal(code, oracle.canonical_codes(oln))
+        assert nsym == int((h > 0).sum()) and mx == int(oln.max())
+
+
+def test_codebook_fibonacci_boundary():
+    f = [1, 1]
+    while len(f) < 34:
+        f.append(f[-1] + f[-2])
+    h = np.zeros(256, dtype=np.uint64)
+    h[:33] = f[:33]
+    (ln, code, nsym, mx), st = _gpu_cb_from_hist(h)
+    ost, oln = oracle.code_lengths(h)
+    assert st == 0 and ost == 0 and mx == 32 and np.array_equal(ln, oln)
+    assert np.array_equal(code, oracle.canonical_codes(oln))
+    h = np.zeros(256, dtype=np.uint64)
+    h[:34] = f[:34]
+    (_, _, _, _), st = _gpu_cb_from_hist(h)
+    assert st == hg.HUFF_ERR_CODE_TOO_LONG == oracle.code_lengths(h)[0]
+
+
+def test_codebook_empty_and_single():
+    (ln, code, nsym, mx), st = _gpu_cb_from_hist(np.zeros(256, dtype=np.uint64))
+    assert st == 0 and not ln.any() and nsym == 0 and mx == 0
+    h = np.zeros(256, dtype=np.uint64)
+    h[77] = 5
+    (ln, code, nsym, mx), st = _gpu_cb_from_hist(h)
+    assert st == 0 and ln[77] == 1 and code[77] == 0 and nsym == 1 and mx == 1
+
+
+# ------------------------------------------------------------------ encode / decode
+def _check_roundtrip(x, cs=16384):
+    d, h, cb, st = gpu_codebook(x)
+    assert st == 0
+    ln = hg.parse_codebook(cb)[0]
+    ost, oln = oracle.code_lengths(oracle.histogram(x))
+    assert np.array_equal(ln, oln)
+    out, nbytes, st = gpu_encode(d, cb, cs)
+    ost, ref, need = oracle.encode(x, oln, cs)
+    assert st == 0 and ost == 0
+    assert nbytes == need
+    got = out[:nbytes].cpu().numpy()
+    assert np.array_equal(got, ref)
+    back, n, st = gpu_decode(out[:nbytes])
+    assert st == 0 and n == x.size
+    assert np.array_equal(back[:n].cpu().numpy(), x)
+
+
+@pytest.mark.parametrize("gen", list(GENS))
+@pytest.mark.parametrize("n", SIZES)
+def test_stream_bit_exact_and_round_trip(gen, n):
+    _check_roundtrip(GENS[gen](n, 11 + n % 97))
+
+
+@pytest.mark.parametrize("cs", [16, 32, 48, 1024, 4096, 4112, 65536])
+def test_chunk_sizes(cs):
+    _check_roundtrip(synth.text(5 * 4096 + 77, 5), cs)
+    _check_roundtrip(synth.zipf_ascii(3 * 65536 + 5, 6), cs)
+
+
+def test_empty_input():
+    x = np.zeros(0, dtype=np.uint8)
+    d, h, cb, st = gpu_codebook(x)
+    out, nbytes, st = gpu_encode(d, cb)
+    ost, ref, need = oracle.encode(x, np.zeros(256, np.uint8))
+    assert st == 0 and nbytes == need == 272
+    assert np.array_equal(out[:nbytes].cpu().numpy(), ref)
+    back, n, st = gpu_decode(out[:nbytes])
+    assert st == 0 and n == 0
+
+
+@pytest.mark.parametrize("k", [25, 28, 30, 32])
+def test_long_codes(k):
+    # Fibonacci counts give the deepest trees: codes up to k-1 bits
+    f = [1, 1]
+    while len(f) < k:
+        f.append(f[-1] + f[-2])
+    x = synth.counted(f[:k], seed=k)
+    _check_roundtrip(x)
+    _check_roundtrip(x, cs=64)
+
+
+def test_oracle_stream_decodes_on_gpu():
+    x = synth.text(200001, 3)
+    st, s = oracle.compress(x, 1024)
+    back, n, st = gpu_decode(s)
+    assert st == 0 and np.array_equal(back[:n].cpu().numpy(), x)
+
+
+def test_compress_matches_oracle():
+    x = synth.zipf_ascii(MiB, 0)
+    got = hg.compress(dev(x)).cpu().numpy()
+    st, ref = oracle.compress(x)
+    assert np.array_equal(got, ref)
+
+
+# ------------------------------------------------------------------ error paths
+def _corruptions():
+    x = synth.text(40000, 21)
+    st, s = oracle.compress(x, 1024)
+    chunks = (x.size + 1023) // 1024
+    o = 272 + 8
+    cases = {"short_header": s[:271].copy()}
+    t = s.copy(); t[264:268] = np.frombuffer((1000).to_bytes(4, "little"), np.uint8)
+    cases["bad_chunk_size"] = t
+    t = s.copy(); t[ord("e")] = max(1, int(t[ord("e")]) - 1); cases["kraft_over"] = t
+    t = s.copy(); t[ord("e")] = int(t[ord("e")]) + 1; cases["kraft_under"] = t
+    t = s.copy(); t[268] ^= 1; cases["max_len_field"] = t
+    t = s.copy(); t[0] = 33; cases["len_above_32"] = t
+    t = s.copy(); t[256:264] = np.frombuffer((10**12).to_bytes(8, "little"), np.uint8)
+    cases["table_too_big"] = t
+    t = s.copy()
+    t[o:o + 8] = np.frombuffer((int.from_bytes(bytes(t[o:o + 8]), "little") + 1)
+                               .to_bytes(8, "little"), np.uint8)
+    cases["offset_shifted"] = t
+    t = s.copy(); t[272:280] = np.frombuffer((5).to_bytes(8, "little"), np.uint8)
+    cases["first_offset"] = t
+    t = s.copy(); t[o:o + 8], t[o + 8:o + 16] = t[o + 8:o + 16].copy(), t[o:o + 8].copy()
+    cases["offsets_swapped"] = t
+    cases["payload_cut"] = s[:272 + 8 * chunks + 8].copy()
+    t = s.copy(); t[-1] ^= 0xFF; cases["last_word_flipped"] = t
+    t = s.copy(); t[-9] ^= 0x10; cases["payload_bit"] = t
+    x1 = synth.single(100, 0x61)
+    st, s1 = oracle.compress(x1)
+    t = s1.copy(); t[-1] |= 0x80; cases["single_symbol_one_bit"] = t
+    return cases
+
+
+@pytest.mark.parametrize("name", list(_corruptions()))
+def test_corrupt_stream_status_matches_oracle(name):
+    s = _corruptions()[name]
+    ost, oback, on = oracle.decode(s, cap=1 << 20)
+    back, n, st = gpu_decode(s, cap=1 << 20)
+    assert st == ost, (name, st, ost)
+    if ost == 0:  # a change the format cannot detect: both sides decode the same bytes
+        assert n == on and np.array_equal(back[:n].cpu().numpy(), oback)
+
+
+def test_capacity_statuses():
+    x = synth.text(100000, 4)
+    d, h, cb, st = gpu_codebook(x)
+    ln = hg.parse_codebook(cb)[0]
+    ost, ref, need = oracle.encode(x, ln)
+    out, nbytes, st = gpu_encode(d, cb, cap=need - 1)
+    assert st == hg.HUFF_ERR_CAPACITY and nbytes == need
+    out, nbytes, st = gpu_encode(d, cb, cap=need)
+    assert st == 0 and np.array_equal(out[:need].cpu().numpy(), ref)
+    out, nbytes, st = gpu_encode(d, cb, cap=200)
+    assert st == hg.HUFF_ERR_CAPACITY
+    _, n, st = gpu_decode(ref, cap=x.size - 1)
+    assert st == hg.HUFF_ERR_CAPACITY == oracle.decode(ref, cap=x.size - 1)[0] and n == x.size
+
+
+def test_chain_stops_after_error():
+    f = [1, 1]
+    while len(f) < 34:
+        f.append(f[-1] + f[-2])
+    x = synth.counted(f, seed=1)
+    d = dev(x)
+    out, ob, st = hg.huff_compress(d)
+    torch.cuda.synchronize()
+    assert int(st.item()) == hg.HUFF_ERR_CODE_TOO_LONG
+    assert int(ob.item()) == 0  # the encoder never ran
+
+
+def test_host_argument_errors():
+    d = torch.zeros(64, dtype=torch.uint8, device="cuda")
+    with pytest.raises(hg.HuffError) as e:
+        hg.huff_histogram(d[1:17])  # misaligned
+    assert e.value.status == hg.HUFF_ERR_INVALID_ARG
+    with pytest.raises(hg.HuffError):
+        hg.huff_encode(d, torch.zeros(1288, dtype=torch.uint8, device="cuda"), chunk_symbols=100)
+
+
+# ------------------------------------------------------------------ full-size workloads
+def _full_size_check(x, cs=16384, samples=24):
+    """Whole histogram, codebook and offset table against the oracle; sampled
+    chunk payloads against the oracle's packing; round trip on the GPU."""
+    d, h, cb, st = gpu_codebook(x)
+    assert np.array_equal(h.cpu().numpy().view(np.uint64), oracle.histogram(x))
+    ost, oln = oracle.code_lengths(oracle.histogram(x))
+    assert st == ost
+    if ost != 0:
+        return
+    ln, code, nsym, mx = hg.parse_codebook(cb)
+    assert np.array_equal(ln, oln) and np.array_equal(code, oracle.canonical_codes(oln))
+    out, nbytes, st = gpu_encode(d, cb, cs)
+    assert st == 0
+    chunks = (x.size + cs - 1) // cs
+    st, ooff, total = oracle.chunk_offsets(x, oln, cs)
+    assert nbytes == 272 + 8 * chunks + 4 * ((total + 31) // 32)
+    head = out[:272 + 8 * chunks].cpu().numpy()
+    assert np.array_equal(head[:256], oln)
+    off = head[272:].view("<u8")
+    assert np.array_equal(off, ooff)
+    rng = np.random.default_rng(1)
+    pick = sorted(set([0, chunks - 1] + list(rng.integers(0, chunks, size=samples))))
+    pay0 = 272 + 8 * chunks
+    for c in pick:
+        st, w, nb = oracle.pack_bits(x[c * cs:(c + 1) * cs], oln)
+        a = int(ooff[c])
+        wlo, whi = a // 32, (a + nb + 31) // 32
+        gw = out[pay0 + 4 * wlo:pay0 + 4 * whi].cpu().numpy().view("<u4")
+        gb = np.unpackbits(gw.astype(">u4").view(np.uint8))[a - 32 * wlo:a - 32 * wlo + nb]
+        ob = np.unpackbits(w.astype(">u4").view(np.uint8))[:nb]
+        assert np.array_equal(gb, ob), c
+    # padding bits after the last code are zero
+    lastw = int(out[nbytes - 4:nbytes].cpu().numpy().view("<u4")[0])
+    pad = (32 - total % 32) % 32
+    assert lastw & ((1 << pad) - 1) == 0
+    back, n, st = gpu_decode(out[:nbytes])
+    assert st == 0 and n == x.size
+    assert torch.equal(back[:n], d)
+
+
+@pytest.mark.parametrize("name", ["zipf_ascii_1m", "text_64m", "text_1g", "uniform_1g",
+                                  "geometric_1g", "single_1g"])
+def test_full_size_workloads(name):
+    x = synth.make(name)
+    _full_size_check(x)
