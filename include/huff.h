@@ -107,6 +107,18 @@ uint64_t huff_workspace_size(uint64_t n, uint32_t chunk_symbols);
 huff_status_t huff_histogram(const uint8_t *d_in, uint64_t n, uint64_t *d_hist,
                              huff_stream_t stream);
 
+/* Bytes of per-unit histograms that huff_histogram_units writes for n input
+ * bytes: 512 (u16[256]) per 16384-byte unit. */
+uint64_t huff_unit_hist_size(uint64_t n);
+
+/* huff_histogram plus every 16384-byte unit's own histogram, u16[256] per
+ * unit, into d_unit_hist (huff_unit_hist_size(n) bytes, 16-byte aligned).
+ * huff_encode_units turns them into each unit's bit offset (a dot product
+ * with the code lengths), which spares the encoder a counting pass over the
+ * input.  Errors as huff_histogram. */
+huff_status_t huff_histogram_units(const uint8_t *d_in, uint64_t n, uint64_t *d_hist,
+                                   uint16_t *d_unit_hist, huff_stream_t stream);
+
 /* Method 1, tree step (Section III-A): from d_hist (u64[256]) build the code
  * lengths with the (weight, id) merge tree, then the canonical codes, into
  * *d_cb.  One CTA; no host synchronisation.  Device errors in *d_status:
@@ -135,6 +147,15 @@ huff_status_t huff_encode(const uint8_t *d_in, uint64_t n, const huff_codebook_t
                           uint64_t *d_out_bytes, void *d_ws, uint64_t ws_bytes,
                           int32_t *d_status, huff_stream_t stream);
 
+/* huff_encode for a codebook built from the same input, with the unit
+ * histograms of huff_histogram_units(d_in, n, ...): same arguments, result
+ * and errors, one input read fewer. */
+huff_status_t huff_encode_units(const uint8_t *d_in, uint64_t n, const huff_codebook_t *d_cb,
+                                const uint16_t *d_unit_hist, uint32_t chunk_symbols,
+                                uint8_t *d_out, uint64_t out_cap, uint64_t *d_out_bytes,
+                                void *d_ws, uint64_t ws_bytes, int32_t *d_status,
+                                huff_stream_t stream);
+
 /* Decode the stream d_stream[0, stream_bytes) into d_out[0, n) (Method 2's
  * reassembly by chunk id; the code is lossless).  The stream is validated:
  * header fields, a complete code (sum of 2^-len == 1, or one code of length
@@ -149,9 +170,10 @@ huff_status_t huff_decode(const uint8_t *d_stream, uint64_t stream_bytes, uint8_
                           huff_stream_t stream);
 
 /* Method 1 end to end on one stream, no host synchronisation: clear
- * *d_status, huff_histogram, huff_build_codebook and huff_encode, with the
- * histogram and codebook kept in d_ws (ws_bytes >= huff_workspace_size).
- * Same arguments and errors as huff_encode. */
+ * *d_status, huff_histogram_units, huff_build_codebook and
+ * huff_encode_units, with the histograms and codebook kept in d_ws
+ * (ws_bytes >= huff_workspace_size).  Same arguments and errors as
+ * huff_encode. */
 huff_status_t huff_compress(const uint8_t *d_in, uint64_t n, uint32_t chunk_symbols,
                             uint8_t *d_out, uint64_t out_cap, uint64_t *d_out_bytes,
                             void *d_ws, uint64_t ws_bytes, int32_t *d_status,

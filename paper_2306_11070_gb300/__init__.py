@@ -63,6 +63,12 @@ def lib() -> ctypes.CDLL:
         L.huff_workspace_size.argtypes = [u64, u32]
         L.huff_histogram.restype = i32
         L.huff_histogram.argtypes = [vp, u64, vp, vp]
+        L.huff_unit_hist_size.restype = u64
+        L.huff_unit_hist_size.argtypes = [u64]
+        L.huff_histogram_units.restype = i32
+        L.huff_histogram_units.argtypes = [vp, u64, vp, vp, vp]
+        L.huff_encode_units.restype = i32
+        L.huff_encode_units.argtypes = [vp, u64, vp, vp, u32, vp, u64, vp, vp, u64, vp, vp]
         L.huff_build_codebook.restype = i32
         L.huff_build_codebook.argtypes = [vp, vp, vp, vp]
         L.huff_encode.restype = i32
@@ -139,6 +145,24 @@ def huff_histogram(d_in: torch.Tensor, d_hist: torch.Tensor | None = None, strea
     return d_hist
 
 
+def huff_unit_hist_size(n: int) -> int:
+    return int(lib().huff_unit_hist_size(int(n)))
+
+
+def huff_histogram_units(d_in: torch.Tensor, d_hist: torch.Tensor | None = None,
+                         d_unit_hist: torch.Tensor | None = None, stream=None):
+    """(u64[256] counts, u16[256] per 16 KiB unit) -- the latter as uint8 bytes."""
+    x = _u8(d_in)
+    if d_hist is None:
+        d_hist = torch.empty(256, dtype=torch.int64, device=x.device)
+    if d_unit_hist is None:
+        d_unit_hist = torch.empty(max(huff_unit_hist_size(x.numel()), 16), dtype=torch.uint8,
+                                  device=x.device)
+    _check(lib().huff_histogram_units(_ptr(x), x.numel(), _ptr(d_hist), _ptr(d_unit_hist),
+                                      _stream(stream)), "huff_histogram_units")
+    return d_hist, d_unit_hist
+
+
 def huff_build_codebook(d_hist: torch.Tensor, d_cb: torch.Tensor | None = None,
                         d_status: torch.Tensor | None = None, stream=None):
     """(codebook bytes uint8[1288], status int32[1])."""
@@ -172,6 +196,31 @@ def huff_encode(d_in: torch.Tensor, d_cb: torch.Tensor, chunk_symbols: int = DEF
     _check(lib().huff_encode(_ptr(x), n, _ptr(d_cb), int(chunk_symbols), _ptr(d_out), cap,
                              _ptr(d_out_bytes), _ptr(d_ws), d_ws.numel(), _ptr(d_status),
                              _stream(stream)), "huff_encode")
+    return d_out, d_out_bytes, d_status
+
+
+def huff_encode_units(d_in: torch.Tensor, d_cb: torch.Tensor, d_unit_hist: torch.Tensor,
+                      chunk_symbols: int = DEFAULT_CHUNK_SYMBOLS,
+                      d_out: torch.Tensor | None = None, d_out_bytes: torch.Tensor | None = None,
+                      d_ws: torch.Tensor | None = None, d_status: torch.Tensor | None = None,
+                      stream=None, out_cap: int | None = None):
+    """huff_encode with the unit histograms of huff_histogram_units."""
+    x = _u8(d_in)
+    n = x.numel()
+    dev = x.device
+    if d_out is None:
+        d_out = torch.empty(huff_max_stream_size(n, chunk_symbols), dtype=torch.uint8, device=dev)
+    if d_out_bytes is None:
+        d_out_bytes = torch.zeros(1, dtype=torch.int64, device=dev)
+    if d_ws is None:
+        d_ws = torch.empty(max(huff_workspace_size(n, chunk_symbols), 256), dtype=torch.uint8,
+                           device=dev)
+    if d_status is None:
+        d_status = new_status(dev)
+    cap = d_out.numel() if out_cap is None else int(out_cap)
+    _check(lib().huff_encode_units(_ptr(x), n, _ptr(d_cb), _ptr(d_unit_hist), int(chunk_symbols),
+                                   _ptr(d_out), cap, _ptr(d_out_bytes), _ptr(d_ws), d_ws.numel(),
+                                   _ptr(d_status), _stream(stream)), "huff_encode_units")
     return d_out, d_out_bytes, d_status
 
 

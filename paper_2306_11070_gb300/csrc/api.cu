@@ -24,10 +24,16 @@ int device_sm_count()
 
 namespace {
 
-// huff_compress workspace: histogram, codebook, then the encoder's part.
+// huff_compress workspace: histogram, codebook, per-unit histograms, then
+// the encoder's part (unit bit counts and offsets).
 constexpr uint64_t kWsHistOffset = 0;
 constexpr uint64_t kWsCodebookOffset = 2048;
-constexpr uint64_t kWsEncodeOffset = 4096;
+constexpr uint64_t kWsUnitHistOffset = 4096;
+
+inline uint64_t unit_hist_bytes(uint64_t n)
+{
+    return 512 * ((n + kUnitSymbols - 1) / kUnitSymbols);
+}
 
 inline bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
 
@@ -79,7 +85,7 @@ uint64_t huff_workspace_size(uint64_t n, uint32_t chunk_symbols)
 {
     if (!chunk_symbols_valid(chunk_symbols))
         return 0;
-    const uint64_t b = kWsEncodeOffset + encode_workspace_bytes(n);
+    const uint64_t b = kWsUnitHistOffset + unit_hist_bytes(n) + encode_workspace_bytes(n);
     return (b + 255) & ~uint64_t(255);
 }
 
@@ -88,7 +94,19 @@ huff_status_t huff_histogram(const uint8_t *d_in, uint64_t n, uint64_t *d_hist, 
     if (!d_hist || (n && !d_in) || (d_in && !aligned16(d_in)))
         return HUFF_ERR_INVALID_ARG;
     return cuda_status(launch_histogram(d_in, n, reinterpret_cast<unsigned long long *>(d_hist),
-                                        reinterpret_cast<cudaStream_t>(stream)));
+                                        nullptr, reinterpret_cast<cudaStream_t>(stream)));
+}
+
+uint64_t huff_unit_hist_size(uint64_t n) { return unit_hist_bytes(n); }
+
+huff_status_t huff_histogram_units(const uint8_t *d_in, uint64_t n, uint64_t *d_hist,
+                                   uint16_t *d_unit_hist, huff_stream_t stream)
+{
+    if (!d_hist || !d_unit_hist || (n && !d_in) || (d_in && !aligned16(d_in)) ||
+        !aligned16(d_unit_hist))
+        return HUFF_ERR_INVALID_ARG;
+    return cuda_status(launch_histogram(d_in, n, reinterpret_cast<unsigned long long *>(d_hist),
+                                        d_unit_hist, reinterpret_cast<cudaStream_t>(stream)));
 }
 
 huff_status_t huff_build_codebook(const uint64_t *d_hist, huff_codebook_t *d_cb, int32_t *d_status,
@@ -109,11 +127,27 @@ huff_status_t huff_encode(const uint8_t *d_in, uint64_t n, const huff_codebook_t
     if (!chunk_symbols_valid(chunk_symbols) || !d_cb || !d_out || !d_out_bytes || !d_ws ||
         !d_status || (n && !d_in) || (d_in && !aligned16(d_in)) || !aligned16(d_out) ||
         !aligned16(d_ws) || ws_bytes < encode_workspace_bytes(n) ||
-        n > (uint64_t)UINT32_MAX * 4096u)
+        n > (uint64_t)UINT32_MAX * kUnitSymbols)
         return HUFF_ERR_INVALID_ARG;
     return cuda_status(launch_encode(d_in, n, d_cb, chunk_symbols, d_out, out_cap,
                                      reinterpret_cast<unsigned long long *>(d_out_bytes), d_ws,
-                                     d_status, reinterpret_cast<cudaStream_t>(stream)));
+                                     nullptr, d_status, reinterpret_cast<cudaStream_t>(stream)));
+}
+
+huff_status_t huff_encode_units(const uint8_t *d_in, uint64_t n, const huff_codebook_t *d_cb,
+                                const uint16_t *d_unit_hist, uint32_t chunk_symbols,
+                                uint8_t *d_out, uint64_t out_cap, uint64_t *d_out_bytes,
+                                void *d_ws, uint64_t ws_bytes, int32_t *d_status,
+                                huff_stream_t stream)
+{
+    if (!chunk_symbols_valid(chunk_symbols) || !d_cb || !d_out || !d_out_bytes || !d_ws ||
+        !d_status || !d_unit_hist || !aligned16(d_unit_hist) || (n && !d_in) ||
+        (d_in && !aligned16(d_in)) || !aligned16(d_out) || !aligned16(d_ws) ||
+        ws_bytes < encode_workspace_bytes(n) || n > (uint64_t)UINT32_MAX * kUnitSymbols)
+        return HUFF_ERR_INVALID_ARG;
+    return cuda_status(launch_encode(d_in, n, d_cb, chunk_symbols, d_out, out_cap,
+                                     reinterpret_cast<unsigned long long *>(d_out_bytes), d_ws,
+                                     d_unit_hist, d_status, reinterpret_cast<cudaStream_t>(stream)));
 }
 
 huff_status_t huff_decode(const uint8_t *d_stream, uint64_t stream_bytes, uint8_t *d_out,
@@ -132,22 +166,25 @@ huff_status_t huff_compress(const uint8_t *d_in, uint64_t n, uint32_t chunk_symb
                             int32_t *d_status, huff_stream_t stream)
 {
     if (!chunk_symbols_valid(chunk_symbols) || !d_ws || !aligned16(d_ws) || !d_status ||
-        ws_bytes < huff_workspace_size(n, chunk_symbols))
+        !d_out || !d_out_bytes || (n && !d_in) || (d_in && !aligned16(d_in)) ||
+        !aligned16(d_out) || ws_bytes < huff_workspace_size(n, chunk_symbols) ||
+        n > (uint64_t)UINT32_MAX * kUnitSymbols)
         return HUFF_ERR_INVALID_ARG;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     uint8_t *ws = static_cast<uint8_t *>(d_ws);
-    uint64_t *hist = reinterpret_cast<uint64_t *>(ws + kWsHistOffset);
+    unsigned long long *hist = reinterpret_cast<unsigned long long *>(ws + kWsHistOffset);
     huff_codebook_t *cb = reinterpret_cast<huff_codebook_t *>(ws + kWsCodebookOffset);
+    uint16_t *unit_hist = reinterpret_cast<uint16_t *>(ws + kWsUnitHistOffset);
+    uint8_t *enc_ws = ws + kWsUnitHistOffset + unit_hist_bytes(n);
     if (cudaMemsetAsync(d_status, 0, sizeof(int32_t), s) != cudaSuccess)
         return HUFF_ERR_CUDA;
-    huff_status_t st = huff_histogram(d_in, n, hist, stream);
-    if (st != HUFF_OK)
-        return st;
-    st = huff_build_codebook(hist, cb, d_status, stream);
-    if (st != HUFF_OK)
-        return st;
-    return huff_encode(d_in, n, cb, chunk_symbols, d_out, out_cap, d_out_bytes,
-                       ws + kWsEncodeOffset, ws_bytes - kWsEncodeOffset, d_status, stream);
+    if (launch_histogram(d_in, n, hist, unit_hist, s) != cudaSuccess)
+        return HUFF_ERR_CUDA;
+    if (launch_build_codebook(hist, cb, d_status, s) != cudaSuccess)
+        return HUFF_ERR_CUDA;
+    return cuda_status(launch_encode(d_in, n, cb, chunk_symbols, d_out, out_cap,
+                                     reinterpret_cast<unsigned long long *>(d_out_bytes), enc_ws,
+                                     unit_hist, d_status, s));
 }
 
 }  // extern "C"

@@ -3,24 +3,240 @@
 // bytes [c*cs, c*cs + m)" (Section III-A).
 //
 // Every CTA validates the header and builds the canonical decode tables in
-// shared memory from the 256 stored lengths: a 2^11-entry lookup table for
-// codes of up to 11 bits (entry = byte | length << 8) and, per length, the
-// first code and the index of its first symbol for longer codes.  One thread
-// decodes one chunk from its stored bit offset with a 64-bit bit buffer fed
-// by aligned 32-bit loads, and writes 16 output bytes at a time.
+// shared memory from the 256 stored lengths:
+//  - a 2^12-entry lookup table; an entry holds up to two symbols whose codes
+//    both fit in the 12-bit window (sym0 | sym1 << 8 | len0 << 16 |
+//    total << 24 | count << 30), so text decodes ~1.8 symbols per lookup;
+//  - per length, the first canonical code and the index of its first symbol,
+//    for codes longer than 12 bits (searched by length).
+//
+// Parallelism inside a chunk comes from self-synchronisation (Huffman codes
+// resynchronise after a few codewords when decoding starts at an arbitrary
+// bit; Klein & Wiseman 2003, Weissenberger & Schmidt 2018).  A chunk's bit
+// range is cut into S sub-segments, S = 1..32 picked on the device from the
+// chunk count so that there are enough independent decoders; one thread per
+// sub-segment, S consecutive lanes per chunk:
+//  1. every sub-segment but the last counts codewords from its cut point up
+//     to the first codeword boundary at or past the next cut, remembering
+//     which of its first 64 bits started a codeword;
+//  2. sub-segment k's true entry point is where k-1 exits; if that bit is one
+//     of k's own early boundaries, k's path has already joined the true one
+//     and only its count is corrected, otherwise k re-counts from the entry
+//     point (a warp loop that settles in order, usually in one step);
+//  3. a segmented scan of the counts gives each sub-segment its output
+//     offset; the last one takes the rest of the chunk's symbols;
+//  4. each sub-segment decodes its symbols again on the true path, checking
+//     every code and the chunk's bit limit, and writes them through a small
+//     per-thread ring in shared memory as 16-byte stores.
+// Input words are read as 8-byte pairs kept three pairs ahead of use.  The
+// decoded codeword sequence is exactly the sequential one, so the stream
+// checks are those of a sequential decoder.
 #include "huff_internal.cuh"
 
 namespace huff {
 namespace {
 
 constexpr int kDecBlock = 128;
-constexpr int kLutBits = 11;
+constexpr int kLutBits = 12;
+constexpr int kLutSize = 1 << kLutBits;
+constexpr int kRingWords = 9;  // 32-byte ring + 1 pad word per thread
 
-__global__ void __launch_bounds__(kDecBlock)
-    k_decode(const uint8_t *__restrict__ stream, uint64_t bytes, uint8_t *__restrict__ out,
-             uint64_t cap, unsigned long long *d_n, int32_t *status)
+struct DecodeArgs {
+    const uint8_t *stream;
+    uint64_t bytes;
+    uint8_t *out;
+    uint64_t cap;
+    unsigned long long *d_n;
+    int32_t *status;
+    uint32_t min_chains;
+};
+
+struct Tables {
+    const uint32_t *lut;
+    const uint32_t *count;
+    const uint32_t *first;
+    const uint32_t *start;
+    const uint8_t *sorted;
+    uint32_t max_len;
+};
+
+// Codes longer than the table: canonical search by length on a 32-bit window.
+__device__ __forceinline__ bool long_code(const Tables &T, uint64_t buf, uint32_t &L, uint32_t &sym)
 {
-    __shared__ uint16_t lut[1 << kLutBits];
+    const uint32_t v = (uint32_t)(buf >> 32);
+    for (uint32_t l = kLutBits + 1; l <= T.max_len; ++l) {
+        const uint32_t cv = v >> (32 - l);
+        if (T.count[l] && cv - T.first[l] < T.count[l]) {
+            L = l;
+            sym = T.sorted[T.start[l] + cv - T.first[l]];
+            return true;
+        }
+    }
+    return false;
+}
+
+// Bit reader over the payload's u32 words.  Words come in blocks of four
+// (two 8-byte loads); the block after the current one is always in flight,
+// so a register is never read right after its load was issued, and an L2
+// prefetch runs 256 bytes ahead.  Words past the payload read as zero.
+struct Reader {
+    const uint2 *pairs;
+    uint64_t nwords;
+    uint64_t next_blk;
+    uint2 c0, c1, n0, n1;
+    uint32_t idx;  // next word of the current block
+    uint64_t buf;  // valid bits left-aligned
+    int have;
+
+    __device__ __forceinline__ void load_block(uint64_t b, uint2 &x0, uint2 &x1) const
+    {
+        const uint64_t w = 4 * b;
+        if (w + 4 <= nwords) {
+            x0 = pairs[2 * b];
+            x1 = pairs[2 * b + 1];
+        } else {
+            const uint32_t *words = reinterpret_cast<const uint32_t *>(pairs);
+            x0.x = w < nwords ? words[w] : 0u;
+            x0.y = w + 1 < nwords ? words[w + 1] : 0u;
+            x1.x = w + 2 < nwords ? words[w + 2] : 0u;
+            x1.y = 0u;
+        }
+    }
+    __device__ __forceinline__ uint32_t next_word()
+    {
+        const uint32_t w = idx == 0 ? c0.x : idx == 1 ? c0.y : idx == 2 ? c1.x : c1.y;
+        if (++idx == 4) {
+            idx = 0;
+            c0 = n0;
+            c1 = n1;
+            load_block(next_blk, n0, n1);
+            ++next_blk;
+            if ((next_blk & 7) == 0 && 4 * (next_blk + 16) < nwords)
+                asm volatile("prefetch.global.L2 [%0];" ::"l"(pairs + 2 * (next_blk + 16)));
+        }
+        return w;
+    }
+    __device__ __forceinline__ void init(const uint8_t *pay, uint64_t nw, uint64_t pos)
+    {
+        pairs = reinterpret_cast<const uint2 *>(pay);
+        nwords = nw;
+        const uint64_t wi = pos >> 5, b = wi >> 2;
+        load_block(b, c0, c1);
+        load_block(b + 1, n0, n1);
+        next_blk = b + 2;
+        idx = (uint32_t)(wi & 3);
+        buf = ((uint64_t)next_word() << 32) << (pos & 31);
+        have = 32 - (int)(pos & 31);
+    }
+    __device__ __forceinline__ void refill()
+    {
+        if (have <= 32) {
+            buf |= (uint64_t)next_word() << (32 - have);
+            have += 32;
+        }
+    }
+    __device__ __forceinline__ void consume(uint32_t L)
+    {
+        buf <<= L;
+        have -= (int)L;
+    }
+};
+
+// Count codewords from bit `pos` (relative to the chunk's first bit `cbase`)
+// until the first boundary at or past `stop`.  Bit i of bmap is set when a
+// codeword starts at pos0 + i (i < 64).  Invalid bits (possible off the true
+// path) count as 1-bit codewords.
+__device__ __forceinline__ void count_codes(const Tables &T, const uint8_t *pay, uint64_t nw,
+                                            uint64_t cbase, uint32_t pos, uint32_t stop,
+                                            uint32_t &n, uint32_t &e, uint64_t &bmap)
+{
+    const uint32_t pos0 = pos;
+    uint32_t cnt = 0;
+    bmap = 1;
+    if (pos < stop) {
+        Reader rd;
+        rd.init(pay, nw, cbase + pos);
+        while (pos < stop) {
+            rd.refill();
+            const uint32_t ent = T.lut[rd.buf >> (64 - kLutBits)];
+            uint32_t ns = ent >> 30, L = (ent >> 24) & 31u;
+            if (ns == 0) {
+                uint32_t sym;
+                if (!long_code(T, rd.buf, L, sym))
+                    L = 1;
+                ns = 1;
+            } else if (ns == 2) {
+                const uint32_t L0 = (ent >> 16) & 31u;
+                if (pos + L0 >= stop) {
+                    ns = 1;
+                    L = L0;
+                } else if (pos + L0 - pos0 < 64) {
+                    bmap |= 1ull << (pos + L0 - pos0);
+                }
+            }
+            pos += L;
+            if (pos - pos0 < 64)
+                bmap |= 1ull << (pos - pos0);
+            cnt += ns;
+            rd.consume(L);
+        }
+    }
+    n = cnt;
+    e = pos;
+}
+
+// Sub-segment [g, stop) was counted from g (cnt codewords, exit e, early
+// boundaries bmap).  Given its true entry point, walk the true path one
+// codeword at a time until it lands on one of the recorded boundaries: from
+// there both paths are the same codeword sequence, so only the codewords
+// before the meeting point change.  If they do not meet within the recorded
+// 64 bits, recount from the entry point.
+__device__ __forceinline__ void settle_segment(const Tables &T, const uint8_t *pay, uint64_t nw,
+                                               uint64_t cbase, uint32_t g, uint32_t stop,
+                                               uint32_t entry, uint64_t bmap, uint32_t cnt1,
+                                               uint32_t e1, uint32_t &cnt, uint32_t &e)
+{
+    uint32_t pos = entry, steps = 0;
+    Reader rd;
+    bool started = false;
+    for (;;) {
+        const uint32_t d = pos - g;
+        if (d < 64 && ((bmap >> d) & 1)) {  // met: same path from here on
+            cnt = steps + cnt1 - __popcll(bmap & ((1ull << d) - 1));
+            e = e1;
+            return;
+        }
+        if (pos >= stop) {  // left the sub-segment before meeting
+            cnt = steps;
+            e = pos;
+            return;
+        }
+        if (d >= 64)
+            break;
+        if (!started) {
+            rd.init(pay, nw, cbase + pos);
+            started = true;
+        }
+        rd.refill();
+        const uint32_t ent = T.lut[rd.buf >> (64 - kLutBits)];
+        uint32_t L = (ent >> 16) & 31u;  // first code only: every boundary matters
+        if ((ent >> 30) == 0) {
+            uint32_t sym;
+            if (!long_code(T, rd.buf, L, sym))
+                L = 1;
+        }
+        pos += L;
+        ++steps;
+        rd.consume(L);
+    }
+    uint64_t unused;
+    count_codes(T, pay, nw, cbase, entry, stop, cnt, e, unused);
+}
+
+__global__ void __launch_bounds__(kDecBlock) k_decode(DecodeArgs a)
+{
+    __shared__ uint32_t lut[kLutSize];
+    __shared__ uint32_t ring[kDecBlock * kRingWords];
     __shared__ uint8_t len_s[256];
     __shared__ uint8_t sorted[256];
     __shared__ uint32_t count[kMaxCodeLen + 1];
@@ -29,13 +245,14 @@ __global__ void __launch_bounds__(kDecBlock)
     __shared__ unsigned long long s_kraft;
     __shared__ int s_max, s_nsym, s_bad;
 
-    if (chain_failed(status))
+    if (chain_failed(a.status))
         return;
     const int tid = threadIdx.x;
     const bool reporter = blockIdx.x == 0 && tid == 0;
-    if (bytes < kHeaderBytes) {
+    const uint8_t *stream = a.stream;
+    if (a.bytes < kHeaderBytes) {
         if (reporter)
-            set_status(status, HUFF_ERR_CORRUPT_STREAM);
+            set_status(a.status, HUFF_ERR_CORRUPT_STREAM);
         return;
     }
     const uint64_t n = *reinterpret_cast<const uint64_t *>(stream + 256);
@@ -43,13 +260,13 @@ __global__ void __launch_bounds__(kDecBlock)
     const uint32_t max_field = *reinterpret_cast<const uint32_t *>(stream + 268);
     if (!chunk_symbols_valid(cs)) {
         if (reporter)
-            set_status(status, HUFF_ERR_CORRUPT_STREAM);
+            set_status(a.status, HUFF_ERR_CORRUPT_STREAM);
         return;
     }
     const uint64_t chunks = n / cs + (n % cs != 0);
-    if (chunks > (bytes - kHeaderBytes) / 8) {
+    if (chunks > (a.bytes - kHeaderBytes) / 8) {
         if (reporter)
-            set_status(status, HUFF_ERR_CORRUPT_STREAM);
+            set_status(a.status, HUFF_ERR_CORRUPT_STREAM);
         return;
     }
 
@@ -78,18 +295,19 @@ __global__ void __launch_bounds__(kDecBlock)
     __syncthreads();
     const uint32_t max_len = (uint32_t)s_max;
     const int nsym = s_nsym;
-    bool bad = s_bad || max_len != max_field || (n > 0 && nsym == 0) ||
-               (nsym == 1 && max_len != 1) || (nsym >= 2 && s_kraft != (1ull << 32));
-    if (bad) {
+    const bool bad_header = s_bad || max_len != max_field || (n > 0 && nsym == 0) ||
+                            (nsym == 1 && max_len != 1) ||
+                            (nsym >= 2 && s_kraft != (1ull << 32));
+    if (bad_header) {
         if (reporter)
-            set_status(status, HUFF_ERR_CORRUPT_STREAM);
+            set_status(a.status, HUFF_ERR_CORRUPT_STREAM);
         return;
     }
     if (reporter)
-        *d_n = n;
-    if (n > cap) {
+        *a.d_n = n;
+    if (n > a.cap) {
         if (reporter)
-            set_status(status, HUFF_ERR_CAPACITY);
+            set_status(a.status, HUFF_ERR_CAPACITY);
         return;
     }
     if (n == 0)
@@ -116,86 +334,186 @@ __global__ void __launch_bounds__(kDecBlock)
         }
     }
     __syncthreads();
+    // pass 1: the first code of every 12-bit window
     const uint32_t lut_len = max_len < (uint32_t)kLutBits ? max_len : (uint32_t)kLutBits;
-    for (int v = tid; v < (1 << kLutBits); v += kDecBlock) {
-        uint16_t ent = 0;
+    for (int v = tid; v < kLutSize; v += kDecBlock) {
+        uint32_t ent = 0;
         for (uint32_t L = 1; L <= lut_len; ++L) {
             const uint32_t c = (uint32_t)v >> (kLutBits - L);
             if (count[L] && c - first[L] < count[L]) {
-                ent = (uint16_t)(sorted[start[L] + c - first[L]] | (L << 8));
+                ent = sorted[start[L] + c - first[L]] | (L << 16) | (L << 24) | (1u << 30);
                 break;
             }
         }
         lut[v] = ent;
     }
     __syncthreads();
+    // pass 2: append a second code when it fits in the rest of the window
+    uint32_t ent2[kLutSize / kDecBlock];
+#pragma unroll
+    for (int i = 0; i < kLutSize / kDecBlock; ++i) {
+        const int v = tid + i * kDecBlock;
+        uint32_t ent = lut[v];
+        const uint32_t L0 = (ent >> 16) & 31u;
+        if (ent && L0 < (uint32_t)kLutBits) {
+            const uint32_t nxt = lut[((uint32_t)v << L0) & (kLutSize - 1)];
+            const uint32_t L1 = (nxt >> 16) & 31u;
+            if (nxt && L0 + L1 <= (uint32_t)kLutBits)
+                ent = (ent & 0xffu) | ((nxt & 0xffu) << 8) | (L0 << 16) | ((L0 + L1) << 24) |
+                      (2u << 30);
+        }
+        ent2[i] = ent;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < kLutSize / kDecBlock; ++i)
+        lut[tid + i * kDecBlock] = ent2[i];
+    __syncthreads();
 
-    const uint64_t pay_words = (bytes - kHeaderBytes - 8 * chunks) / 4;
+    Tables T;
+    T.lut = lut;
+    T.count = count;
+    T.first = first;
+    T.start = start;
+    T.sorted = sorted;
+    T.max_len = max_len;
+
+    const uint64_t pay_words = (a.bytes - kHeaderBytes - 8 * chunks) / 4;
     const uint64_t pbits = 32 * pay_words;
     const uint64_t *offs = reinterpret_cast<const uint64_t *>(stream + kHeaderBytes);
-    const uint32_t *pay = reinterpret_cast<const uint32_t *>(stream + kHeaderBytes + 8 * chunks);
+    const uint8_t *pay = stream + kHeaderBytes + 8 * chunks;
 
-    for (uint64_t c = (uint64_t)blockIdx.x * kDecBlock + tid; c < chunks;
-         c += (uint64_t)gridDim.x * kDecBlock) {
-        uint64_t pos = offs[c];
-        const uint64_t limit = c + 1 < chunks ? offs[c + 1] : pbits;
-        if ((c == 0 && pos != 0) || pos > limit) {
-            set_status(status, HUFF_ERR_CORRUPT_STREAM);
-            return;
-        }
-        const uint64_t obase = c * cs;
-        const uint64_t m = n - obase < cs ? n - obase : cs;
+    // sub-segments per chunk
+    uint32_t S = 1;
+    while (S < 32 && chunks * S < a.min_chains)
+        S <<= 1;
+    const uint32_t G = 32 / S;  // chunks per warp
+    const uint64_t tasks = (chunks + G - 1) / G;
+    const int lane = tid & 31;
+    const uint32_t k = (uint32_t)lane & (S - 1);
+    const uint32_t grp = (uint32_t)lane / S;
+    uint8_t *ringb = reinterpret_cast<uint8_t *>(ring + tid * kRingWords);
+    const uint32_t *ringw = ring + tid * kRingWords;
+    const uint64_t nwarps = (uint64_t)gridDim.x * (kDecBlock / 32);
 
-        // bit buffer: valid bits left-aligned in buf, `have` of them
-        uint64_t wi = pos >> 5;
-        uint64_t buf = (uint64_t)(wi < pay_words ? pay[wi] : 0u) << 32;
-        buf <<= (pos & 31);
-        int have = 32 - (int)(pos & 31);
-        ++wi;
-        bool ok = true;
-
-        auto next_symbol = [&]() -> uint32_t {
-            if (have <= 32) {
-                buf |= (uint64_t)(wi < pay_words ? pay[wi] : 0u) << (32 - have);
-                have += 32;
-                ++wi;
+    for (uint64_t task = ((uint64_t)blockIdx.x * kDecBlock + tid) >> 5; task < tasks;
+         task += nwarps) {
+        const uint64_t c = task * G + grp;
+        const bool valid = c < chunks;
+        bool bad = false;
+        uint64_t cbase = 0;  // chunk's first bit; positions below are relative to it
+        uint32_t lim = 0, m = 0, g = 0, stop = 0;
+        if (valid) {
+            cbase = offs[c];
+            const bool lastc = c + 1 == chunks;
+            const uint64_t limit = lastc ? pbits : offs[c + 1];
+            m = (uint32_t)(n - c * cs < cs ? n - c * cs : cs);
+            // a chunk spans at most 32 bits per symbol; beyond that it is corrupt
+            bad = (c == 0 && cbase != 0) || cbase > limit ||
+                  (!lastc && limit - cbase > 32ull * m);
+            if (!bad) {
+                const uint64_t span = limit - cbase < 32ull * m ? limit - cbase : 32ull * m;
+                lim = (uint32_t)(limit - cbase < 32ull * m ? limit - cbase : 32ull * m + 32);
+                g = (uint32_t)(span * k / S);
+                stop = (uint32_t)(span * (k + 1) / S);
             }
-            const uint32_t ent = lut[buf >> (64 - kLutBits)];
-            uint32_t L = ent >> 8, sym = ent & 0xffu;
-            if (L == 0) {  // longer than the table: canonical search by length
-                const uint32_t v = (uint32_t)(buf >> 32);
-                for (L = lut_len + 1; L <= max_len; ++L) {
-                    const uint32_t cv = v >> (32 - L);
-                    if (count[L] && cv - first[L] < count[L]) {
-                        sym = sorted[start[L] + cv - first[L]];
+        }
+        const bool work = valid && !bad;
+
+        // 1. count each sub-segment but the last from its cut point
+        uint32_t cnt1 = 0, e1 = g;
+        uint64_t bmap = 1;
+        if (work && k + 1 < S)
+            count_codes(T, pay, pay_words, cbase, g, stop, cnt1, e1, bmap);
+        uint32_t cnt = cnt1, e = e1;
+        // 2. settle the entry points: all at once on the exits just counted,
+        //    then again wherever an exit moved
+        uint32_t entry = g;  // lane 0 already starts on the true path (g == 0)
+        uint32_t used = g;
+        bool first = true;
+        for (;;) {
+            const uint32_t pe = __shfl_up_sync(0xffffffffu, e, 1, S);
+            const bool redo = work && k > 0 && (first || pe != used);
+            if (!__any_sync(0xffffffffu, redo))
+                break;
+            if (redo) {
+                used = pe;
+                entry = pe;
+                if (k + 1 < S)
+                    settle_segment(T, pay, pay_words, cbase, g, stop, entry, bmap, cnt1, e1, cnt,
+                                   e);
+            }
+            first = false;
+        }
+        // 3. output offsets: segmented exclusive scan of the counts
+        const uint32_t own = (work && k + 1 < S) ? cnt : 0u;
+        uint32_t x = own;
+        for (uint32_t d = 1; d < S; d <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, x, d, S);
+            if (k >= d)
+                x += y;
+        }
+        const uint32_t O = x - own;
+        uint32_t todo = 0;
+        if (work && O < m)
+            todo = (k + 1 == S) ? m - O : (own < m - O ? own : m - O);
+        const bool final_seg = work && O < m && O + todo == m;
+
+        // 4. decode on the true path and write the bytes
+        if (todo) {
+            Reader rd;
+            rd.init(pay, pay_words, cbase + entry);
+            uint32_t pos = entry;
+            const uint64_t ob = c * cs + O, oend = ob + todo;
+            uint64_t o = ob;
+            while (o < oend) {
+                rd.refill();
+                const uint32_t ent = lut[rd.buf >> (64 - kLutBits)];
+                uint32_t ns = ent >> 30, L = (ent >> 24) & 31u, sy = ent & 0xffffu;
+                if (ns == 0) {
+                    uint32_t sym;
+                    if (!long_code(T, rd.buf, L, sym)) {
+                        bad = true;
                         break;
                     }
+                    ns = 1;
+                    sy = sym;
+                } else if (ns == 2 && (oend - o < 2 || pos + L > lim)) {
+                    ns = 1;
+                    L = (ent >> 16) & 31u;
                 }
-                if (L > max_len) {
-                    ok = false;
-                    L = 1;
+                if (pos + L > lim) {
+                    bad = true;
+                    break;
                 }
+                ringb[o & 31] = (uint8_t)sy;
+                if (ns == 2)
+                    ringb[(o + 1) & 31] = (uint8_t)(sy >> 8);
+                const uint64_t o2 = o + ns;
+                if ((o2 ^ o) & ~15ull) {  // a 16-byte half of the ring is complete
+                    const uint64_t hs = o & ~15ull;
+                    const uint32_t *h = ringw + ((hs & 16) >> 2);
+                    if (hs >= ob)
+                        *reinterpret_cast<uint4 *>(a.out + hs) = make_uint4(h[0], h[1], h[2], h[3]);
+                    else
+                        for (uint64_t j = ob; j < hs + 16; ++j)
+                            a.out[j] = ringb[j & 31];
+                }
+                o = o2;
+                pos += L;
+                rd.consume(L);
             }
-            if (pos + L > limit)
-                ok = false;
-            pos += L;
-            buf <<= L;
-            have -= (int)L;
-            return sym;
-        };
-
-        uint64_t i = 0;
-        for (; i + 16 <= m && ok; i += 16) {
-            uint32_t q[4] = {0u, 0u, 0u, 0u};
-#pragma unroll
-            for (int k = 0; k < 16; ++k)
-                q[k >> 2] |= next_symbol() << (8 * (k & 3));
-            *reinterpret_cast<uint4 *>(out + obase + i) = make_uint4(q[0], q[1], q[2], q[3]);
+            if (!bad) {
+                const uint64_t hs = o & ~15ull;
+                for (uint64_t j = hs > ob ? hs : ob; j < o; ++j)
+                    a.out[j] = ringb[j & 31];
+                if (final_seg && c + 1 < chunks && pos != lim)
+                    bad = true;
+            }
         }
-        for (; i < m && ok; ++i)
-            out[obase + i] = (uint8_t)next_symbol();
-        if (!ok || (c + 1 < chunks && pos != limit)) {
-            set_status(status, HUFF_ERR_CORRUPT_STREAM);
+        if (__any_sync(0xffffffffu, bad)) {
+            if (lane == 0)
+                set_status(a.status, HUFF_ERR_CORRUPT_STREAM);
             return;
         }
     }
@@ -215,15 +533,24 @@ cudaError_t launch_decode(const uint8_t *d_stream, uint64_t bytes, uint8_t *d_ou
         if (per_sm < 1)
             per_sm = 1;
     }
+    const int sms = device_sm_count();
     // the chunk count is only known on the device; bound it by the table size
     const uint64_t max_chunks = bytes > kHeaderBytes ? (bytes - kHeaderBytes) / 8 : 0;
-    uint64_t grid = (max_chunks + kDecBlock - 1) / kDecBlock;
-    const uint64_t cap = (uint64_t)device_sm_count() * per_sm;
+    uint64_t grid = (max_chunks + (kDecBlock / 32) - 1) / (kDecBlock / 32);
+    const uint64_t cap = (uint64_t)sms * per_sm;
     if (grid > cap)
         grid = cap;
     if (grid < 1)
         grid = 1;
-    k_decode<<<(unsigned)grid, kDecBlock, 0, s>>>(d_stream, bytes, d_out, out_cap, d_n, d_status);
+    DecodeArgs a;
+    a.stream = d_stream;
+    a.bytes = bytes;
+    a.out = d_out;
+    a.cap = out_cap;
+    a.d_n = d_n;
+    a.status = d_status;
+    a.min_chains = (uint32_t)sms * 256u;
+    k_decode<<<(unsigned)grid, kDecBlock, 0, s>>>(a);
     return cudaGetLastError();
 }
 

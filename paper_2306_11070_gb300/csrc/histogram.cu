@@ -5,16 +5,22 @@
 // counters in shared memory, laid out [bin][lane], and lane l only touches
 // column l, so the 32 shared-memory atomics of one warp instruction always
 // fall in 32 different banks, whatever the data (a single repeated byte
-// included).  Loads are 16-byte, streaming (no L1 allocation), four in flight
-// per thread.  At the end every CTA folds its 32 columns and adds one u64 per
-// non-zero bin to the global histogram.
+// included).  Persistent CTAs take 16 KiB units round robin; each thread
+// loads its two 16-byte pieces of the next unit before counting the current
+// one.
+//
+// Optionally the kernel also writes every unit's own histogram (u16[256],
+// 512 bytes per 16 KiB): the encoder turns these into the bit offset of each
+// unit with a dot product against the code lengths, so it never has to wait
+// on another CTA.  A unit's counts are the difference of two folds of the
+// running columns, so the columns are never cleared.
 #include "huff_internal.cuh"
 
 namespace huff {
 namespace {
 
 constexpr int kHistBlock = 512;
-constexpr int kHistUnroll = 4;
+constexpr int kVecPerThread = kUnitSymbols / 16 / kHistBlock;  // 2
 
 __device__ __forceinline__ void count_word(uint32_t *col, uint32_t w)
 {
@@ -32,53 +38,77 @@ __device__ __forceinline__ void count16(uint32_t *col, uint4 v)
     count_word(col, v.w);
 }
 
+// Sum of bin (tid >> 1) over the 16 columns of half (tid & 1), combined over
+// the thread pair; the rotation keeps one warp's reads in distinct banks.
+__device__ __forceinline__ uint32_t fold_bin(const uint32_t *cnt, int tid)
+{
+    const int b = tid >> 1, h = (tid & 1) << 4;
+    uint32_t s = 0;
+#pragma unroll
+    for (int l = 0; l < 16; ++l)
+        s += cnt[(b << 5) + ((h + l + b) & 31)];
+    return s + __shfl_xor_sync(0xffffffffu, s, 1);
+}
+
 __global__ void __launch_bounds__(kHistBlock)
-    k_histogram(const uint8_t *__restrict__ in, uint64_t n, unsigned long long *__restrict__ hist)
+    k_histogram(const uint8_t *__restrict__ in, uint64_t n, unsigned long long *__restrict__ hist,
+                uint16_t *__restrict__ unit_hist)
 {
     __shared__ uint32_t cnt[256 * 32];
-    const int lane = threadIdx.x & 31;
-    for (int i = threadIdx.x; i < 256 * 32; i += kHistBlock)
+    const int tid = threadIdx.x, lane = tid & 31;
+    for (int i = tid; i < 256 * 32; i += kHistBlock)
         cnt[i] = 0;
-    __syncthreads();
-
     uint32_t *col = cnt + lane;
+    const uint64_t units = (n + kUnitSymbols - 1) / kUnitSymbols;
     const uint64_t nvec = n >> 4;
-    const uint64_t stride = (uint64_t)gridDim.x * kHistBlock;
-    uint64_t i = (uint64_t)blockIdx.x * kHistBlock + threadIdx.x;
     const uint4 *v = reinterpret_cast<const uint4 *>(in);
-    for (; i + (kHistUnroll - 1) * stride < nvec; i += kHistUnroll * stride) {
-        uint4 a[kHistUnroll];
+    uint32_t prev = 0;  // fold of this thread's bin at the previous unit end
+    uint4 a[kVecPerThread];
+    auto load_unit = [&](uint64_t uu) {
 #pragma unroll
-        for (int u = 0; u < kHistUnroll; ++u)
-            a[u] = ld_stream16(v + i + u * stride);
-#pragma unroll
-        for (int u = 0; u < kHistUnroll; ++u)
-            count16(col, a[u]);
-    }
-    for (; i < nvec; i += stride)
-        count16(col, ld_stream16(v + i));
-    // ragged tail (< 16 bytes)
-    const uint64_t g = (uint64_t)blockIdx.x * kHistBlock + threadIdx.x;
-    if (g < (n & 15u))
-        atomicAdd(col + ((uint32_t)in[(nvec << 4) + g] << 5), 1u);
+        for (int j = 0; j < kVecPerThread; ++j) {
+            const uint64_t q = uu * (kUnitSymbols / 16) + j * kHistBlock + tid;
+            a[j] = (uu < units && q < nvec) ? ld_stream16(v + q) : make_uint4(0, 0, 0, 0);
+        }
+    };
+    uint64_t u = blockIdx.x;
+    load_unit(u);
     __syncthreads();
-
-    // fold the 32 columns of each bin; the rotation keeps the reads of one
-    // warp in 32 different banks
-    for (int b = threadIdx.x; b < 256; b += kHistBlock) {
-        uint32_t s = 0;
-#pragma unroll 8
-        for (int l = 0; l < 32; ++l)
-            s += cnt[(b << 5) + ((l + b) & 31)];
-        if (s)
-            atomicAdd(hist + b, (unsigned long long)s);
+    for (; u < units; u += gridDim.x) {
+        uint4 cur[kVecPerThread];
+#pragma unroll
+        for (int j = 0; j < kVecPerThread; ++j)
+            cur[j] = a[j];
+        load_unit(u + gridDim.x);  // in flight while this unit is counted
+#pragma unroll
+        for (int j = 0; j < kVecPerThread; ++j) {
+            const uint64_t q = u * (kUnitSymbols / 16) + j * kHistBlock + tid;
+            if (q < nvec)
+                count16(col, cur[j]);
+        }
+        if (u == units - 1) {  // ragged tail (< 16 bytes) belongs to the last unit
+            if (tid < (int)(n & 15u))
+                atomicAdd(col + ((uint32_t)in[(nvec << 4) + tid] << 5), 1u);
+        }
+        if (unit_hist) {
+            __syncthreads();  // all counts of unit u are in
+            const uint32_t s = fold_bin(cnt, tid);
+            if ((tid & 1) == 0)
+                unit_hist[u * 256 + (tid >> 1)] = (uint16_t)(s - prev);
+            prev = s;
+            __syncthreads();  // folds read before the next unit's counts
+        }
     }
+    __syncthreads();
+    const uint32_t s = fold_bin(cnt, tid);
+    if ((tid & 1) == 0 && s)
+        atomicAdd(hist + (tid >> 1), (unsigned long long)s);
 }
 
 }  // namespace
 
 cudaError_t launch_histogram(const uint8_t *d_in, uint64_t n, unsigned long long *d_hist,
-                             cudaStream_t s)
+                             uint16_t *d_unit_hist, cudaStream_t s)
 {
     cudaError_t err = cudaMemsetAsync(d_hist, 0, 256 * sizeof(unsigned long long), s);
     if (err != cudaSuccess || n == 0)
@@ -91,13 +121,10 @@ cudaError_t launch_histogram(const uint8_t *d_in, uint64_t n, unsigned long long
         if (per_sm < 1)
             per_sm = 1;
     }
-    const uint64_t nvec = n >> 4;
-    uint64_t want = (nvec + (uint64_t)kHistBlock * kHistUnroll - 1) / ((uint64_t)kHistBlock * kHistUnroll);
-    uint64_t cap = (uint64_t)device_sm_count() * per_sm;
-    uint64_t grid = want < cap ? want : cap;
-    if (grid < 1)
-        grid = 1;
-    k_histogram<<<(unsigned)grid, kHistBlock, 0, s>>>(d_in, n, d_hist);
+    const uint64_t units = (n + kUnitSymbols - 1) / kUnitSymbols;
+    const uint64_t cap = (uint64_t)device_sm_count() * per_sm;
+    const uint64_t grid = units < cap ? units : cap;
+    k_histogram<<<(unsigned)grid, kHistBlock, 0, s>>>(d_in, n, d_hist, d_unit_hist);
     return cudaGetLastError();
 }
 

@@ -51,13 +51,70 @@ __device__ __forceinline__ void st_volatile_u64(unsigned long long *p, uint64_t 
                  : "memory");
 }
 
-// ---- stream header access (device; GB300 is little-endian) ----------------
-struct StreamHeader {
-    uint64_t n;
-    uint32_t chunk_symbols;
-    uint32_t max_len;
-};
+// ---- shared-memory barriers and bulk (TMA) copies -------------------------
+__device__ __forceinline__ uint32_t smem_u32(const void *p)
+{
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
 
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count)
+                 : "memory");
+}
+
+__device__ __forceinline__ void fence_mbar_init()
+{
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void fence_proxy_async_smem()
+{
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+// One arrival that also announces `bytes` of asynchronous transfer.
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity)
+{
+    uint32_t done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(done)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return done != 0;
+}
+
+// Bounded wait for the phase with the given parity; false on timeout.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity)
+{
+    for (uint32_t spin = 0; spin < kSpinLimit; ++spin)
+        if (mbar_try_wait(bar, parity))
+            return true;
+    return false;
+}
+
+// 1-D bulk copy global -> shared through the TMA unit; completion is counted
+// on `bar`.  Both addresses 16-byte aligned, bytes a multiple of 16.
+__device__ __forceinline__ void tma_load_1d(void *dst, const void *src, uint32_t bytes, uint64_t *bar)
+{
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
+            "r"(smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+
+// ---- stream header checks --------------------------------------------------
 __host__ __device__ __forceinline__ bool chunk_symbols_valid(uint32_t cs)
 {
     return cs >= HUFF_MIN_CHUNK_SYMBOLS && cs <= HUFF_MAX_CHUNK_SYMBOLS && (cs % 16u) == 0;
@@ -75,14 +132,22 @@ int device_sm_count();
 
 // Kernel launchers (one per translation unit); each returns a cudaError_t.
 namespace huff {
+
+// Encoder unit: the granularity of precomputed bit offsets (and of the
+// optional per-unit histograms).  16 KiB; u16 counts cannot overflow.
+constexpr uint32_t kUnitSymbols = 16384;
+
 cudaError_t launch_histogram(const uint8_t *d_in, uint64_t n, unsigned long long *d_hist,
-                             cudaStream_t s);
+                             uint16_t *d_unit_hist, cudaStream_t s);
 cudaError_t launch_build_codebook(const unsigned long long *d_hist, huff_codebook_t *d_cb,
                                   int32_t *d_status, cudaStream_t s);
+cudaError_t launch_unit_offsets(const uint8_t *d_in, uint64_t n, const uint16_t *d_unit_hist,
+                                const huff_codebook_t *d_cb, uint32_t *d_unit_bits,
+                                unsigned long long *d_unit_off, int32_t *d_status, cudaStream_t s);
 cudaError_t launch_encode(const uint8_t *d_in, uint64_t n, const huff_codebook_t *d_cb,
                           uint32_t cs, uint8_t *d_out, uint64_t out_cap,
-                          unsigned long long *d_out_bytes, void *d_ws, int32_t *d_status,
-                          cudaStream_t s);
+                          unsigned long long *d_out_bytes, void *d_ws,
+                          const uint16_t *d_unit_hist, int32_t *d_status, cudaStream_t s);
 cudaError_t launch_decode(const uint8_t *d_stream, uint64_t bytes, uint8_t *d_out,
                           uint64_t out_cap, unsigned long long *d_n, int32_t *d_status,
                           cudaStream_t s);
