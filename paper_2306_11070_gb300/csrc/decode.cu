@@ -26,9 +26,15 @@
 //  3. a segmented scan of the counts gives each sub-segment its output
 //     offset; the last one takes the rest of the chunk's symbols;
 //  4. each sub-segment decodes its symbols again on the true path, checking
-//     every code and the chunk's bit limit, and writes them through a small
-//     per-thread ring in shared memory as 16-byte stores.
-// Input words are read as 8-byte pairs kept three pairs ahead of use.  The
+//     every code and the chunk's bit limit.
+// Counting (1) and decoding (4) run in windows of 8 lookups with no per-lane
+// branching inside a window (only predication), so the 32 independent bit
+// streams of a warp stay converged.  Between windows each lane tops up a
+// 32-word input ring in shared memory with cp.async (4-byte copies, laid out
+// [word][lane] so a warp's reads and writes never share a bank) and flushes
+// a completed 16-byte half of its 32-byte output ring (same layout) with one
+// 16-byte global store.  The next input word is always preloaded, so the
+// shared-memory latency stays off the per-codeword dependency chain.  The
 // decoded codeword sequence is exactly the sequential one, so the stream
 // checks are those of a sequential decoder.
 #include "huff_internal.cuh"
@@ -39,7 +45,9 @@ namespace {
 constexpr int kDecBlock = 128;
 constexpr int kLutBits = 12;
 constexpr int kLutSize = 1 << kLutBits;
-constexpr int kRingWords = 9;  // 32-byte ring + 1 pad word per thread
+constexpr int kInRing = 32;   // input ring: words per lane
+constexpr int kOutRing = 8;   // output ring: 32 bytes per lane
+constexpr int kWindow = 8;    // lookups between ring maintenance
 
 struct DecodeArgs {
     const uint8_t *stream;
@@ -133,6 +141,90 @@ struct Reader {
         if (have <= 32) {
             buf |= (uint64_t)next_word() << (32 - have);
             have += 32;
+        }
+    }
+    __device__ __forceinline__ void consume(uint32_t L)
+    {
+        buf <<= L;
+        have -= (int)L;
+    }
+};
+
+__device__ __forceinline__ void cp_async4(uint32_t *dst, const uint32_t *src, bool valid)
+{
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(smem_u32(dst)), "l"(src),
+                 "r"(valid ? 4 : 0)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait()
+{
+    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+// Bit stream of one lane fed through its column of the warp's input ring
+// (word slot w of lane l at ring[w * 32 + l]).  Word indices are relative to
+// w0, the payload word that holds the chunk's first bit.  Invariants: after
+// every top-up at least 25 words are requested beyond the next one to read,
+// groups are 4 words, and the two most recent groups may still be in flight,
+// so the >= 9 words a window can touch have landed.
+struct RingStream {
+    uint32_t *col;          // this lane's column
+    const uint32_t *words;  // payload
+    uint64_t nwords;
+    uint64_t w0;
+    uint32_t widx;  // next word to move into buf
+    uint32_t fidx;  // next word to request
+    uint32_t nxt;   // word widx, preloaded
+    uint64_t buf;   // valid bits left-aligned
+    int have;
+
+    __device__ __forceinline__ void fetch4()
+    {
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const uint64_t aw = w0 + fidx + j;
+            const bool ok = aw < nwords;
+            cp_async4(col + ((fidx + j) & (kInRing - 1)) * 32, words + (ok ? aw : 0), ok);
+        }
+        fidx += 4;
+        cp_async_commit();
+    }
+    __device__ __forceinline__ void top_up()
+    {
+        if (fidx - widx <= kInRing - 8)
+            fetch4();
+        if (fidx - widx <= kInRing - 8)
+            fetch4();
+    }
+    // start at bit `pbit` counted from the first bit of word w0
+    __device__ __forceinline__ void init(uint32_t *column, const uint32_t *pay, uint64_t nw,
+                                         uint64_t word0, uint32_t pbit)
+    {
+        col = column;
+        words = pay;
+        nwords = nw;
+        w0 = word0;
+        widx = pbit >> 5;
+        fidx = widx;
+#pragma unroll
+        for (int r = 0; r < kInRing / 4; ++r)
+            fetch4();
+        cp_async_wait<0>();
+        const uint32_t first = col[(widx & (kInRing - 1)) * 32];
+        ++widx;
+        buf = ((uint64_t)first << 32) << (pbit & 31);
+        have = 32 - (int)(pbit & 31);
+        nxt = col[(widx & (kInRing - 1)) * 32];
+    }
+    __device__ __forceinline__ void refill()
+    {
+        if (have <= 32) {
+            buf |= (uint64_t)nxt << (32 - have);
+            have += 32;
+            ++widx;
+            nxt = col[(widx & (kInRing - 1)) * 32];
         }
     }
     __device__ __forceinline__ void consume(uint32_t L)
@@ -236,7 +328,8 @@ __device__ __forceinline__ void settle_segment(const Tables &T, const uint8_t *p
 __global__ void __launch_bounds__(kDecBlock) k_decode(DecodeArgs a)
 {
     __shared__ uint32_t lut[kLutSize];
-    __shared__ uint32_t ring[kDecBlock * kRingWords];
+    __shared__ uint32_t in_ring[(kDecBlock / 32) * kInRing * 32];
+    __shared__ uint32_t out_ring[(kDecBlock / 32) * kOutRing * 32];
     __shared__ uint8_t len_s[256];
     __shared__ uint8_t sorted[256];
     __shared__ uint32_t count[kMaxCodeLen + 1];
@@ -392,8 +485,10 @@ __global__ void __launch_bounds__(kDecBlock) k_decode(DecodeArgs a)
     const int lane = tid & 31;
     const uint32_t k = (uint32_t)lane & (S - 1);
     const uint32_t grp = (uint32_t)lane / S;
-    uint8_t *ringb = reinterpret_cast<uint8_t *>(ring + tid * kRingWords);
-    const uint32_t *ringw = ring + tid * kRingWords;
+    const int wib = tid >> 5;  // warp in block
+    uint32_t *in_col = in_ring + wib * kInRing * 32 + lane;
+    uint32_t *out_col = out_ring + wib * kOutRing * 32 + lane;
+    uint8_t *out_colb = reinterpret_cast<uint8_t *>(out_col);
     const uint64_t nwarps = (uint64_t)gridDim.x * (kDecBlock / 32);
 
     for (uint64_t task = ((uint64_t)blockIdx.x * kDecBlock + tid) >> 5; task < tasks;
@@ -423,8 +518,49 @@ __global__ void __launch_bounds__(kDecBlock) k_decode(DecodeArgs a)
         // 1. count each sub-segment but the last from its cut point
         uint32_t cnt1 = 0, e1 = g;
         uint64_t bmap = 1;
-        if (work && k + 1 < S)
-            count_codes(T, pay, pay_words, cbase, g, stop, cnt1, e1, bmap);
+        if (S > 1) {  // uniform: every lane of the warp takes this branch
+            RingStream rs;
+            bool act = work && k + 1 < S && g < stop;
+            if (act)
+                rs.init(in_col, reinterpret_cast<const uint32_t *>(pay), pay_words, cbase >> 5,
+                        (uint32_t)(cbase & 31) + g);
+            uint32_t pos = g;
+            while (__any_sync(0xffffffffu, act)) {
+#pragma unroll
+                for (int j = 0; j < kWindow; ++j) {
+                    if (act) {
+                        rs.refill();
+                        const uint32_t ent = lut[rs.buf >> (64 - kLutBits)];
+                        uint32_t ns = ent >> 30, L = (ent >> 24) & 31u;
+                        if (ns == 0) {
+                            uint32_t sym;
+                            if (!long_code(T, rs.buf, L, sym))
+                                L = 1;
+                            ns = 1;
+                        } else if (ns == 2) {
+                            const uint32_t L0 = (ent >> 16) & 31u;
+                            if (pos + L0 >= stop) {
+                                ns = 1;
+                                L = L0;
+                            } else if (pos + L0 - g < 64) {
+                                bmap |= 1ull << (pos + L0 - g);
+                            }
+                        }
+                        pos += L;
+                        if (pos - g < 64)
+                            bmap |= 1ull << (pos - g);
+                        cnt1 += ns;
+                        rs.consume(L);
+                        act = pos < stop;
+                    }
+                }
+                if (act)
+                    rs.top_up();
+                cp_async_wait<2>();
+            }
+            cp_async_wait<0>();  // the ring is reused below
+            e1 = pos;
+        }
         uint32_t cnt = cnt1, e = e1;
         // 2. settle the entry points: all at once on the exits just counted,
         //    then again wherever an exit moved
@@ -460,54 +596,68 @@ __global__ void __launch_bounds__(kDecBlock) k_decode(DecodeArgs a)
         const bool final_seg = work && O < m && O + todo == m;
 
         // 4. decode on the true path and write the bytes
-        if (todo) {
-            Reader rd;
-            rd.init(pay, pay_words, cbase + entry);
-            uint32_t pos = entry;
-            const uint64_t ob = c * cs + O, oend = ob + todo;
-            uint64_t o = ob;
-            while (o < oend) {
-                rd.refill();
-                const uint32_t ent = lut[rd.buf >> (64 - kLutBits)];
-                uint32_t ns = ent >> 30, L = (ent >> 24) & 31u, sy = ent & 0xffffu;
-                if (ns == 0) {
-                    uint32_t sym;
-                    if (!long_code(T, rd.buf, L, sym)) {
-                        bad = true;
-                        break;
+        {
+            RingStream rs;
+            bool act = todo > 0;
+            uint8_t *const ob = a.out + c * cs;  // chunk output, 16-byte aligned
+            const uint32_t qend = O + todo;
+            uint32_t pos = entry, q = O, fl = O;  // q: next byte, fl: first unflushed byte
+            if (act)
+                rs.init(in_col, reinterpret_cast<const uint32_t *>(pay), pay_words, cbase >> 5,
+                        (uint32_t)(cbase & 31) + entry);
+            while (__any_sync(0xffffffffu, act)) {
+#pragma unroll
+                for (int j = 0; j < kWindow; ++j) {
+                    if (act) {
+                        rs.refill();
+                        const uint32_t ent = lut[rs.buf >> (64 - kLutBits)];
+                        uint32_t ns = ent >> 30, L = (ent >> 24) & 31u, sy = ent;
+                        if (ns == 0) {
+                            uint32_t sym = 0;
+                            if (!long_code(T, rs.buf, L, sym)) {
+                                bad = true;
+                                L = 0;
+                            }
+                            ns = 1;
+                            sy = sym;
+                        } else if (ns == 2 && (qend - q < 2 || pos + L > lim)) {
+                            ns = 1;
+                            L = (ent >> 16) & 31u;
+                        }
+                        if (pos + L > lim)
+                            bad = true;
+                        out_colb[((q & 31u) >> 2) * 128 + (q & 3u)] = (uint8_t)sy;
+                        if (ns == 2) {
+                            const uint32_t q1 = q + 1;
+                            out_colb[((q1 & 31u) >> 2) * 128 + (q1 & 3u)] = (uint8_t)(sy >> 8);
+                        }
+                        q += ns;
+                        pos += L;
+                        rs.consume(L);
+                        act = !bad && q < qend;
                     }
-                    ns = 1;
-                    sy = sym;
-                } else if (ns == 2 && (oend - o < 2 || pos + L > lim)) {
-                    ns = 1;
-                    L = (ent >> 16) & 31u;
                 }
-                if (pos + L > lim) {
-                    bad = true;
-                    break;
+                if (act)
+                    rs.top_up();
+                cp_async_wait<2>();
+                // flush the half that holds `fl` once it is complete
+                const uint32_t hs = fl & ~15u;
+                if (!bad && q >= hs + 16) {
+                    if (fl == hs) {
+                        const uint32_t *h = out_col + ((hs & 31u) >> 2) * 32;
+                        *reinterpret_cast<uint4 *>(ob + hs) = make_uint4(h[0], h[32], h[64], h[96]);
+                    } else {
+                        for (uint32_t b = fl; b < hs + 16; ++b)
+                            ob[b] = out_colb[((b & 31u) >> 2) * 128 + (b & 3u)];
+                    }
+                    fl = hs + 16;
                 }
-                ringb[o & 31] = (uint8_t)sy;
-                if (ns == 2)
-                    ringb[(o + 1) & 31] = (uint8_t)(sy >> 8);
-                const uint64_t o2 = o + ns;
-                if ((o2 ^ o) & ~15ull) {  // a 16-byte half of the ring is complete
-                    const uint64_t hs = o & ~15ull;
-                    const uint32_t *h = ringw + ((hs & 16) >> 2);
-                    if (hs >= ob)
-                        *reinterpret_cast<uint4 *>(a.out + hs) = make_uint4(h[0], h[1], h[2], h[3]);
-                    else
-                        for (uint64_t j = ob; j < hs + 16; ++j)
-                            a.out[j] = ringb[j & 31];
-                }
-                o = o2;
-                pos += L;
-                rd.consume(L);
             }
+            cp_async_wait<0>();
             if (!bad) {
-                const uint64_t hs = o & ~15ull;
-                for (uint64_t j = hs > ob ? hs : ob; j < o; ++j)
-                    a.out[j] = ringb[j & 31];
-                if (final_seg && c + 1 < chunks && pos != lim)
+                for (uint32_t b = fl; b < q; ++b)
+                    ob[b] = out_colb[((b & 31u) >> 2) * 128 + (b & 3u)];
+                if (todo && final_seg && c + 1 < chunks && pos != lim)
                     bad = true;
             }
         }

@@ -6,7 +6,7 @@
 // column l, so the 32 shared-memory atomics of one warp instruction always
 // fall in 32 different banks, whatever the data (a single repeated byte
 // included).  Persistent CTAs take 16 KiB units round robin; each thread
-// loads its two 16-byte pieces of the next unit before counting the current
+// loads its four 16-byte pieces of the next unit before counting the current
 // one.
 //
 // Optionally the kernel also writes every unit's own histogram (u16[256],
@@ -19,8 +19,8 @@
 namespace huff {
 namespace {
 
-constexpr int kHistBlock = 512;
-constexpr int kVecPerThread = kUnitSymbols / 16 / kHistBlock;  // 2
+constexpr int kHistBlock = 256;
+constexpr int kVecPerThread = kUnitSymbols / 16 / kHistBlock;  // 4
 
 __device__ __forceinline__ void count_word(uint32_t *col, uint32_t w)
 {
@@ -38,16 +38,15 @@ __device__ __forceinline__ void count16(uint32_t *col, uint4 v)
     count_word(col, v.w);
 }
 
-// Sum of bin (tid >> 1) over the 16 columns of half (tid & 1), combined over
-// the thread pair; the rotation keeps one warp's reads in distinct banks.
+// Sum of bin `tid` over its 32 columns; the rotation keeps one warp's reads
+// in distinct banks.
 __device__ __forceinline__ uint32_t fold_bin(const uint32_t *cnt, int tid)
 {
-    const int b = tid >> 1, h = (tid & 1) << 4;
     uint32_t s = 0;
 #pragma unroll
-    for (int l = 0; l < 16; ++l)
-        s += cnt[(b << 5) + ((h + l + b) & 31)];
-    return s + __shfl_xor_sync(0xffffffffu, s, 1);
+    for (int l = 0; l < 32; ++l)
+        s += cnt[(tid << 5) + ((l + tid) & 31)];
+    return s;
 }
 
 __global__ void __launch_bounds__(kHistBlock)
@@ -93,16 +92,15 @@ __global__ void __launch_bounds__(kHistBlock)
         if (unit_hist) {
             __syncthreads();  // all counts of unit u are in
             const uint32_t s = fold_bin(cnt, tid);
-            if ((tid & 1) == 0)
-                unit_hist[u * 256 + (tid >> 1)] = (uint16_t)(s - prev);
+            unit_hist[u * 256 + tid] = (uint16_t)(s - prev);
             prev = s;
             __syncthreads();  // folds read before the next unit's counts
         }
     }
     __syncthreads();
     const uint32_t s = fold_bin(cnt, tid);
-    if ((tid & 1) == 0 && s)
-        atomicAdd(hist + (tid >> 1), (unsigned long long)s);
+    if (s)
+        atomicAdd(hist + tid, (unsigned long long)s);
 }
 
 }  // namespace
