@@ -174,10 +174,10 @@ struct RingStream {
     const uint32_t *words;  // payload
     uint64_t nwords;
     uint64_t w0;
-    uint32_t widx;  // next word to move into buf
-    uint32_t fidx;  // next word to request
-    uint32_t nxt;   // word widx, preloaded
-    uint64_t buf;   // valid bits left-aligned
+    uint32_t widx;    // next word to move into the bit buffer
+    uint32_t fidx;    // next word to request
+    uint32_t nxt;     // word widx, preloaded
+    uint32_t bh, bl;  // bit buffer, valid bits left-aligned in bh:bl
     int have;
 
     __device__ __forceinline__ void fetch4()
@@ -212,24 +212,38 @@ struct RingStream {
         for (int r = 0; r < kInRing / 4; ++r)
             fetch4();
         cp_async_wait<0>();
-        const uint32_t first = col[(widx & (kInRing - 1)) * 32];
+        const uint32_t sh = pbit & 31;
+        bh = col[(widx & (kInRing - 1)) * 32] << sh;
+        bl = 0;
+        have = 32 - (int)sh;
         ++widx;
-        buf = ((uint64_t)first << 32) << (pbit & 31);
-        have = 32 - (int)(pbit & 31);
         nxt = col[(widx & (kInRing - 1)) * 32];
     }
+    // top the buffer up to more than 32 valid bits
     __device__ __forceinline__ void refill()
     {
         if (have <= 32) {
-            buf |= (uint64_t)nxt << (32 - have);
+            bh |= __funnelshift_rc(nxt, 0u, (uint32_t)have);  // nxt >> have (0 at 32)
+            bl |= nxt << (32 - have);
             have += 32;
             ++widx;
             nxt = col[(widx & (kInRing - 1)) * 32];
         }
     }
+    __device__ __forceinline__ uint32_t peek12() const { return bh >> (32 - kLutBits); }
+    __device__ __forceinline__ uint64_t buf64() const { return ((uint64_t)bh << 32) | bl; }
+    // drop L < 32 bits
+    __device__ __forceinline__ void consume_small(uint32_t L)
+    {
+        bh = __funnelshift_l(bl, bh, L);
+        bl <<= L;
+        have -= (int)L;
+    }
+    // drop L <= 32 bits
     __device__ __forceinline__ void consume(uint32_t L)
     {
-        buf <<= L;
+        bh = __funnelshift_lc(bl, bh, L);
+        bl = L >= 32 ? 0u : bl << L;
         have -= (int)L;
     }
 };
@@ -529,28 +543,34 @@ __global__ void __launch_bounds__(kDecBlock) k_decode(DecodeArgs a)
 #pragma unroll
                 for (int j = 0; j < kWindow; ++j) {
                     if (act) {
-                        rs.refill();
-                        const uint32_t ent = lut[rs.buf >> (64 - kLutBits)];
+                        if ((j & 1) == 0)
+                            rs.refill();  // two table codes use at most 24 of > 32 bits
+                        const uint32_t ent = lut[rs.peek12()];
                         uint32_t ns = ent >> 30, L = (ent >> 24) & 31u;
-                        if (ns == 0) {
+                        if (ns == 0) {  // longer than the table (rare)
+                            rs.refill();
                             uint32_t sym;
-                            if (!long_code(T, rs.buf, L, sym))
+                            if (!long_code(T, rs.buf64(), L, sym))
                                 L = 1;
                             ns = 1;
-                        } else if (ns == 2) {
-                            const uint32_t L0 = (ent >> 16) & 31u;
-                            if (pos + L0 >= stop) {
-                                ns = 1;
-                                L = L0;
-                            } else if (pos + L0 - g < 64) {
-                                bmap |= 1ull << (pos + L0 - g);
+                            rs.consume(L);
+                            rs.refill();  // keep >= 12 bits for the next lookup
+                        } else {
+                            if (ns == 2) {
+                                const uint32_t L0 = (ent >> 16) & 31u;
+                                if (pos + L0 >= stop) {
+                                    ns = 1;
+                                    L = L0;
+                                } else if (pos + L0 - g < 64) {
+                                    bmap |= 1ull << (pos + L0 - g);
+                                }
                             }
+                            rs.consume_small(L);
                         }
                         pos += L;
                         if (pos - g < 64)
                             bmap |= 1ull << (pos - g);
                         cnt1 += ns;
-                        rs.consume(L);
                         act = pos < stop;
                     }
                 }
@@ -606,37 +626,51 @@ __global__ void __launch_bounds__(kDecBlock) k_decode(DecodeArgs a)
                 rs.init(in_col, reinterpret_cast<const uint32_t *>(pay), pay_words, cbase >> 5,
                         (uint32_t)(cbase & 31) + entry);
             while (__any_sync(0xffffffffu, act)) {
+                // a window far from the segment's end needs no per-code checks:
+                // at most 16 symbols and 8 x 32 bits
+                const bool easy = act && qend - q >= 2 * kWindow && lim - pos >= 32 * kWindow;
 #pragma unroll
                 for (int j = 0; j < kWindow; ++j) {
                     if (act) {
-                        rs.refill();
-                        const uint32_t ent = lut[rs.buf >> (64 - kLutBits)];
+                        if ((j & 1) == 0)
+                            rs.refill();  // two table codes use at most 24 of > 32 bits
+                        const uint32_t ent = lut[rs.peek12()];
                         uint32_t ns = ent >> 30, L = (ent >> 24) & 31u, sy = ent;
-                        if (ns == 0) {
+                        if (ns == 0) {  // longer than the table (rare)
+                            rs.refill();
                             uint32_t sym = 0;
-                            if (!long_code(T, rs.buf, L, sym)) {
+                            if (!long_code(T, rs.buf64(), L, sym)) {
                                 bad = true;
                                 L = 0;
                             }
                             ns = 1;
                             sy = sym;
-                        } else if (ns == 2 && (qend - q < 2 || pos + L > lim)) {
-                            ns = 1;
-                            L = (ent >> 16) & 31u;
+                            if (!easy && pos + L > lim)
+                                bad = true;
+                            rs.consume(L);
+                            rs.refill();  // keep >= 12 bits for the next lookup
+                        } else {
+                            if (!easy && ns == 2 && (qend - q < 2 || pos + L > lim)) {
+                                ns = 1;
+                                L = (ent >> 16) & 31u;
+                            }
+                            if (!easy && pos + L > lim)
+                                bad = true;
+                            rs.consume_small(L);
                         }
-                        if (pos + L > lim)
-                            bad = true;
+                        // both bytes always: an unused second byte is overwritten
+                        // by the next symbol and never flushed
+                        const uint32_t q1 = q + 1;
                         out_colb[((q & 31u) >> 2) * 128 + (q & 3u)] = (uint8_t)sy;
-                        if (ns == 2) {
-                            const uint32_t q1 = q + 1;
-                            out_colb[((q1 & 31u) >> 2) * 128 + (q1 & 3u)] = (uint8_t)(sy >> 8);
-                        }
+                        out_colb[((q1 & 31u) >> 2) * 128 + (q1 & 3u)] = (uint8_t)(sy >> 8);
                         q += ns;
                         pos += L;
-                        rs.consume(L);
-                        act = !bad && q < qend;
+                        if (!easy)
+                            act = !bad && q < qend;
                     }
                 }
+                if (easy)
+                    act = !bad && q < qend;
                 if (act)
                     rs.top_up();
                 cp_async_wait<2>();

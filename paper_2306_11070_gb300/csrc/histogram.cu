@@ -22,15 +22,22 @@ namespace {
 constexpr int kHistBlock = 256;
 constexpr int kVecPerThread = kUnitSymbols / 16 / kHistBlock;  // 4
 
-__device__ __forceinline__ void count_word(uint32_t *col, uint32_t w)
+// One count: a shared-memory reduction at the 32-bit shared address of
+// (byte, lane); byte * 128 is the row offset of the [byte][lane] layout.
+__device__ __forceinline__ void count_at(uint32_t col, uint32_t byte)
 {
-    atomicAdd(col + ((w & 0xffu) << 5), 1u);
-    atomicAdd(col + (((w >> 8) & 0xffu) << 5), 1u);
-    atomicAdd(col + (((w >> 16) & 0xffu) << 5), 1u);
-    atomicAdd(col + ((w >> 24) << 5), 1u);
+    asm volatile("red.shared.add.u32 [%0], 1;" ::"r"(col + (byte << 7)) : "memory");
 }
 
-__device__ __forceinline__ void count16(uint32_t *col, uint4 v)
+__device__ __forceinline__ void count_word(uint32_t col, uint32_t w)
+{
+    count_at(col, __byte_perm(w, 0u, 0x4440u));
+    count_at(col, __byte_perm(w, 0u, 0x4441u));
+    count_at(col, __byte_perm(w, 0u, 0x4442u));
+    count_at(col, __byte_perm(w, 0u, 0x4443u));
+}
+
+__device__ __forceinline__ void count16(uint32_t col, uint4 v)
 {
     count_word(col, v.x);
     count_word(col, v.y);
@@ -57,7 +64,7 @@ __global__ void __launch_bounds__(kHistBlock)
     const int tid = threadIdx.x, lane = tid & 31;
     for (int i = tid; i < 256 * 32; i += kHistBlock)
         cnt[i] = 0;
-    uint32_t *col = cnt + lane;
+    const uint32_t col = smem_u32(cnt) + 4u * lane;  // this lane's column
     const uint64_t units = (n + kUnitSymbols - 1) / kUnitSymbols;
     const uint64_t nvec = n >> 4;
     const uint4 *v = reinterpret_cast<const uint4 *>(in);
@@ -87,7 +94,7 @@ __global__ void __launch_bounds__(kHistBlock)
         }
         if (u == units - 1) {  // ragged tail (< 16 bytes) belongs to the last unit
             if (tid < (int)(n & 15u))
-                atomicAdd(col + ((uint32_t)in[(nvec << 4) + tid] << 5), 1u);
+                count_at(col, in[(nvec << 4) + tid]);
         }
         if (unit_hist) {
             __syncthreads();  // all counts of unit u are in
