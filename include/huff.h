@@ -156,6 +156,32 @@ huff_status_t huff_encode_units(const uint8_t *d_in, uint64_t n, const huff_code
                                 void *d_ws, uint64_t ws_bytes, int32_t *d_status,
                                 huff_stream_t stream);
 
+/* Largest input huff_encode_noalloc accepts (1 GiB). */
+#define HUFF_NOALLOC_MAX_SYMBOLS (1ull << 30)
+
+/* huff_encode for callers that cannot allocate device memory while they
+ * encode -- for example a latency-critical loop where an allocation would
+ * synchronise the device, a service that runs inside a fixed memory budget
+ * reserved at start-up, or a wrapper that only ever hands over input and
+ * output buffers.  It takes no workspace: the encoder's scratch (bit count
+ * and bit offset of each 16 KiB unit) is a fixed array inside the library,
+ * about 0.75 MiB of device memory that every GPU which loads the library
+ * keeps until the process exits.  The paper has no counterpart; this is a
+ * deployment variant of huff_encode with the same arguments minus
+ * d_ws / ws_bytes, the same stream and the same device errors.
+ *  - n above HUFF_NOALLOC_MAX_SYMBOLS -> HUFF_ERR_BUDGET, nothing launched.
+ *  - The first call on a device looks up the array's device address
+ *    (cudaGetSymbolAddress) with that device current; make that first call
+ *    before any stream capture.
+ *  - All calls share the one array: each call rewrites the entries it reads,
+ *    but calls that overlap on the GPU (other streams, other threads) race
+ *    on it and must be serialised by the caller.
+ * Host errors: HUFF_ERR_INVALID_ARG, HUFF_ERR_CUDA, HUFF_ERR_UNSUPPORTED. */
+huff_status_t huff_encode_noalloc(const uint8_t *d_in, uint64_t n, const huff_codebook_t *d_cb,
+                                  uint32_t chunk_symbols, uint8_t *d_out, uint64_t out_cap,
+                                  uint64_t *d_out_bytes, int32_t *d_status,
+                                  huff_stream_t stream);
+
 /* Decode the stream d_stream[0, stream_bytes) into d_out[0, n) (Method 2's
  * reassembly by chunk id; the code is lossless).  The stream is validated:
  * header fields, a complete code (sum of 2^-len == 1, or one code of length

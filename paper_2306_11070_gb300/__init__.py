@@ -73,6 +73,8 @@ def lib() -> ctypes.CDLL:
         L.huff_build_codebook.argtypes = [vp, vp, vp, vp]
         L.huff_encode.restype = i32
         L.huff_encode.argtypes = [vp, u64, vp, u32, vp, u64, vp, vp, u64, vp, vp]
+        L.huff_encode_noalloc.restype = i32
+        L.huff_encode_noalloc.argtypes = [vp, u64, vp, u32, vp, u64, vp, vp, vp]
         L.huff_decode.restype = i32
         L.huff_decode.argtypes = [vp, u64, vp, u64, vp, vp, vp]
         L.huff_compress.restype = i32
@@ -221,6 +223,29 @@ def huff_encode_units(d_in: torch.Tensor, d_cb: torch.Tensor, d_unit_hist: torch
     _check(lib().huff_encode_units(_ptr(x), n, _ptr(d_cb), _ptr(d_unit_hist), int(chunk_symbols),
                                    _ptr(d_out), cap, _ptr(d_out_bytes), _ptr(d_ws), d_ws.numel(),
                                    _ptr(d_status), _stream(stream)), "huff_encode_units")
+    return d_out, d_out_bytes, d_status
+
+
+def huff_encode_noalloc(d_in: torch.Tensor, d_cb: torch.Tensor,
+                        chunk_symbols: int = DEFAULT_CHUNK_SYMBOLS,
+                        d_out: torch.Tensor | None = None,
+                        d_out_bytes: torch.Tensor | None = None,
+                        d_status: torch.Tensor | None = None, stream=None,
+                        out_cap: int | None = None):
+    """huff_encode without a workspace (the library's fixed scratch array)."""
+    x = _u8(d_in)
+    n = x.numel()
+    dev = x.device
+    if d_out is None:
+        d_out = torch.empty(huff_max_stream_size(n, chunk_symbols), dtype=torch.uint8, device=dev)
+    if d_out_bytes is None:
+        d_out_bytes = torch.zeros(1, dtype=torch.int64, device=dev)
+    if d_status is None:
+        d_status = new_status(dev)
+    cap = d_out.numel() if out_cap is None else int(out_cap)
+    _check(lib().huff_encode_noalloc(_ptr(x), n, _ptr(d_cb), int(chunk_symbols), _ptr(d_out), cap,
+                                     _ptr(d_out_bytes), _ptr(d_status), _stream(stream)),
+           "huff_encode_noalloc")
     return d_out, d_out_bytes, d_status
 
 
