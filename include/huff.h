@@ -205,6 +205,61 @@ huff_status_t huff_compress(const uint8_t *d_in, uint64_t n, uint32_t chunk_symb
                             void *d_ws, uint64_t ws_bytes, int32_t *d_status,
                             huff_stream_t stream);
 
+/* ---------------------------------------------------------------------
+ * Batched engine.  The paper's Method 2 (Section III-A) compresses every
+ * segment independently with its own tree and reassembles the results by
+ * segment id; here each descriptor is one independent buffer with its own
+ * codebook and stream, and a whole batch runs as one persistent fused
+ * launch (histograms, codebooks and unit offsets, encode -- or header
+ * scan and decode) captured once in a CUDA graph.  Every buffer's stream is
+ * byte-identical to huff_compress on that buffer alone.
+ * ------------------------------------------------------------------- */
+typedef enum huff_op { HUFF_BATCH_COMPRESS = 0, HUFF_BATCH_DECOMPRESS = 1 } huff_op_t;
+
+typedef struct huff_batch_desc {
+    const uint8_t *d_in;   /* compress: input bytes; decompress: one stream  */
+    uint64_t in_bytes;     /* compress: n; decompress: stream bytes          */
+    uint8_t *d_out;        /* compress: stream; decompress: decoded bytes    */
+    uint64_t out_cap;      /* bytes available at d_out                       */
+    uint64_t *d_out_bytes; /* compress: stream size; decompress: n           */
+    int32_t *d_status;     /* this buffer's device status, cleared each run  */
+} huff_batch_desc_t;
+
+typedef struct huff_batch_params {
+    uint32_t chunk_symbols; /* compress: chunk size of every stream           */
+    uint32_t ctas_per_sm;   /* persistent CTAs per SM, 0 = as many as fit     */
+    uint32_t decode_lanes;  /* decompress: lanes to spread a buffer over      */
+    uint32_t use_graph;     /* capture the launch in a CUDA graph (1) or not  */
+} huff_batch_params_t;
+
+typedef struct huff_batch_plan huff_batch_plan_t; /* opaque */
+
+/* Defaults: 16384-symbol chunks, full occupancy, 32 decode lanes, graph on. */
+void huff_batch_default_params(huff_batch_params_t *params);
+
+/* Plan a batch of `count` buffers for `op` (params may be NULL for the
+ * defaults).  The plan copies the descriptors, allocates its own device
+ * metadata and scratch (per-unit histograms, codebooks, offsets: about
+ * 520 bytes per 16 KiB of input for compression) and captures the launch in
+ * a CUDA graph; runs then allocate nothing.  Buffers are 16-byte aligned;
+ * compress outputs need out_cap >= header + offset table (use
+ * huff_max_stream_size).  Errors: HUFF_ERR_INVALID_ARG, HUFF_ERR_CUDA. */
+huff_status_t huff_batch_plan(const huff_batch_desc_t *descs, uint32_t count, huff_op_t op,
+                              const huff_batch_params_t *params, huff_batch_plan_t **plan);
+
+/* Run the planned batch on `stream`, asynchronously.  Per-buffer results
+ * and errors land in each descriptor's d_out_bytes and d_status (a wait
+ * that gave up marks every buffer HUFF_ERR_TIMEOUT).  Runs of one plan must
+ * not overlap on the GPU. */
+huff_status_t huff_batch_run(huff_batch_plan_t *plan, huff_stream_t stream);
+
+/* The parameters a plan uses, its grid size and whether it runs as a graph. */
+huff_status_t huff_batch_info(const huff_batch_plan_t *plan, huff_batch_params_t *params,
+                              uint32_t *grid, int32_t *used_graph);
+
+/* Free a plan (NULL is ignored).  Its runs must have completed. */
+void huff_batch_destroy(huff_batch_plan_t *plan);
+
 #ifdef __cplusplus
 }
 #endif

@@ -36,6 +36,22 @@ CODEBOOK_BYTES = 1288  # sizeof(huff_codebook_t)
 
 _lib = None
 
+HUFF_BATCH_COMPRESS = 0
+HUFF_BATCH_DECOMPRESS = 1
+
+
+class BatchDesc(ctypes.Structure):
+    """huff_batch_desc_t"""
+    _fields_ = [("d_in", ctypes.c_void_p), ("in_bytes", ctypes.c_uint64),
+                ("d_out", ctypes.c_void_p), ("out_cap", ctypes.c_uint64),
+                ("d_out_bytes", ctypes.c_void_p), ("d_status", ctypes.c_void_p)]
+
+
+class BatchParams(ctypes.Structure):
+    """huff_batch_params_t"""
+    _fields_ = [("chunk_symbols", ctypes.c_uint32), ("ctas_per_sm", ctypes.c_uint32),
+                ("decode_lanes", ctypes.c_uint32), ("use_graph", ctypes.c_uint32)]
+
 
 class HuffError(RuntimeError):
     def __init__(self, status: int, where: str = ""):
@@ -79,6 +95,18 @@ def lib() -> ctypes.CDLL:
         L.huff_decode.argtypes = [vp, u64, vp, u64, vp, vp, vp]
         L.huff_compress.restype = i32
         L.huff_compress.argtypes = [vp, u64, u32, vp, u64, vp, vp, u64, vp, vp]
+        L.huff_batch_default_params.restype = None
+        L.huff_batch_default_params.argtypes = [ctypes.POINTER(BatchParams)]
+        L.huff_batch_plan.restype = i32
+        L.huff_batch_plan.argtypes = [ctypes.POINTER(BatchDesc), u32, ctypes.c_int,
+                                      ctypes.POINTER(BatchParams), ctypes.POINTER(vp)]
+        L.huff_batch_run.restype = i32
+        L.huff_batch_run.argtypes = [vp, vp]
+        L.huff_batch_info.restype = i32
+        L.huff_batch_info.argtypes = [vp, ctypes.POINTER(BatchParams), ctypes.POINTER(u32),
+                                      ctypes.POINTER(i32)]
+        L.huff_batch_destroy.restype = None
+        L.huff_batch_destroy.argtypes = [vp]
         _lib = L
     return _lib
 
@@ -296,6 +324,63 @@ def huff_compress(d_in: torch.Tensor, chunk_symbols: int = DEFAULT_CHUNK_SYMBOLS
     return d_out, d_out_bytes, d_status
 
 
+# ---------------------------------------------------------------- batched engine
+def huff_batch_default_params() -> BatchParams:
+    p = BatchParams()
+    lib().huff_batch_default_params(ctypes.byref(p))
+    return p
+
+
+class BatchPlan:
+    """A planned batch (huff_batch_plan / huff_batch_run / huff_batch_destroy).
+
+    `inputs` and `outputs` are lists of uint8 CUDA tensors; for compression
+    the outputs must hold huff_max_stream_size bytes, for decompression the
+    decoded size.  Per-buffer sizes and statuses are the int64 / int32
+    tensors `out_bytes` and `status` (one entry per buffer).  The tensors
+    must stay alive as long as the plan."""
+
+    def __init__(self, inputs, outputs, op=HUFF_BATCH_COMPRESS, params: BatchParams | None = None,
+                 in_bytes=None):
+        count = len(inputs)
+        assert count == len(outputs) and count > 0
+        dev = inputs[0].device
+        self.inputs, self.outputs = list(inputs), list(outputs)
+        self.out_bytes = torch.zeros(count, dtype=torch.int64, device=dev)
+        self.status = torch.zeros(count, dtype=torch.int32, device=dev)
+        descs = (BatchDesc * count)()
+        for i, (x, y) in enumerate(zip(self.inputs, self.outputs)):
+            nb = x.numel() if in_bytes is None else int(in_bytes[i])
+            descs[i] = BatchDesc(x.data_ptr() if x.numel() else 0, nb, y.data_ptr(), y.numel(),
+                                 self.out_bytes.data_ptr() + 8 * i, self.status.data_ptr() + 4 * i)
+        self._descs = descs
+        h = ctypes.c_void_p(0)
+        prm = ctypes.byref(params) if params is not None else None
+        _check(lib().huff_batch_plan(descs, count, op, prm, ctypes.byref(h)), "huff_batch_plan")
+        self._h = h
+
+    def run(self, stream=None):
+        _check(lib().huff_batch_run(self._h, _stream(stream)), "huff_batch_run")
+
+    def info(self):
+        p, g, used = BatchParams(), ctypes.c_uint32(0), ctypes.c_int32(0)
+        _check(lib().huff_batch_info(self._h, ctypes.byref(p), ctypes.byref(g), ctypes.byref(used)),
+               "huff_batch_info")
+        return {"chunk_symbols": p.chunk_symbols, "ctas_per_sm": p.ctas_per_sm,
+                "decode_lanes": p.decode_lanes, "grid": g.value, "graph": bool(used.value)}
+
+    def close(self):
+        if self._h and self._h.value:
+            lib().huff_batch_destroy(self._h)
+            self._h = ctypes.c_void_p(0)
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 # ---------------------------------------------------------------- conveniences
 def parse_codebook(d_cb: torch.Tensor):
     """(len u8[256], code u32[256], nsym, max_len) as numpy, from a device codebook."""
@@ -325,4 +410,5 @@ def decompress(stream_t: torch.Tensor, stream=None) -> torch.Tensor:
 
 __all__ = [name for name in dir() if name.startswith("huff_")] + [
     "compress", "decompress", "parse_codebook", "new_status", "HuffError", "lib", "LIB_PATH",
+    "BatchPlan", "BatchDesc", "BatchParams", "HUFF_BATCH_COMPRESS", "HUFF_BATCH_DECOMPRESS",
 ]

@@ -1,0 +1,645 @@
+// Batched engine: many independent buffers, each with its own codebook (the
+// paper's Method 2, Section III-A, where every segment is compressed with
+// its own tree and reassembled by id), compressed or decompressed in one
+// persistent fused launch, captured once in a CUDA graph.
+//
+// One cooperative kernel (all CTAs resident) walks through phases separated
+// by a software grid barrier with a bounded wait:
+//   compress:   1. per-unit histograms of every 16 KiB unit of every buffer
+//                  (static round robin, next unit loaded ahead);
+//               2. per buffer (dynamic tickets): sum its unit histograms,
+//                  build the codebook, dot each unit's histogram with the
+//                  code lengths, scan them into unit bit offsets, write the
+//                  stream header and size;
+//               3. encode items of up to 8 units of one buffer (one unit per
+//                  warp, dynamic tickets), the CTA's code table rebuilt only
+//                  when the item's buffer changes.
+//   decompress: 1. per buffer: read n and the chunk size from the header and
+//                  size its work (chunks split across lanes so that even a
+//                  one-chunk buffer fills a warp);
+//               2. one CTA scans the work sizes;
+//               3. decode items of up to 8 warp tasks of one buffer (dynamic
+//                  tickets), tables rebuilt only when the buffer changes.
+// Every step reuses the single-stream device routines (*_impl.cuh), so a
+// buffer's stream is byte-identical to huff_compress on it alone.
+#include <algorithm>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "codebook_impl.cuh"
+#include "decode_impl.cuh"
+#include "encode_impl.cuh"
+#include "hist_impl.cuh"
+
+namespace huff {
+namespace {
+
+constexpr int kBatchBlock = 256;
+constexpr int kBatchWarps = kBatchBlock / 32;
+constexpr int kUnitsPerItem = kBatchWarps;  // encode: one unit per warp
+constexpr int kTasksPerItem = kBatchWarps;  // decode: one task per warp
+
+// control words (device): barrier arrivals and generation, then tickets
+enum { kCtlArrive = 0, kCtlGen = 1, kCtlTicket0 = 2, kCtlWords = 8 };
+
+struct BatchBuf {
+    const uint8_t *in;
+    uint64_t in_bytes;
+    uint8_t *out;
+    uint64_t out_cap;
+    unsigned long long *out_bytes;
+    int32_t *status;
+};
+
+struct BatchArgs {
+    const BatchBuf *bufs;
+    uint32_t count;
+    uint32_t cs;                    // compress: chunk symbols
+    const uint64_t *unit_base;      // compress: [count + 1] prefix of units
+    const uint64_t *item_base;      // compress: [count + 1] prefix of encode items
+    uint16_t *unit_hist;            // compress: [units][256]
+    unsigned long long *unit_off;   // compress: per buffer units_b + 1 entries at unit_base[b] + b
+    huff_codebook_t *cbs;           // compress: [count]
+    uint64_t *dec_items;            // decompress: [count + 1] items, then their prefix
+    uint32_t min_lanes;             // decompress: lanes per buffer to aim for
+    unsigned int *ctl;              // kCtlWords
+    int32_t *fail;                  // whole-batch failure (barrier timeout)
+};
+
+// Sense-free generation barrier over all CTAs of a cooperative launch.
+// Returns false (uniformly) when a wait gave up.
+__device__ bool grid_barrier(unsigned int *ctl, int32_t *fail)
+{
+    __shared__ int s_ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        volatile unsigned int *gen = ctl + kCtlGen;
+        const unsigned int g = *gen;
+        __threadfence();
+        const unsigned int arrived = atomicAdd(ctl + kCtlArrive, 1u) + 1;
+        int ok = 1;
+        if (arrived == gridDim.x) {
+            ctl[kCtlArrive] = 0;
+            __threadfence();
+            atomicAdd(ctl + kCtlGen, 1u);
+        } else {
+            uint32_t spins = 0;
+            while (*gen == g) {
+                if (++spins > kSpinLimit || *reinterpret_cast<volatile int32_t *>(fail)) {
+                    ok = 0;
+                    break;
+                }
+                __nanosleep(100);
+            }
+        }
+        if (!ok)
+            atomicCAS(fail, 0, HUFF_ERR_TIMEOUT);
+        __threadfence();
+        s_ok = ok;
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+
+// After a barrier gave up: every buffer reports the timeout.
+__device__ void fail_all(const BatchBuf *bufs, uint32_t count)
+{
+    if (threadIdx.x == 0)
+        for (uint32_t b = 0; b < count; ++b)
+            set_status(bufs[b].status, HUFF_ERR_TIMEOUT);
+}
+
+
+// Largest b with base[b] <= x, for x < base[count].
+__device__ __forceinline__ uint32_t find_owner(const uint64_t *base, uint32_t count, uint64_t x)
+{
+    uint32_t lo = 0, hi = count - 1;
+    while (lo < hi) {
+        const uint32_t mid = (lo + hi + 1) >> 1;
+        if (base[mid] <= x)
+            lo = mid;
+        else
+            hi = mid - 1;
+    }
+    return lo;
+}
+
+// A status word read once by thread 0 and broadcast, so that every thread of
+// the CTA takes the same branch even while other CTAs may be setting it.
+__device__ __forceinline__ bool uniform_failed(const int32_t *status)
+{
+    __shared__ int s_f;
+    if (threadIdx.x == 0)
+        s_f = chain_failed(status);
+    __syncthreads();
+    const bool f = s_f != 0;
+    __syncthreads();
+    return f;
+}
+
+__device__ __forceinline__ unsigned int take_ticket(unsigned int *ctl, int phase)
+{
+    __shared__ unsigned int s_t;
+    if (threadIdx.x == 0)
+        s_t = atomicAdd(ctl + kCtlTicket0 + phase, 1u);
+    __syncthreads();
+    const unsigned int t = s_t;
+    __syncthreads();
+    return t;
+}
+
+// ------------------------------------------------------------------ compress
+__global__ void __launch_bounds__(kBatchBlock, 3) k_batch_compress(BatchArgs a)
+{
+    extern __shared__ uint4 smem_raw[];
+    __shared__ unsigned long long s_hist[256];
+    __shared__ uint32_t s_len[256];
+    __shared__ unsigned long long s_scan[kBatchWarps];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const uint64_t total_units = a.unit_base[a.count];
+
+    // phase 0: clear the per-buffer statuses
+    for (uint32_t b = blockIdx.x * kBatchBlock + tid; b < a.count; b += gridDim.x * kBatchBlock)
+        *a.bufs[b].status = 0;
+    if (!grid_barrier(a.ctl, a.fail)) {
+        fail_all(a.bufs, a.count);
+        return;
+    }
+
+    // phase 1: per-unit histograms (columns never cleared: folds are differenced)
+    {
+        uint32_t *cnt = reinterpret_cast<uint32_t *>(smem_raw);
+        for (int i = tid; i < 256 * 32; i += kBatchBlock)
+            cnt[i] = 0;
+        const uint32_t col = smem_u32(cnt) + 4u * lane;
+        uint32_t prev = 0;
+        uint4 v[hst::kVecPerThread];
+        uint64_t g = blockIdx.x;
+        uint32_t b = g < total_units ? find_owner(a.unit_base, a.count, g) : 0;
+        if (g < total_units)
+            hst::load_unit(a.bufs[b].in, a.bufs[b].in_bytes, g - a.unit_base[b], v);
+        __syncthreads();
+        for (; g < total_units; g += gridDim.x) {
+            uint4 cur[hst::kVecPerThread];
+#pragma unroll
+            for (int j = 0; j < hst::kVecPerThread; ++j)
+                cur[j] = v[j];
+            const uint32_t cb = b;
+            const uint64_t gn = g + gridDim.x;
+            if (gn < total_units) {
+                b = find_owner(a.unit_base, a.count, gn);
+                hst::load_unit(a.bufs[b].in, a.bufs[b].in_bytes, gn - a.unit_base[b], v);
+            }
+            hst::count_unit(a.bufs[cb].in, a.bufs[cb].in_bytes, g - a.unit_base[cb], cur, col);
+            __syncthreads();
+            const uint32_t s = hst::fold_bin(cnt, tid);
+            a.unit_hist[g * 256 + tid] = (uint16_t)(s - prev);
+            prev = s;
+            __syncthreads();
+        }
+    }
+    if (!grid_barrier(a.ctl, a.fail)) {
+        fail_all(a.bufs, a.count);
+        return;
+    }
+
+    // phase 2: per buffer codebook, unit offsets and header
+    {
+        cbk::CodebookShared &csh = *reinterpret_cast<cbk::CodebookShared *>(smem_raw);
+        for (;;) {
+            const unsigned int b = take_ticket(a.ctl, 0);
+            if (b >= a.count)
+                break;
+            const BatchBuf B = a.bufs[b];
+            const uint64_t u0 = a.unit_base[b], nu = a.unit_base[b + 1] - u0;
+            unsigned long long h = 0;
+            for (uint64_t u = 0; u < nu; ++u)
+                h += a.unit_hist[(u0 + u) * 256 + tid];
+            s_hist[tid] = h;
+            __syncthreads();
+            cbk::build_codebook(s_hist, a.cbs + b, B.status, csh);
+            __syncthreads();
+            s_len[tid] = a.cbs[b].len[tid];
+            __syncthreads();
+            unsigned long long *off = a.unit_off + u0 + b;
+            // unit bit counts, scanned 256 at a time with a running carry
+            unsigned long long carry = 0;
+            for (uint64_t t0 = 0; t0 < nu; t0 += kBatchBlock) {
+                const uint64_t u = t0 + tid;
+                uint32_t bits = 0;
+                if (u < nu) {
+                    const uint16_t *uh = a.unit_hist + (u0 + u) * 256;
+                    for (int k = 0; k < 256; ++k)
+                        bits += (uint32_t)uh[k] * s_len[k];
+                }
+                unsigned long long x = bits;
+#pragma unroll
+                for (int d = 1; d < 32; d <<= 1) {
+                    const unsigned long long y = __shfl_up_sync(0xffffffffu, x, d);
+                    if (lane >= d)
+                        x += y;
+                }
+                if (lane == 31)
+                    s_scan[warp] = x;
+                __syncthreads();
+                unsigned long long before = 0, tot = 0;
+                for (int w = 0; w < kBatchWarps; ++w) {
+                    if (w < warp)
+                        before += s_scan[w];
+                    tot += s_scan[w];
+                }
+                if (u < nu)
+                    off[u] = carry + before + x - bits;
+                carry += tot;
+                __syncthreads();
+            }
+            if (tid == 0)
+                off[nu] = carry;
+            __syncthreads();
+            const enc::Job J = enc::make_job(B.in, B.in_bytes, a.cs, off, B.out, B.out_cap);
+            if (!uniform_failed(B.status))
+                enc::write_header(J, a.cbs + b, B.out_bytes, B.status);
+            __syncthreads();
+        }
+    }
+    if (!grid_barrier(a.ctl, a.fail)) {
+        fail_all(a.bufs, a.count);
+        return;
+    }
+
+    // phase 3: encode
+    {
+        uint32_t *tbl = reinterpret_cast<uint32_t *>(smem_raw);
+        uint32_t *wob = tbl + enc::kTblWords + warp * enc::kWarpObuf;
+        const uint64_t total_items = a.item_base[a.count];
+        uint32_t have = 0xffffffffu;  // buffer whose table is loaded
+        bool fast = true;
+        int group = 1;
+        for (;;) {
+            const unsigned int it = take_ticket(a.ctl, 1);
+            if (it >= total_items)
+                break;
+            const uint32_t b = find_owner(a.item_base, a.count, it);
+            const BatchBuf B = a.bufs[b];
+            if (uniform_failed(B.status))
+                continue;  // this buffer's codebook failed
+            if (b != have) {
+                const uint32_t max_len = a.cbs[b].max_len;
+                fast = max_len <= (uint32_t)enc::kFastMaxLen;
+                group = enc::emit_group(max_len);
+                enc::build_table(a.cbs + b, tbl, fast);
+                __syncthreads();
+                have = b;
+            }
+            const uint64_t u0 = a.unit_base[b];
+            const enc::Job J =
+                enc::make_job(B.in, B.in_bytes, a.cs, a.unit_off + u0 + b, B.out, B.out_cap);
+            const uint64_t u = (uint64_t)(it - a.item_base[b]) * kUnitsPerItem + warp;
+            bool overflow = false;
+            if (u < J.units)
+                overflow = enc::encode_unit(J, u, tbl, fast, group, wob);
+            if (overflow)
+                set_status(B.status, HUFF_ERR_CAPACITY);
+            __syncthreads();  // the table may be rebuilt for the next item
+        }
+    }
+}
+
+// ------------------------------------------------------------------ decompress
+__global__ void __launch_bounds__(kBatchBlock, 2) k_batch_decompress(BatchArgs a)
+{
+    __shared__ dec::DecodeShared sh;
+    __shared__ uint32_t in_ring[kBatchWarps * dec::kInRing * 32];
+    __shared__ uint32_t out_ring[kBatchWarps * dec::kOutRing * 32];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+
+    // phase 1: statuses and work sizes from the headers
+    for (uint32_t b = blockIdx.x * kBatchBlock + tid; b < a.count; b += gridDim.x * kBatchBlock) {
+        const BatchBuf B = a.bufs[b];
+        *B.status = 0;
+        uint64_t items = 1;  // a malformed header still gets one item to report it
+        if (B.in_bytes >= kHeaderBytes) {
+            const uint64_t n = *reinterpret_cast<const uint64_t *>(B.in + 256);
+            const uint32_t cs = *reinterpret_cast<const uint32_t *>(B.in + 264);
+            if (chunk_symbols_valid(cs)) {
+                const uint64_t chunks = n / cs + (n % cs != 0);
+                if (chunks <= (B.in_bytes - kHeaderBytes) / 8) {
+                    const uint32_t S = dec::pick_split(chunks, a.min_lanes);
+                    const uint64_t tasks = (chunks + (32 / S) - 1) / (32 / S);
+                    items = tasks ? (tasks + kTasksPerItem - 1) / kTasksPerItem : 1;
+                }
+            }
+        }
+        a.dec_items[b] = items;
+    }
+    if (!grid_barrier(a.ctl, a.fail)) {
+        fail_all(a.bufs, a.count);
+        return;
+    }
+    // phase 2: exclusive scan of the work sizes (CTA 0), in place
+    if (blockIdx.x == 0) {
+        __shared__ unsigned long long s_part[kBatchBlock];
+        const uint32_t per = (a.count + kBatchBlock - 1) / kBatchBlock;
+        const uint32_t b0 = tid * per, b1 = min(a.count, b0 + per);
+        unsigned long long own = 0;
+        for (uint32_t b = b0; b < b1; ++b)
+            own += a.dec_items[b];
+        s_part[tid] = own;
+        __syncthreads();
+        unsigned long long before = 0;
+        for (int t = 0; t < tid; ++t)
+            before += s_part[t];
+        for (uint32_t b = b0; b < b1; ++b) {
+            const unsigned long long v = a.dec_items[b];
+            a.dec_items[b] = before;
+            before += v;
+        }
+        if (tid == kBatchBlock - 1)
+            a.dec_items[a.count] = before;
+    }
+    if (!grid_barrier(a.ctl, a.fail)) {
+        fail_all(a.bufs, a.count);
+        return;
+    }
+
+    // phase 3: decode items
+    uint32_t *in_col = in_ring + warp * dec::kInRing * 32 + lane;
+    uint32_t *out_col = out_ring + warp * dec::kOutRing * 32 + lane;
+    const uint64_t total_items = a.dec_items[a.count];
+    uint32_t have = 0xffffffffu;
+    bool ready = false;
+    dec::StreamInfo si;
+    uint32_t S = 1;
+    for (;;) {
+        const unsigned int it = take_ticket(a.ctl, 2);
+        if (it >= total_items)
+            break;
+        const uint32_t b = find_owner(a.dec_items, a.count, it);
+        const BatchBuf B = a.bufs[b];
+        if (b != have) {
+            __syncthreads();
+            ready = dec::prepare<kBatchBlock>(B.in, B.in_bytes, B.out, B.out_cap, B.out_bytes,
+                                              B.status, it == a.dec_items[b] && tid == 0, sh, si);
+            if (ready)
+                S = dec::pick_split(si.chunks, a.min_lanes);
+            have = b;
+        }
+        if (!ready || uniform_failed(B.status))
+            continue;
+        const uint64_t tasks = (si.chunks + (32 / S) - 1) / (32 / S);
+        const uint64_t task = (uint64_t)(it - a.dec_items[b]) * kTasksPerItem + warp;
+        if (task < tasks && dec::decode_task(si, S, task, in_col, out_col)) {
+            if (lane == 0)
+                set_status(B.status, HUFF_ERR_CORRUPT_STREAM);
+        }
+    }
+}
+
+constexpr int kCompressSmem = (enc::kTblWords + kBatchWarps * enc::kWarpObuf) * 4;
+
+}  // namespace
+}  // namespace huff
+
+// ====================================================================== host
+using namespace huff;
+
+struct huff_batch_plan {
+    huff_op_t op;
+    huff_batch_params_t params;
+    uint32_t count;
+    int device;
+    unsigned grid;
+    // device memory owned by the plan
+    void *d_block;
+    BatchArgs args;
+    cudaGraph_t graph;
+    cudaGraphExec_t exec;
+};
+
+namespace {
+
+inline uint64_t align256(uint64_t x) { return (x + 255) & ~uint64_t(255); }
+
+huff_status_t launch_batch(huff_batch_plan_t *p, cudaStream_t s)
+{
+    if (cudaMemsetAsync(p->args.ctl, 0, sizeof(unsigned int) * kCtlWords + sizeof(int32_t), s) !=
+        cudaSuccess)
+        return HUFF_ERR_CUDA;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(p->grid);
+    cfg.blockDim = dim3(kBatchBlock);
+    cfg.dynamicSmemBytes = p->op == HUFF_BATCH_COMPRESS ? kCompressSmem : 0;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    cudaError_t err = p->op == HUFF_BATCH_COMPRESS
+                          ? cudaLaunchKernelEx(&cfg, k_batch_compress, p->args)
+                          : cudaLaunchKernelEx(&cfg, k_batch_decompress, p->args);
+    return err == cudaSuccess ? HUFF_OK : HUFF_ERR_CUDA;
+}
+
+void free_plan(huff_batch_plan_t *p)
+{
+    if (!p)
+        return;
+    if (p->exec)
+        cudaGraphExecDestroy(p->exec);
+    if (p->graph)
+        cudaGraphDestroy(p->graph);
+    if (p->d_block)
+        cudaFree(p->d_block);
+    delete p;
+}
+
+}  // namespace
+
+extern "C" {
+
+void huff_batch_default_params(huff_batch_params_t *params)
+{
+    if (!params)
+        return;
+    params->chunk_symbols = HUFF_DEFAULT_CHUNK_SYMBOLS;
+    params->ctas_per_sm = 0;  // as many as fit
+    params->decode_lanes = 32;
+    params->use_graph = 1;
+}
+
+huff_status_t huff_batch_plan(const huff_batch_desc_t *descs, uint32_t count, huff_op_t op,
+                              const huff_batch_params_t *params, huff_batch_plan_t **out_plan)
+{
+    if (!out_plan)
+        return HUFF_ERR_INVALID_ARG;
+    *out_plan = nullptr;
+    if (!descs || count == 0 || (op != HUFF_BATCH_COMPRESS && op != HUFF_BATCH_DECOMPRESS))
+        return HUFF_ERR_INVALID_ARG;
+    huff_batch_params_t prm;
+    huff_batch_default_params(&prm);
+    if (params)
+        prm = *params;
+    if (op == HUFF_BATCH_COMPRESS && !chunk_symbols_valid(prm.chunk_symbols))
+        return HUFF_ERR_INVALID_ARG;
+    if (prm.decode_lanes == 0 || prm.decode_lanes > 1024)
+        return HUFF_ERR_INVALID_ARG;
+    for (uint32_t i = 0; i < count; ++i) {
+        const huff_batch_desc_t &d = descs[i];
+        if (!d.d_out || !d.d_out_bytes || !d.d_status || (d.in_bytes && !d.d_in) ||
+            (reinterpret_cast<uintptr_t>(d.d_in) & 15) || (reinterpret_cast<uintptr_t>(d.d_out) & 15))
+            return HUFF_ERR_INVALID_ARG;
+        if (op == HUFF_BATCH_COMPRESS &&
+            (d.in_bytes > (uint64_t)UINT32_MAX * kUnitSymbols ||
+             d.out_cap < kHeaderBytes + 8 * ceil_div_u64(d.in_bytes, prm.chunk_symbols)))
+            return HUFF_ERR_INVALID_ARG;
+    }
+
+    huff_batch_plan_t *p = new (std::nothrow) huff_batch_plan_t();
+    if (!p)
+        return HUFF_ERR_CUDA;
+    std::memset(p, 0, sizeof(*p));
+    p->op = op;
+    p->params = prm;
+    p->count = count;
+    cudaGetDevice(&p->device);
+
+    // host-side layout of the plan's device block
+    std::vector<BatchBuf> bufs(count);
+    std::vector<uint64_t> unit_base(count + 1, 0), item_base(count + 1, 0);
+    for (uint32_t i = 0; i < count; ++i) {
+        bufs[i] = {descs[i].d_in, descs[i].in_bytes, descs[i].d_out, descs[i].out_cap,
+                   reinterpret_cast<unsigned long long *>(descs[i].d_out_bytes),
+                   descs[i].d_status};
+        const uint64_t units = (descs[i].in_bytes + kUnitSymbols - 1) / kUnitSymbols;
+        unit_base[i + 1] = unit_base[i] + units;
+        item_base[i + 1] = item_base[i] + (units + kUnitsPerItem - 1) / kUnitsPerItem;
+    }
+    const uint64_t total_units = unit_base[count];
+    uint64_t off = 0;
+    const uint64_t o_ctl = off;
+    off = align256(off + sizeof(unsigned int) * kCtlWords + sizeof(int32_t));
+    const uint64_t o_bufs = off;
+    off = align256(off + sizeof(BatchBuf) * count);
+    const uint64_t o_ub = off;
+    off = align256(off + 8 * (count + 1));
+    const uint64_t o_ib = off;
+    off = align256(off + 8 * (count + 1));
+    const uint64_t o_di = off;
+    off = align256(off + 8 * (count + 1));
+    uint64_t o_uh = 0, o_uo = 0, o_cb = 0;
+    if (op == HUFF_BATCH_COMPRESS) {
+        o_uh = off;
+        off = align256(off + 512 * total_units);
+        o_uo = off;
+        off = align256(off + 8 * (total_units + count));
+        o_cb = off;
+        off = align256(off + sizeof(huff_codebook_t) * count);
+    }
+    if (cudaMalloc(&p->d_block, off) != cudaSuccess) {
+        free_plan(p);
+        return HUFF_ERR_CUDA;
+    }
+    uint8_t *blk = static_cast<uint8_t *>(p->d_block);
+    if (cudaMemcpy(blk + o_bufs, bufs.data(), sizeof(BatchBuf) * count, cudaMemcpyHostToDevice) !=
+            cudaSuccess ||
+        cudaMemcpy(blk + o_ub, unit_base.data(), 8 * (count + 1), cudaMemcpyHostToDevice) !=
+            cudaSuccess ||
+        cudaMemcpy(blk + o_ib, item_base.data(), 8 * (count + 1), cudaMemcpyHostToDevice) !=
+            cudaSuccess) {
+        free_plan(p);
+        return HUFF_ERR_CUDA;
+    }
+    BatchArgs &a = p->args;
+    a.bufs = reinterpret_cast<const BatchBuf *>(blk + o_bufs);
+    a.count = count;
+    a.cs = prm.chunk_symbols;
+    a.unit_base = reinterpret_cast<const uint64_t *>(blk + o_ub);
+    a.item_base = reinterpret_cast<const uint64_t *>(blk + o_ib);
+    a.dec_items = reinterpret_cast<uint64_t *>(blk + o_di);
+    a.unit_hist = op == HUFF_BATCH_COMPRESS ? reinterpret_cast<uint16_t *>(blk + o_uh) : nullptr;
+    a.unit_off =
+        op == HUFF_BATCH_COMPRESS ? reinterpret_cast<unsigned long long *>(blk + o_uo) : nullptr;
+    a.cbs = op == HUFF_BATCH_COMPRESS ? reinterpret_cast<huff_codebook_t *>(blk + o_cb) : nullptr;
+    a.min_lanes = prm.decode_lanes;
+    a.ctl = reinterpret_cast<unsigned int *>(blk + o_ctl);
+    a.fail = reinterpret_cast<int32_t *>(blk + o_ctl + sizeof(unsigned int) * kCtlWords);
+
+    // persistent grid: every CTA must be resident (cooperative launch)
+    int per_sm = 0;
+    cudaError_t err;
+    if (op == HUFF_BATCH_COMPRESS) {
+        err = cudaFuncSetAttribute(k_batch_compress, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   kCompressSmem);
+        if (err == cudaSuccess)
+            err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch_compress,
+                                                                kBatchBlock, kCompressSmem);
+    } else {
+        err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch_decompress,
+                                                            kBatchBlock, 0);
+    }
+    if (err != cudaSuccess || per_sm < 1) {
+        free_plan(p);
+        return HUFF_ERR_CUDA;
+    }
+    if (prm.ctas_per_sm && (int)prm.ctas_per_sm < per_sm)
+        per_sm = (int)prm.ctas_per_sm;
+    p->grid = (unsigned)(device_sm_count() * per_sm);
+
+    if (prm.use_graph) {
+        cudaStream_t cs;
+        if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) {
+            free_plan(p);
+            return HUFF_ERR_CUDA;
+        }
+        bool ok = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+        if (ok) {
+            const huff_status_t st = launch_batch(p, cs);
+            ok = cudaStreamEndCapture(cs, &p->graph) == cudaSuccess && st == HUFF_OK;
+        }
+        if (ok)
+            ok = cudaGraphInstantiate(&p->exec, p->graph, 0) == cudaSuccess;
+        cudaStreamDestroy(cs);
+        if (!ok) {  // fall back to direct launches
+            cudaGetLastError();
+            if (p->exec)
+                cudaGraphExecDestroy(p->exec);
+            if (p->graph)
+                cudaGraphDestroy(p->graph);
+            p->exec = nullptr;
+            p->graph = nullptr;
+            p->params.use_graph = 0;
+        }
+    }
+    *out_plan = p;
+    return HUFF_OK;
+}
+
+huff_status_t huff_batch_run(huff_batch_plan_t *plan, huff_stream_t stream)
+{
+    if (!plan)
+        return HUFF_ERR_INVALID_ARG;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    if (plan->exec)
+        return cudaGraphLaunch(plan->exec, s) == cudaSuccess ? HUFF_OK : HUFF_ERR_CUDA;
+    return launch_batch(plan, s);
+}
+
+huff_status_t huff_batch_info(const huff_batch_plan_t *plan, huff_batch_params_t *params,
+                              uint32_t *grid, int32_t *used_graph)
+{
+    if (!plan)
+        return HUFF_ERR_INVALID_ARG;
+    if (params)
+        *params = plan->params;
+    if (grid)
+        *grid = plan->grid;
+    if (used_graph)
+        *used_graph = plan->exec != nullptr;
+    return HUFF_OK;
+}
+
+void huff_batch_destroy(huff_batch_plan_t *plan) { free_plan(plan); }
+
+}  // extern "C"

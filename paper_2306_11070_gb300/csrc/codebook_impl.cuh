@@ -1,0 +1,157 @@
+// Codebook device routine (one CTA of 256 threads per histogram), shared by
+// the single-stream kernel (codebook.cu) and the batched kernel (batch.cu).
+// See codebook.cu for the method.
+#pragma once
+
+#include "huff_internal.cuh"
+
+namespace huff {
+namespace cbk {
+
+struct CodebookShared {
+    unsigned long long w[256];
+    unsigned long long nw[511];  // [0,m): leaves by (weight, byte); [m,2m-1): merged
+    int16_t par[511];
+    int16_t dep[511];
+    int16_t anc[511];
+    uint8_t leaf_sym[256];
+    uint8_t len_s[256];
+    uint32_t bl[kMaxCodeLen + 1];
+    uint32_t next_code[kMaxCodeLen + 1];
+    int s_max;
+};
+
+// Build *cb from hist (u64[256]); blockDim.x must be 256.  On a code longer
+// than 32 bits *cb is cleared and HUFF_ERR_CODE_TOO_LONG goes to *status.
+__device__ __forceinline__ void build_codebook(const unsigned long long *__restrict__ hist,
+                                               huff_codebook_t *__restrict__ cb, int32_t *status,
+                                               CodebookShared &sh)
+{
+    if (chain_failed(status))
+        return;
+    const int t = threadIdx.x;
+    const unsigned long long wt = hist[t];
+    sh.w[t] = wt;
+    sh.len_s[t] = 0;
+    if (t <= (int)kMaxCodeLen)
+        sh.bl[t] = 0;
+    if (t == 0)
+        sh.s_max = 0;
+    const int present = wt > 0;
+    const int m = __syncthreads_count(present);
+
+    // 1. rank of byte t among present bytes, ordered by (weight, byte)
+    if (present) {
+        int rank = 0;
+        for (int j = 0; j < 256; ++j) {
+            const unsigned long long wj = sh.w[j];
+            rank += (wj > 0) & ((wj < wt) | ((wj == wt) & (j < t)));
+        }
+        sh.leaf_sym[rank] = (uint8_t)t;
+        sh.nw[rank] = wt;
+    }
+    __syncthreads();
+
+    if (m >= 2) {
+        // 2. two-queue merge
+        if (t == 0) {
+            int li = 0, ii = m, ni = m;
+            for (int step = 0; step < m - 1; ++step) {
+                int a, b;
+                if (li < m && (ii >= ni || sh.nw[li] <= sh.nw[ii]))
+                    a = li++;
+                else
+                    a = ii++;
+                if (li < m && (ii >= ni || sh.nw[li] <= sh.nw[ii]))
+                    b = li++;
+                else
+                    b = ii++;
+                sh.nw[ni] = sh.nw[a] + sh.nw[b];
+                sh.par[a] = (int16_t)ni;
+                sh.par[b] = (int16_t)ni;
+                ++ni;
+            }
+            sh.par[2 * m - 2] = (int16_t)(2 * m - 2);  // the root points at itself
+        }
+        __syncthreads();
+        // 3. depth = distance to the root, by pointer jumping (9 rounds cover 511 nodes)
+        const int nn = 2 * m - 1, root = 2 * m - 2;
+        for (int k = t; k < nn; k += 256) {
+            sh.dep[k] = (k == root) ? 0 : 1;
+            sh.anc[k] = sh.par[k];
+        }
+        __syncthreads();
+        for (int round = 0; round < 9; ++round) {
+            int16_t nd[2], na[2];
+#pragma unroll
+            for (int j = 0; j < 2; ++j) {
+                const int k = t + j * 256;
+                if (k < nn) {
+                    nd[j] = (int16_t)(sh.dep[k] + sh.dep[sh.anc[k]]);
+                    na[j] = sh.anc[sh.anc[k]];
+                }
+            }
+            __syncthreads();
+#pragma unroll
+            for (int j = 0; j < 2; ++j) {
+                const int k = t + j * 256;
+                if (k < nn) {
+                    sh.dep[k] = nd[j];
+                    sh.anc[k] = na[j];
+                }
+            }
+            __syncthreads();
+        }
+        if (t < m) {
+            const int d = sh.dep[t];
+            sh.len_s[sh.leaf_sym[t]] = (uint8_t)(d > 255 ? 255 : d);
+            atomicMax(&sh.s_max, d);
+        }
+    } else if (m == 1 && present) {
+        sh.len_s[t] = 1;  // one distinct byte: the 1-bit code "0"
+        sh.s_max = 1;
+    }
+    __syncthreads();
+
+    // 4. length limit, then canonical codes
+    const int max_len = sh.s_max;
+    if (max_len > (int)kMaxCodeLen) {
+        set_status(status, HUFF_ERR_CODE_TOO_LONG);
+        cb->len[t] = 0;
+        cb->code[t] = 0;
+        if (t == 0) {
+            cb->nsym = 0;
+            cb->max_len = 0;
+        }
+        return;
+    }
+    const int L = sh.len_s[t];
+    if (L)
+        atomicAdd(&sh.bl[L], 1u);
+    __syncthreads();
+    if (t == 0) {
+        uint32_t code = 0;
+        sh.next_code[0] = 0;
+        for (int bits = 1; bits <= (int)kMaxCodeLen; ++bits) {
+            code = (code + (bits == 1 ? 0u : sh.bl[bits - 1])) << 1;
+            sh.next_code[bits] = code;
+        }
+    }
+    __syncthreads();
+    uint32_t code = 0;
+    if (L) {
+        uint32_t r = 0;
+        for (int j = 0; j < t; ++j)
+            r += (sh.len_s[j] == L);
+        code = sh.next_code[L] + r;
+    }
+    cb->len[t] = (uint8_t)L;
+    cb->code[t] = code;
+    if (t == 0) {
+        cb->nsym = (uint32_t)m;
+        cb->max_len = (uint32_t)max_len;
+    }
+}
+
+}  // namespace cbk
+}  // namespace huff

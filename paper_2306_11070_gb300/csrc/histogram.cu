@@ -14,47 +14,14 @@
 // unit with a dot product against the code lengths, so it never has to wait
 // on another CTA.  A unit's counts are the difference of two folds of the
 // running columns, so the columns are never cleared.
-#include "huff_internal.cuh"
+#include "hist_impl.cuh"
 
 namespace huff {
 namespace {
 
-constexpr int kHistBlock = 256;
-constexpr int kVecPerThread = kUnitSymbols / 16 / kHistBlock;  // 4
+using namespace hst;
 
-// One count: a shared-memory reduction at the 32-bit shared address of
-// (byte, lane); byte * 128 is the row offset of the [byte][lane] layout.
-__device__ __forceinline__ void count_at(uint32_t col, uint32_t byte)
-{
-    asm volatile("red.shared.add.u32 [%0], 1;" ::"r"(col + (byte << 7)) : "memory");
-}
-
-__device__ __forceinline__ void count_word(uint32_t col, uint32_t w)
-{
-    count_at(col, __byte_perm(w, 0u, 0x4440u));
-    count_at(col, __byte_perm(w, 0u, 0x4441u));
-    count_at(col, __byte_perm(w, 0u, 0x4442u));
-    count_at(col, __byte_perm(w, 0u, 0x4443u));
-}
-
-__device__ __forceinline__ void count16(uint32_t col, uint4 v)
-{
-    count_word(col, v.x);
-    count_word(col, v.y);
-    count_word(col, v.z);
-    count_word(col, v.w);
-}
-
-// Sum of bin `tid` over its 32 columns; the rotation keeps one warp's reads
-// in distinct banks.
-__device__ __forceinline__ uint32_t fold_bin(const uint32_t *cnt, int tid)
-{
-    uint32_t s = 0;
-#pragma unroll
-    for (int l = 0; l < 32; ++l)
-        s += cnt[(tid << 5) + ((l + tid) & 31)];
-    return s;
-}
+constexpr int kHistBlock = kThreads;
 
 __global__ void __launch_bounds__(kHistBlock)
     k_histogram(const uint8_t *__restrict__ in, uint64_t n, unsigned long long *__restrict__ hist,
@@ -66,36 +33,18 @@ __global__ void __launch_bounds__(kHistBlock)
         cnt[i] = 0;
     const uint32_t col = smem_u32(cnt) + 4u * lane;  // this lane's column
     const uint64_t units = (n + kUnitSymbols - 1) / kUnitSymbols;
-    const uint64_t nvec = n >> 4;
-    const uint4 *v = reinterpret_cast<const uint4 *>(in);
     uint32_t prev = 0;  // fold of this thread's bin at the previous unit end
     uint4 a[kVecPerThread];
-    auto load_unit = [&](uint64_t uu) {
-#pragma unroll
-        for (int j = 0; j < kVecPerThread; ++j) {
-            const uint64_t q = uu * (kUnitSymbols / 16) + j * kHistBlock + tid;
-            a[j] = (uu < units && q < nvec) ? ld_stream16(v + q) : make_uint4(0, 0, 0, 0);
-        }
-    };
     uint64_t u = blockIdx.x;
-    load_unit(u);
+    load_unit(in, n, u, a);
     __syncthreads();
     for (; u < units; u += gridDim.x) {
         uint4 cur[kVecPerThread];
 #pragma unroll
         for (int j = 0; j < kVecPerThread; ++j)
             cur[j] = a[j];
-        load_unit(u + gridDim.x);  // in flight while this unit is counted
-#pragma unroll
-        for (int j = 0; j < kVecPerThread; ++j) {
-            const uint64_t q = u * (kUnitSymbols / 16) + j * kHistBlock + tid;
-            if (q < nvec)
-                count16(col, cur[j]);
-        }
-        if (u == units - 1) {  // ragged tail (< 16 bytes) belongs to the last unit
-            if (tid < (int)(n & 15u))
-                count_at(col, in[(nvec << 4) + tid]);
-        }
+        load_unit(in, n, u + gridDim.x, a);  // in flight while this unit is counted
+        count_unit(in, n, u, cur, col);
         if (unit_hist) {
             __syncthreads();  // all counts of unit u are in
             const uint32_t s = fold_bin(cnt, tid);

@@ -1,0 +1,153 @@
+"""GPU parity of the batched engine: every buffer of a batch against the CPU
+oracle, byte for byte, and the same buffer compressed alone.
+
+The batch mixes sizes (empty, a few bytes, below and across 16 KiB units and
+16384-symbol chunks, up to ~0.3 MiB) and distributions, includes a buffer
+whose tree is deeper than 32 bits (its status must be CODE_TOO_LONG while
+its neighbours succeed) and, for decompression, corrupt streams whose
+statuses must match the oracle's.  Each plan runs twice to check that the
+runs are repeatable.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import synth
+import paper_2306_11070_gb300 as hg
+from paper_2306_11070_gb300 import build as nvbuild
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    nvbuild.build()
+    hg.lib()
+
+
+def _fib(k):
+    f = [1, 1]
+    while len(f) < k:
+        f.append(f[-1] + f[-2])
+    return f[:k]
+
+
+def _mixed_inputs():
+    gens = [lambda n, s: synth.text(n, s), lambda n, s: synth.zipf_ascii(n, s),
+            lambda n, s: synth.uniform(n, s), lambda n, s: synth.geometric(n, s),
+            lambda n, s: synth.single(n, 0x41 + s % 20)]
+    sizes = [0, 1, 7, 16, 1000, 1024, 4097, 16383, 16384, 16385, 40000, 131072, 300001]
+    out = []
+    for i, n in enumerate(sizes * 2):
+        out.append(gens[i % len(gens)](n, 100 + i))
+    out.append(synth.counted(_fib(30), 7))    # 29-bit codes: the wide path
+    out.append(synth.counted(_fib(34), 8))    # 33-bit tree: error
+    return out
+
+
+def _dev(x):
+    t = torch.zeros(max(x.size, 16), dtype=torch.uint8, device="cuda")
+    if x.size:
+        t[:x.size] = torch.from_numpy(np.ascontiguousarray(x)).cuda()
+    return t[:x.size] if x.size else t[:0]
+
+
+def _compress_batch(xs, cs=16384, params=None):
+    ins = [_dev(x) for x in xs]
+    outs = [torch.zeros(hg.huff_max_stream_size(x.size, cs), dtype=torch.uint8, device="cuda")
+            for x in xs]
+    if params is None:
+        params = hg.huff_batch_default_params()
+        params.chunk_symbols = cs
+    plan = hg.BatchPlan(ins, outs, hg.HUFF_BATCH_COMPRESS, params)
+    return plan, ins, outs
+
+
+@pytest.mark.parametrize("cs", [16384, 4096])
+def test_batch_compress_matches_oracle_and_single(cs):
+    xs = _mixed_inputs()
+    plan, ins, outs = _compress_batch(xs, cs)
+    for rep in range(2):
+        plan.run()
+        torch.cuda.synchronize()
+        st = plan.status.cpu().numpy()
+        nb = plan.out_bytes.cpu().numpy()
+        for i, x in enumerate(xs):
+            ost, ref = oracle.compress(x, cs)
+            assert st[i] == ost, (rep, i, st[i], ost)
+            if ost != 0:
+                continue
+            got = outs[i][:nb[i]].cpu().numpy()
+            assert nb[i] == ref.size, (i, nb[i], ref.size)
+            assert np.array_equal(got, ref), i
+    # and each buffer alone through huff_compress
+    for i, x in enumerate(xs[:8]):
+        if x.size:
+            alone = hg.compress(_dev(x), cs).cpu().numpy()
+            assert np.array_equal(alone, outs[i][:alone.size].cpu().numpy())
+    info = plan.info()
+    assert info["grid"] > 0
+    plan.close()
+
+
+def test_batch_decompress_round_trip_and_corruption():
+    xs = [x for x in _mixed_inputs()[:-1]]  # drop the too-long one
+    streams = []
+    for i, x in enumerate(xs):
+        st, s = oracle.compress(x, 1024 if i % 3 == 0 else 16384)
+        assert st == 0
+        streams.append(s)
+    # two corrupt streams: a shifted chunk offset and a Kraft violation
+    bad1 = streams[10].copy()
+    if (bad1.size - 272) // 8 > 1:
+        o = 272 + 8
+        bad1[o:o + 8] = np.frombuffer((int.from_bytes(bytes(bad1[o:o + 8]), "little") + 1)
+                                      .to_bytes(8, "little"), np.uint8)
+    bad2 = streams[4].copy()
+    bad2[ord("e")] = 1
+    streams += [bad1, bad2]
+    xs += [xs[10], xs[4]]
+    ins = [_dev(s) for s in streams]
+    outs = [torch.zeros(max(x.size, 16), dtype=torch.uint8, device="cuda") for x in xs]
+    params = hg.huff_batch_default_params()
+    plan = hg.BatchPlan(ins, outs, hg.HUFF_BATCH_DECOMPRESS, params)
+    for rep in range(2):
+        for o in outs:
+            o.zero_()
+        plan.run()
+        torch.cuda.synchronize()
+        st = plan.status.cpu().numpy()
+        nb = plan.out_bytes.cpu().numpy()
+        for i, (s, x) in enumerate(zip(streams, xs)):
+            ost, back, on = oracle.decode(s, cap=outs[i].numel())
+            assert st[i] == ost, (rep, i, st[i], ost)
+            if ost == 0:
+                assert nb[i] == x.size
+                assert np.array_equal(outs[i][:x.size].cpu().numpy(), back)
+    plan.close()
+
+
+def test_batch_many_small_buffers_one_chunk_each():
+    xs = [synth.text(int(n), 500 + i) for i, n in
+          enumerate(synth.log_uniform_sizes(300, seed=9, lo=16, hi=20000))]
+    plan, ins, outs = _compress_batch(xs)
+    plan.run()
+    torch.cuda.synchronize()
+    st = plan.status.cpu().numpy()
+    nb = plan.out_bytes.cpu().numpy()
+    assert (st == 0).all()
+    streams = [outs[i][:nb[i]].clone() for i in range(len(xs))]
+    for i in range(0, len(xs), 37):
+        ost, ref = oracle.compress(xs[i])
+        assert np.array_equal(streams[i].cpu().numpy(), ref)
+    # round trip through the batched decoder
+    dec = [torch.zeros(max(x.size, 16), dtype=torch.uint8, device="cuda") for x in xs]
+    dplan = hg.BatchPlan(streams, dec, hg.HUFF_BATCH_DECOMPRESS)
+    dplan.run()
+    torch.cuda.synchronize()
+    assert (dplan.status.cpu().numpy() == 0).all()
+    for i, x in enumerate(xs):
+        assert np.array_equal(dec[i][:x.size].cpu().numpy(), x), i
+    plan.close()
+    dplan.close()
