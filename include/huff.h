@@ -260,6 +260,69 @@ huff_status_t huff_batch_info(const huff_batch_plan_t *plan, huff_batch_params_t
 /* Free a plan (NULL is ignored).  Its runs must have completed. */
 void huff_batch_destroy(huff_batch_plan_t *plan);
 
+/* ---------------------------------------------------------------------
+ * Served path: compress and decompress requests of mixed sizes arrive at
+ * any time; a scheduler thread admits them into rounds (continuous
+ * batching) as round slots and device memory free up, each round being one
+ * fused batch launch on its own stream, so admitted work overlaps on the
+ * device.  Device memory comes from one arena of `device_budget` bytes
+ * reserved at creation; a request is admitted only when its input, output
+ * and scratch fit.  Every result equals the same request served alone.
+ * ------------------------------------------------------------------- */
+typedef struct huff_server huff_server_t; /* opaque */
+
+typedef struct huff_server_cfg {
+    uint64_t device_budget;  /* arena bytes (default 8 GiB)                     */
+    uint32_t max_rounds;     /* rounds in flight at once (default 3, max 16)    */
+    uint32_t max_batch;      /* requests per round (default 256)                */
+    uint32_t chunk_symbols;  /* chunk size of the streams written (16384)      */
+    uint32_t decode_lanes;   /* lanes to spread a decompress request over (32)  */
+} huff_server_cfg_t;
+
+typedef struct huff_request {
+    int32_t op;            /* HUFF_BATCH_COMPRESS or HUFF_BATCH_DECOMPRESS       */
+    const uint8_t *h_in;   /* host input (pinned for full copy speed)           */
+    uint64_t in_bytes;     /* input bytes (a whole stream for decompress)       */
+    uint8_t *h_out;        /* host output                                        */
+    uint64_t out_cap;      /* bytes available at h_out                           */
+} huff_request_t;
+
+typedef struct huff_result {
+    int32_t done;       /* 1 once the result is in h_out                         */
+    int32_t status;     /* HUFF_OK or the request's error                        */
+    uint64_t out_bytes; /* stream size (compress) or n (decompress)             */
+    double t_submit;    /* seconds since the server started: submitted,         */
+    double t_start;     /*   admitted into a round,                              */
+    double t_done;      /*   result copied out                                   */
+} huff_result_t;
+
+/* Defaults listed in huff_server_cfg_t. */
+void huff_server_default_config(huff_server_cfg_t *cfg);
+
+/* Start a server on the current device (cfg may be NULL).  Reserves the
+ * arena and the pinned staging buffers, then starts the scheduler thread.
+ * Errors: HUFF_ERR_INVALID_ARG, HUFF_ERR_CUDA. */
+huff_status_t huff_server_create(const huff_server_cfg_t *cfg, huff_server_t **server);
+
+/* Queue a request; *ticket identifies it.  Host buffers must stay valid
+ * until the result is done.  HUFF_ERR_BUDGET when the request could never
+ * fit the arena (it is not queued); HUFF_ERR_INVALID_ARG for bad fields. */
+huff_status_t huff_server_submit(huff_server_t *server, const huff_request_t *req,
+                                 uint64_t *ticket);
+
+/* Non-blocking state of a request (res->done tells whether it finished). */
+huff_status_t huff_server_poll(huff_server_t *server, uint64_t ticket, huff_result_t *res);
+
+/* Wait up to timeout_ms for a request; HUFF_ERR_TIMEOUT if still running. */
+huff_status_t huff_server_wait(huff_server_t *server, uint64_t ticket, uint32_t timeout_ms,
+                               huff_result_t *res);
+
+/* Forget a finished request (its ticket becomes invalid). */
+huff_status_t huff_server_release(huff_server_t *server, uint64_t ticket);
+
+/* Finish the queued and running requests, stop the thread, free everything. */
+void huff_server_destroy(huff_server_t *server);
+
 #ifdef __cplusplus
 }
 #endif

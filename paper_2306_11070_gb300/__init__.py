@@ -53,6 +53,26 @@ class BatchParams(ctypes.Structure):
                 ("decode_lanes", ctypes.c_uint32), ("use_graph", ctypes.c_uint32)]
 
 
+class ServerConfig(ctypes.Structure):
+    """huff_server_cfg_t"""
+    _fields_ = [("device_budget", ctypes.c_uint64), ("max_rounds", ctypes.c_uint32),
+                ("max_batch", ctypes.c_uint32), ("chunk_symbols", ctypes.c_uint32),
+                ("decode_lanes", ctypes.c_uint32)]
+
+
+class Request(ctypes.Structure):
+    """huff_request_t"""
+    _fields_ = [("op", ctypes.c_int32), ("h_in", ctypes.c_void_p), ("in_bytes", ctypes.c_uint64),
+                ("h_out", ctypes.c_void_p), ("out_cap", ctypes.c_uint64)]
+
+
+class Result(ctypes.Structure):
+    """huff_result_t"""
+    _fields_ = [("done", ctypes.c_int32), ("status", ctypes.c_int32),
+                ("out_bytes", ctypes.c_uint64), ("t_submit", ctypes.c_double),
+                ("t_start", ctypes.c_double), ("t_done", ctypes.c_double)]
+
+
 class HuffError(RuntimeError):
     def __init__(self, status: int, where: str = ""):
         self.status = int(status)
@@ -95,6 +115,20 @@ def lib() -> ctypes.CDLL:
         L.huff_decode.argtypes = [vp, u64, vp, u64, vp, vp, vp]
         L.huff_compress.restype = i32
         L.huff_compress.argtypes = [vp, u64, u32, vp, u64, vp, vp, u64, vp, vp]
+        L.huff_server_default_config.restype = None
+        L.huff_server_default_config.argtypes = [ctypes.POINTER(ServerConfig)]
+        L.huff_server_create.restype = i32
+        L.huff_server_create.argtypes = [ctypes.POINTER(ServerConfig), ctypes.POINTER(vp)]
+        L.huff_server_submit.restype = i32
+        L.huff_server_submit.argtypes = [vp, ctypes.POINTER(Request), ctypes.POINTER(u64)]
+        L.huff_server_poll.restype = i32
+        L.huff_server_poll.argtypes = [vp, u64, ctypes.POINTER(Result)]
+        L.huff_server_wait.restype = i32
+        L.huff_server_wait.argtypes = [vp, u64, u32, ctypes.POINTER(Result)]
+        L.huff_server_release.restype = i32
+        L.huff_server_release.argtypes = [vp, u64]
+        L.huff_server_destroy.restype = None
+        L.huff_server_destroy.argtypes = [vp]
         L.huff_batch_default_params.restype = None
         L.huff_batch_default_params.argtypes = [ctypes.POINTER(BatchParams)]
         L.huff_batch_plan.restype = i32
@@ -381,6 +415,76 @@ class BatchPlan:
             pass
 
 
+# ---------------------------------------------------------------- served path
+def huff_server_default_config() -> ServerConfig:
+    c = ServerConfig()
+    lib().huff_server_default_config(ctypes.byref(c))
+    return c
+
+
+def _host_ptr(buf) -> int:
+    """Address of a host buffer: a CPU tensor (pinned for full speed) or numpy array."""
+    if isinstance(buf, torch.Tensor):
+        assert not buf.is_cuda and buf.is_contiguous()
+        return buf.data_ptr()
+    return int(buf.ctypes.data)
+
+
+class Server:
+    """huff_server_*: continuous-batching request loop on the current device."""
+
+    def __init__(self, cfg: ServerConfig | None = None):
+        h = ctypes.c_void_p(0)
+        _check(lib().huff_server_create(ctypes.byref(cfg) if cfg is not None else None,
+                                        ctypes.byref(h)), "huff_server_create")
+        self._h = h
+        self._keep = {}
+
+    def submit(self, op: int, h_in, h_out, in_bytes: int | None = None) -> int:
+        n = (h_in.numel() if isinstance(h_in, torch.Tensor) else h_in.size) if in_bytes is None \
+            else int(in_bytes)
+        cap = h_out.numel() if isinstance(h_out, torch.Tensor) else h_out.size
+        req = Request(op, _host_ptr(h_in) if n else 0, n, _host_ptr(h_out), cap)
+        t = ctypes.c_uint64(0)
+        _check(lib().huff_server_submit(self._h, ctypes.byref(req), ctypes.byref(t)),
+               "huff_server_submit")
+        self._keep[t.value] = (h_in, h_out)
+        return t.value
+
+    @staticmethod
+    def _res(r: Result):
+        return {"done": bool(r.done), "status": r.status, "out_bytes": r.out_bytes,
+                "t_submit": r.t_submit, "t_start": r.t_start, "t_done": r.t_done}
+
+    def poll(self, ticket: int):
+        r = Result()
+        _check(lib().huff_server_poll(self._h, ticket, ctypes.byref(r)), "huff_server_poll")
+        return self._res(r)
+
+    def wait(self, ticket: int, timeout_ms: int = 60000):
+        r = Result()
+        st = lib().huff_server_wait(self._h, ticket, timeout_ms, ctypes.byref(r))
+        if st not in (HUFF_OK, HUFF_ERR_TIMEOUT):
+            raise HuffError(st, "huff_server_wait")
+        return self._res(r)
+
+    def release(self, ticket: int):
+        _check(lib().huff_server_release(self._h, ticket), "huff_server_release")
+        self._keep.pop(ticket, None)
+
+    def close(self):
+        if self._h and self._h.value:
+            lib().huff_server_destroy(self._h)
+            self._h = ctypes.c_void_p(0)
+            self._keep.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 # ---------------------------------------------------------------- conveniences
 def parse_codebook(d_cb: torch.Tensor):
     """(len u8[256], code u32[256], nsym, max_len) as numpy, from a device codebook."""
@@ -411,4 +515,5 @@ def decompress(stream_t: torch.Tensor, stream=None) -> torch.Tensor:
 __all__ = [name for name in dir() if name.startswith("huff_")] + [
     "compress", "decompress", "parse_codebook", "new_status", "HuffError", "lib", "LIB_PATH",
     "BatchPlan", "BatchDesc", "BatchParams", "HUFF_BATCH_COMPRESS", "HUFF_BATCH_DECOMPRESS",
+    "Server", "ServerConfig", "Request", "Result",
 ]

@@ -27,6 +27,7 @@
 #include <new>
 #include <vector>
 
+#include "batch_internal.cuh"
 #include "codebook_impl.cuh"
 #include "decode_impl.cuh"
 #include "encode_impl.cuh"
@@ -34,38 +35,6 @@
 
 namespace huff {
 namespace {
-
-constexpr int kBatchBlock = 256;
-constexpr int kBatchWarps = kBatchBlock / 32;
-constexpr int kUnitsPerItem = kBatchWarps;  // encode: one unit per warp
-constexpr int kTasksPerItem = kBatchWarps;  // decode: one task per warp
-
-// control words (device): barrier arrivals and generation, then tickets
-enum { kCtlArrive = 0, kCtlGen = 1, kCtlTicket0 = 2, kCtlWords = 8 };
-
-struct BatchBuf {
-    const uint8_t *in;
-    uint64_t in_bytes;
-    uint8_t *out;
-    uint64_t out_cap;
-    unsigned long long *out_bytes;
-    int32_t *status;
-};
-
-struct BatchArgs {
-    const BatchBuf *bufs;
-    uint32_t count;
-    uint32_t cs;                    // compress: chunk symbols
-    const uint64_t *unit_base;      // compress: [count + 1] prefix of units
-    const uint64_t *item_base;      // compress: [count + 1] prefix of encode items
-    uint16_t *unit_hist;            // compress: [units][256]
-    unsigned long long *unit_off;   // compress: per buffer units_b + 1 entries at unit_base[b] + b
-    huff_codebook_t *cbs;           // compress: [count]
-    uint64_t *dec_items;            // decompress: [count + 1] items, then their prefix
-    uint32_t min_lanes;             // decompress: lanes per buffer to aim for
-    unsigned int *ctl;              // kCtlWords
-    int32_t *fail;                  // whole-batch failure (barrier timeout)
-};
 
 // Sense-free generation barrier over all CTAs of a cooperative launch.
 // Returns false (uniformly) when a wait gave up.
@@ -399,48 +368,174 @@ __global__ void __launch_bounds__(kBatchBlock, 2) k_batch_decompress(BatchArgs a
 constexpr int kCompressSmem = (enc::kTblWords + kBatchWarps * enc::kWarpObuf) * 4;
 
 }  // namespace
+
 }  // namespace huff
 
 // ====================================================================== host
-using namespace huff;
+namespace huff {
 
-struct huff_batch_plan {
-    huff_op_t op;
-    huff_batch_params_t params;
-    uint32_t count;
-    int device;
-    unsigned grid;
-    // device memory owned by the plan
-    void *d_block;
-    BatchArgs args;
-    cudaGraph_t graph;
-    cudaGraphExec_t exec;
-};
-
-namespace {
-
-inline uint64_t align256(uint64_t x) { return (x + 255) & ~uint64_t(255); }
-
-huff_status_t launch_batch(huff_batch_plan_t *p, cudaStream_t s)
+// Device block of one batch: control words, descriptors, prefix arrays and
+// (compress) per-unit histograms, unit offsets and codebooks.
+void batch_layout(const huff_batch_desc_t *descs, uint32_t count, huff_op_t op, BatchLayout &L)
 {
-    if (cudaMemsetAsync(p->args.ctl, 0, sizeof(unsigned int) * kCtlWords + sizeof(int32_t), s) !=
-        cudaSuccess)
-        return HUFF_ERR_CUDA;
+    auto al = [](uint64_t x) { return (x + 255) & ~uint64_t(255); };
+    L.count = count;
+    L.op = op;
+    L.bufs.resize(count);
+    L.unit_base.assign(count + 1, 0);
+    L.item_base.assign(count + 1, 0);
+    for (uint32_t i = 0; i < count; ++i) {
+        L.bufs[i] = {descs[i].d_in, descs[i].in_bytes, descs[i].d_out, descs[i].out_cap,
+                     reinterpret_cast<unsigned long long *>(descs[i].d_out_bytes),
+                     descs[i].d_status};
+        const uint64_t units = op == HUFF_BATCH_COMPRESS
+                                   ? (descs[i].in_bytes + kUnitSymbols - 1) / kUnitSymbols
+                                   : 0;
+        L.unit_base[i + 1] = L.unit_base[i] + units;
+        L.item_base[i + 1] = L.item_base[i] + (units + kUnitsPerItem - 1) / kUnitsPerItem;
+    }
+    const uint64_t total_units = L.unit_base[count];
+    uint64_t off = 0;
+    L.o_ctl = off;
+    off = al(off + sizeof(unsigned int) * kCtlWords + sizeof(int32_t));
+    L.o_bufs = off;
+    off = al(off + sizeof(BatchBuf) * count);
+    L.o_ub = off;
+    off = al(off + 8 * (count + 1));
+    L.o_ib = off;
+    off = al(off + 8 * (count + 1));
+    L.o_di = off;
+    off = al(off + 8 * (count + 1));
+    L.o_uh = L.o_uo = L.o_cb = off;
+    if (op == HUFF_BATCH_COMPRESS) {
+        L.o_uh = off;
+        off = al(off + 512 * total_units);
+        L.o_uo = off;
+        off = al(off + 8 * (total_units + count));
+        L.o_cb = off;
+        off = al(off + sizeof(huff_codebook_t) * count);
+    }
+    L.bytes = off;
+    // the host-side part copied to the device: descriptors and prefixes
+    L.upload_bytes = L.o_di;
+}
+
+BatchArgs batch_args(const BatchLayout &L, void *d_block, uint32_t cs, uint32_t lanes)
+{
+    uint8_t *blk = static_cast<uint8_t *>(d_block);
+    BatchArgs a;
+    a.bufs = reinterpret_cast<const BatchBuf *>(blk + L.o_bufs);
+    a.count = L.count;
+    a.cs = cs;
+    a.unit_base = reinterpret_cast<const uint64_t *>(blk + L.o_ub);
+    a.item_base = reinterpret_cast<const uint64_t *>(blk + L.o_ib);
+    a.dec_items = reinterpret_cast<uint64_t *>(blk + L.o_di);
+    const bool c = L.op == HUFF_BATCH_COMPRESS;
+    a.unit_hist = c ? reinterpret_cast<uint16_t *>(blk + L.o_uh) : nullptr;
+    a.unit_off = c ? reinterpret_cast<unsigned long long *>(blk + L.o_uo) : nullptr;
+    a.cbs = c ? reinterpret_cast<huff_codebook_t *>(blk + L.o_cb) : nullptr;
+    a.min_lanes = lanes;
+    a.ctl = reinterpret_cast<unsigned int *>(blk + L.o_ctl);
+    a.fail = reinterpret_cast<int32_t *>(blk + L.o_ctl + sizeof(unsigned int) * kCtlWords);
+    return a;
+}
+
+// Fill `host` (upload_bytes, ideally pinned) with the descriptors and prefixes
+// and copy it to the start of the device block.
+cudaError_t batch_upload(const BatchLayout &L, void *d_block, uint8_t *host, cudaStream_t s)
+{
+    std::memset(host, 0, L.upload_bytes);
+    std::memcpy(host + L.o_bufs, L.bufs.data(), sizeof(BatchBuf) * L.count);
+    std::memcpy(host + L.o_ub, L.unit_base.data(), 8 * (L.count + 1));
+    std::memcpy(host + L.o_ib, L.item_base.data(), 8 * (L.count + 1));
+    return cudaMemcpyAsync(d_block, host, L.upload_bytes, cudaMemcpyHostToDevice, s);
+}
+
+// Resident CTAs per SM of the batch kernel for `op`.
+int batch_occupancy(huff_op_t op)
+{
+    static int occ[2] = {0, 0};
+    const int i = op == HUFF_BATCH_COMPRESS ? 0 : 1;
+    if (occ[i] == 0) {
+        int per_sm = 0;
+        cudaError_t err;
+        if (i == 0) {
+            err = cudaFuncSetAttribute(k_batch_compress,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, kCompressSmem);
+            if (err == cudaSuccess)
+                err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch_compress,
+                                                                    kBatchBlock, kCompressSmem);
+        } else {
+            err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch_decompress,
+                                                                kBatchBlock, 0);
+        }
+        if (err != cudaSuccess || per_sm < 1)
+            return 0;
+        occ[i] = per_sm;
+    }
+    return occ[i];
+}
+
+// Clear the control words and launch the cooperative batch kernel.
+cudaError_t batch_launch(huff_op_t op, const BatchArgs &args, unsigned grid, cudaStream_t s)
+{
+    cudaError_t err = cudaMemsetAsync(args.ctl, 0, sizeof(unsigned int) * kCtlWords + sizeof(int32_t), s);
+    if (err != cudaSuccess)
+        return err;
     cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(p->grid);
+    cfg.gridDim = dim3(grid);
     cfg.blockDim = dim3(kBatchBlock);
-    cfg.dynamicSmemBytes = p->op == HUFF_BATCH_COMPRESS ? kCompressSmem : 0;
+    cfg.dynamicSmemBytes = op == HUFF_BATCH_COMPRESS ? kCompressSmem : 0;
     cfg.stream = s;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeCooperative;
     attr[0].val.cooperative = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    cudaError_t err = p->op == HUFF_BATCH_COMPRESS
-                          ? cudaLaunchKernelEx(&cfg, k_batch_compress, p->args)
-                          : cudaLaunchKernelEx(&cfg, k_batch_decompress, p->args);
-    return err == cudaSuccess ? HUFF_OK : HUFF_ERR_CUDA;
+    return op == HUFF_BATCH_COMPRESS ? cudaLaunchKernelEx(&cfg, k_batch_compress, args)
+                                     : cudaLaunchKernelEx(&cfg, k_batch_decompress, args);
 }
+
+// Argument checks shared by plans and served rounds.
+huff_status_t batch_check(const huff_batch_desc_t *descs, uint32_t count, huff_op_t op,
+                          const huff_batch_params_t &prm)
+{
+    if (!descs || count == 0 || (op != HUFF_BATCH_COMPRESS && op != HUFF_BATCH_DECOMPRESS))
+        return HUFF_ERR_INVALID_ARG;
+    if (op == HUFF_BATCH_COMPRESS && !chunk_symbols_valid(prm.chunk_symbols))
+        return HUFF_ERR_INVALID_ARG;
+    if (prm.decode_lanes == 0 || prm.decode_lanes > 1024)
+        return HUFF_ERR_INVALID_ARG;
+    for (uint32_t i = 0; i < count; ++i) {
+        const huff_batch_desc_t &d = descs[i];
+        if (!d.d_out || !d.d_out_bytes || !d.d_status || (d.in_bytes && !d.d_in) ||
+            (reinterpret_cast<uintptr_t>(d.d_in) & 15) ||
+            (reinterpret_cast<uintptr_t>(d.d_out) & 15))
+            return HUFF_ERR_INVALID_ARG;
+        if (op == HUFF_BATCH_COMPRESS &&
+            (d.in_bytes > (uint64_t)UINT32_MAX * kUnitSymbols ||
+             d.out_cap < kHeaderBytes + 8 * ceil_div_u64(d.in_bytes, prm.chunk_symbols)))
+            return HUFF_ERR_INVALID_ARG;
+    }
+    return HUFF_OK;
+}
+
+}  // namespace huff
+
+using namespace huff;
+
+struct huff_batch_plan {
+    huff_op_t op;
+    huff_batch_params_t params;
+    uint32_t count;
+    unsigned grid;
+    void *d_block;  // device memory owned by the plan
+    BatchArgs args;
+    cudaGraph_t graph;
+    cudaGraphExec_t exec;
+};
+
+namespace {
 
 void free_plan(huff_batch_plan_t *p)
 {
@@ -475,26 +570,13 @@ huff_status_t huff_batch_plan(const huff_batch_desc_t *descs, uint32_t count, hu
     if (!out_plan)
         return HUFF_ERR_INVALID_ARG;
     *out_plan = nullptr;
-    if (!descs || count == 0 || (op != HUFF_BATCH_COMPRESS && op != HUFF_BATCH_DECOMPRESS))
-        return HUFF_ERR_INVALID_ARG;
     huff_batch_params_t prm;
     huff_batch_default_params(&prm);
     if (params)
         prm = *params;
-    if (op == HUFF_BATCH_COMPRESS && !chunk_symbols_valid(prm.chunk_symbols))
-        return HUFF_ERR_INVALID_ARG;
-    if (prm.decode_lanes == 0 || prm.decode_lanes > 1024)
-        return HUFF_ERR_INVALID_ARG;
-    for (uint32_t i = 0; i < count; ++i) {
-        const huff_batch_desc_t &d = descs[i];
-        if (!d.d_out || !d.d_out_bytes || !d.d_status || (d.in_bytes && !d.d_in) ||
-            (reinterpret_cast<uintptr_t>(d.d_in) & 15) || (reinterpret_cast<uintptr_t>(d.d_out) & 15))
-            return HUFF_ERR_INVALID_ARG;
-        if (op == HUFF_BATCH_COMPRESS &&
-            (d.in_bytes > (uint64_t)UINT32_MAX * kUnitSymbols ||
-             d.out_cap < kHeaderBytes + 8 * ceil_div_u64(d.in_bytes, prm.chunk_symbols)))
-            return HUFF_ERR_INVALID_ARG;
-    }
+    huff_status_t st = batch_check(descs, count, op, prm);
+    if (st != HUFF_OK)
+        return st;
 
     huff_batch_plan_t *p = new (std::nothrow) huff_batch_plan_t();
     if (!p)
@@ -503,83 +585,21 @@ huff_status_t huff_batch_plan(const huff_batch_desc_t *descs, uint32_t count, hu
     p->op = op;
     p->params = prm;
     p->count = count;
-    cudaGetDevice(&p->device);
-
-    // host-side layout of the plan's device block
-    std::vector<BatchBuf> bufs(count);
-    std::vector<uint64_t> unit_base(count + 1, 0), item_base(count + 1, 0);
-    for (uint32_t i = 0; i < count; ++i) {
-        bufs[i] = {descs[i].d_in, descs[i].in_bytes, descs[i].d_out, descs[i].out_cap,
-                   reinterpret_cast<unsigned long long *>(descs[i].d_out_bytes),
-                   descs[i].d_status};
-        const uint64_t units = (descs[i].in_bytes + kUnitSymbols - 1) / kUnitSymbols;
-        unit_base[i + 1] = unit_base[i] + units;
-        item_base[i + 1] = item_base[i] + (units + kUnitsPerItem - 1) / kUnitsPerItem;
-    }
-    const uint64_t total_units = unit_base[count];
-    uint64_t off = 0;
-    const uint64_t o_ctl = off;
-    off = align256(off + sizeof(unsigned int) * kCtlWords + sizeof(int32_t));
-    const uint64_t o_bufs = off;
-    off = align256(off + sizeof(BatchBuf) * count);
-    const uint64_t o_ub = off;
-    off = align256(off + 8 * (count + 1));
-    const uint64_t o_ib = off;
-    off = align256(off + 8 * (count + 1));
-    const uint64_t o_di = off;
-    off = align256(off + 8 * (count + 1));
-    uint64_t o_uh = 0, o_uo = 0, o_cb = 0;
-    if (op == HUFF_BATCH_COMPRESS) {
-        o_uh = off;
-        off = align256(off + 512 * total_units);
-        o_uo = off;
-        off = align256(off + 8 * (total_units + count));
-        o_cb = off;
-        off = align256(off + sizeof(huff_codebook_t) * count);
-    }
-    if (cudaMalloc(&p->d_block, off) != cudaSuccess) {
+    BatchLayout L;
+    batch_layout(descs, count, op, L);
+    if (cudaMalloc(&p->d_block, L.bytes) != cudaSuccess) {
         free_plan(p);
         return HUFF_ERR_CUDA;
     }
-    uint8_t *blk = static_cast<uint8_t *>(p->d_block);
-    if (cudaMemcpy(blk + o_bufs, bufs.data(), sizeof(BatchBuf) * count, cudaMemcpyHostToDevice) !=
-            cudaSuccess ||
-        cudaMemcpy(blk + o_ub, unit_base.data(), 8 * (count + 1), cudaMemcpyHostToDevice) !=
-            cudaSuccess ||
-        cudaMemcpy(blk + o_ib, item_base.data(), 8 * (count + 1), cudaMemcpyHostToDevice) !=
-            cudaSuccess) {
+    std::vector<uint8_t> host(L.upload_bytes);
+    if (batch_upload(L, p->d_block, host.data(), 0) != cudaSuccess ||
+        cudaStreamSynchronize(0) != cudaSuccess) {
         free_plan(p);
         return HUFF_ERR_CUDA;
     }
-    BatchArgs &a = p->args;
-    a.bufs = reinterpret_cast<const BatchBuf *>(blk + o_bufs);
-    a.count = count;
-    a.cs = prm.chunk_symbols;
-    a.unit_base = reinterpret_cast<const uint64_t *>(blk + o_ub);
-    a.item_base = reinterpret_cast<const uint64_t *>(blk + o_ib);
-    a.dec_items = reinterpret_cast<uint64_t *>(blk + o_di);
-    a.unit_hist = op == HUFF_BATCH_COMPRESS ? reinterpret_cast<uint16_t *>(blk + o_uh) : nullptr;
-    a.unit_off =
-        op == HUFF_BATCH_COMPRESS ? reinterpret_cast<unsigned long long *>(blk + o_uo) : nullptr;
-    a.cbs = op == HUFF_BATCH_COMPRESS ? reinterpret_cast<huff_codebook_t *>(blk + o_cb) : nullptr;
-    a.min_lanes = prm.decode_lanes;
-    a.ctl = reinterpret_cast<unsigned int *>(blk + o_ctl);
-    a.fail = reinterpret_cast<int32_t *>(blk + o_ctl + sizeof(unsigned int) * kCtlWords);
-
-    // persistent grid: every CTA must be resident (cooperative launch)
-    int per_sm = 0;
-    cudaError_t err;
-    if (op == HUFF_BATCH_COMPRESS) {
-        err = cudaFuncSetAttribute(k_batch_compress, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                   kCompressSmem);
-        if (err == cudaSuccess)
-            err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch_compress,
-                                                                kBatchBlock, kCompressSmem);
-    } else {
-        err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch_decompress,
-                                                            kBatchBlock, 0);
-    }
-    if (err != cudaSuccess || per_sm < 1) {
+    p->args = batch_args(L, p->d_block, prm.chunk_symbols, prm.decode_lanes);
+    int per_sm = batch_occupancy(op);
+    if (per_sm < 1) {
         free_plan(p);
         return HUFF_ERR_CUDA;
     }
@@ -595,8 +615,8 @@ huff_status_t huff_batch_plan(const huff_batch_desc_t *descs, uint32_t count, hu
         }
         bool ok = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
         if (ok) {
-            const huff_status_t st = launch_batch(p, cs);
-            ok = cudaStreamEndCapture(cs, &p->graph) == cudaSuccess && st == HUFF_OK;
+            const cudaError_t le = batch_launch(op, p->args, p->grid, cs);
+            ok = cudaStreamEndCapture(cs, &p->graph) == cudaSuccess && le == cudaSuccess;
         }
         if (ok)
             ok = cudaGraphInstantiate(&p->exec, p->graph, 0) == cudaSuccess;
@@ -623,7 +643,8 @@ huff_status_t huff_batch_run(huff_batch_plan_t *plan, huff_stream_t stream)
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     if (plan->exec)
         return cudaGraphLaunch(plan->exec, s) == cudaSuccess ? HUFF_OK : HUFF_ERR_CUDA;
-    return launch_batch(plan, s);
+    return batch_launch(plan->op, plan->args, plan->grid, s) == cudaSuccess ? HUFF_OK
+                                                                              : HUFF_ERR_CUDA;
 }
 
 huff_status_t huff_batch_info(const huff_batch_plan_t *plan, huff_batch_params_t *params,

@@ -64,6 +64,19 @@ __global__ void __launch_bounds__(kDecBlock) k_decode(DecodeArgs a)
 
     if (chain_failed(a.status))
         return;
+    // CTAs past the last task leave before building tables (block 0 always
+    // stays: it reports header errors)
+    if (blockIdx.x > 0 && a.bytes >= kHeaderBytes) {
+        const uint64_t n = *reinterpret_cast<const uint64_t *>(a.stream + 256);
+        const uint32_t cs = *reinterpret_cast<const uint32_t *>(a.stream + 264);
+        if (chunk_symbols_valid(cs)) {
+            const uint64_t chunks = n / cs + (n % cs != 0);
+            const uint32_t S = pick_split(chunks, a.min_chains);
+            const uint64_t tasks = (chunks + (32 / S) - 1) / (32 / S);
+            if ((uint64_t)blockIdx.x * (kDecBlock / 32) >= tasks)
+                return;
+        }
+    }
     StreamInfo si;
     if (!prepare<kDecBlock>(a.stream, a.bytes, a.out, a.cap, a.d_n, a.status,
                  blockIdx.x == 0 && threadIdx.x == 0, sh, si))
