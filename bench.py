@@ -150,6 +150,166 @@ def cpu_baseline(x):
                       f"1 thread, {dt:.1f} s"}
 
 
+def measure_batched(hg, synth, torch, count=4096):
+    """Config 3: `count` independent text buffers (log-uniform 1 KiB..4 MiB,
+    per-buffer seeds), one fused launch per batch (CUDA graph) vs one plain
+    call per buffer on one stream."""
+    from concurrent.futures import ThreadPoolExecutor
+    sizes = synth.log_uniform_sizes(count, seed=3, lo=1024, hi=4 << 20)
+    with ThreadPoolExecutor(16) as ex:
+        xs = list(ex.map(lambda i: synth.text(int(sizes[i]), synth.batch_seed(i)), range(count)))
+    total = float(sizes.sum())
+    ins = [torch.from_numpy(x).cuda() for x in xs]
+    outs = [torch.empty(hg.huff_max_stream_size(x.size), dtype=torch.uint8, device="cuda")
+            for x in xs]
+    plan = hg.BatchPlan(ins, outs, hg.HUFF_BATCH_COMPRESS)
+
+    def t_ms(fn, reps, warm):
+        for _ in range(warm):
+            fn()
+        torch.cuda.synchronize()
+        s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s.record()
+        for _ in range(reps):
+            fn()
+        e.record()
+        torch.cuda.synchronize()
+        return s.elapsed_time(e) / reps
+
+    tc = t_ms(plan.run, 10, 3)
+    nb = plan.out_bytes.cpu().numpy()
+    assert (plan.status.cpu().numpy() == 0).all()
+    streams = [outs[i][:int(nb[i])] for i in range(count)]
+    decs = [torch.empty(max(x.size, 16), dtype=torch.uint8, device="cuda") for x in xs]
+    dplan = hg.BatchPlan(streams, decs, hg.HUFF_BATCH_DECOMPRESS)
+    td = t_ms(dplan.run, 10, 3)
+    assert (dplan.status.cpu().numpy() == 0).all()
+    ok = all(torch.equal(decs[i][:xs[i].size], ins[i]) for i in range(count))
+    ws = torch.empty(hg.huff_workspace_size(int(sizes.max())), dtype=torch.uint8, device="cuda")
+    obs = torch.zeros(count, dtype=torch.int64, device="cuda")
+    sts = torch.zeros(count, dtype=torch.int32, device="cuda")
+    dns = torch.zeros(count, dtype=torch.int64, device="cuda")
+
+    def plain_c():
+        for i in range(count):
+            hg.huff_compress(ins[i], d_out=outs[i], d_out_bytes=obs[i:i + 1], d_ws=ws,
+                             d_status=sts[i:i + 1])
+
+    def plain_d():
+        for i in range(count):
+            hg.huff_decode(streams[i], int(nb[i]), d_out=decs[i], out_cap=xs[i].size,
+                           d_n=dns[i:i + 1], d_status=sts[i:i + 1])
+
+    pc = t_ms(plain_c, 2, 1)
+    pd = t_ms(plain_d, 2, 1)
+    info = plan.info()
+    plan.close()
+    dplan.close()
+    return {"workload": f"{count} text buffers, log-uniform 1 KiB-4 MiB, {total / 2**30:.3f} GiB",
+            "graph": info["graph"], "grid": info["grid"], "round_trip_ok": ok,
+            "compress_ms": tc, "compress_gbs": total / tc / 1e6,
+            "decompress_ms": td, "decompress_gbs": total / td / 1e6,
+            "plain_compress_ms": pc, "plain_decompress_ms": pd,
+            "speedup_compress": pc / tc, "speedup_decompress": pd / td}
+
+
+def measure_served(hg, synth, oracle, torch, loads=(20.0, 100.0), seconds=1.5, max_requests=3000):
+    """Config 5: open-loop Poisson arrivals of 50/50 compress/decompress
+    requests over a pool of 64 text buffers with log-uniform sizes
+    4 KiB..16 MiB (streams for decompression pre-made by the oracle), served
+    by the continuous-batching loop under an 8 GiB budget, vs the same trace
+    served one request at a time through the plain calls."""
+    import numpy as np
+    rng_sizes = synth.log_uniform_sizes(64, seed=5, lo=4096, hi=16 << 20)
+    pool = []
+    for i, n in enumerate(rng_sizes):
+        x = synth.text(int(n), 7000 + i)
+        st, s = oracle.compress(x)
+        assert st == 0
+        hx = torch.from_numpy(x).pin_memory()
+        hs = torch.from_numpy(s).pin_memory()
+        pool.append((x, s, hx, hs))
+    mean = float(np.mean([p[0].size for p in pool]))
+    srv = hg.Server()
+    results = []
+    for load in loads:
+        lam = load * 1e9 / mean
+        count = min(max_requests, max(200, int(lam * seconds)))
+        t_arr, op, _ = synth.poisson_trace(count, seed=5, lam=lam)
+        pick = (synth.log_uniform_sizes(count, seed=55, lo=1, hi=64) - 1).astype(np.int64) % 64
+        outs = [torch.empty(hg.huff_max_stream_size(pool[j][0].size) if o == 0 else pool[j][0].size,
+                            dtype=torch.uint8).pin_memory() for o, j in zip(op, pick)]
+        # served, open loop
+        import time
+        t0 = time.perf_counter()
+        tickets, lag = [], []
+        for i in range(count):
+            while time.perf_counter() - t0 < t_arr[i]:
+                pass
+            lag.append(time.perf_counter() - t0 - t_arr[i])
+            x, s, hx, hs = pool[pick[i]]
+            if op[i] == 0:
+                tickets.append(srv.submit(hg.HUFF_BATCH_COMPRESS, hx, outs[i]))
+            else:
+                tickets.append(srv.submit(hg.HUFF_BATCH_DECOMPRESS, hs, outs[i]))
+        res = [srv.wait(t, 600000) for t in tickets]
+        lat = [r["t_done"] - r["t_submit"] + lg for r, lg in zip(res, lag)]
+        span = max(r["t_done"] for r in res) - min(r["t_submit"] for r in res)
+        nbytes = sum(pool[j][0].size for j in pick)
+        bad = 0
+        for i, r in enumerate(res):
+            x, s, _, _ = pool[pick[i]]
+            ref = s if op[i] == 0 else x
+            if r["status"] != 0 or r["out_bytes"] != ref.size or \
+                    not np.array_equal(outs[i][:ref.size].numpy(), ref):
+                bad += 1
+            srv.release(tickets[i])
+        # plain, one request at a time, same arrival times
+        dev = torch.device("cuda")
+        cap = max(hg.huff_max_stream_size(p[0].size) for p in pool)
+        d_in = torch.empty(cap, dtype=torch.uint8, device=dev)
+        d_out = torch.empty(cap, dtype=torch.uint8, device=dev)
+        ws = torch.empty(hg.huff_workspace_size(max(p[0].size for p in pool)), dtype=torch.uint8,
+                         device=dev)
+        ob = torch.zeros(1, dtype=torch.int64, device=dev)
+        st = torch.zeros(1, dtype=torch.int32, device=dev)
+        plat = []
+        t0 = time.perf_counter()
+        for i in range(count):
+            now = time.perf_counter() - t0
+            if now < t_arr[i]:
+                while time.perf_counter() - t0 < t_arr[i]:
+                    pass
+            x, s, hx, hs = pool[pick[i]]
+            if op[i] == 0:
+                d_in[:x.size].copy_(hx, non_blocking=True)
+                hg.huff_compress(d_in[:x.size], d_out=d_out, d_out_bytes=ob, d_ws=ws, d_status=st)
+                m = int(ob.item())
+            else:
+                d_in[:s.size].copy_(hs, non_blocking=True)
+                hg.huff_decode(d_in[:s.size], s.size, d_out=d_out, out_cap=x.size, d_n=ob,
+                               d_status=st)
+                m = int(ob.item())
+            outs[i][:m].copy_(d_out[:m], non_blocking=True)
+            torch.cuda.synchronize()
+            plat.append(time.perf_counter() - t0 - t_arr[i])
+        pspan = time.perf_counter() - t0 - t_arr[0]
+        lat_ms = np.array(lat) * 1e3
+        plat_ms = np.array(plat) * 1e3
+        results.append({"offered_gbs": load, "requests": count,
+                        "served_gbs": nbytes / span / 1e9,
+                        "p50_ms": float(np.percentile(lat_ms, 50)),
+                        "p99_ms": float(np.percentile(lat_ms, 99)),
+                        "plain_gbs": nbytes / pspan / 1e9,
+                        "plain_p50_ms": float(np.percentile(plat_ms, 50)),
+                        "plain_p99_ms": float(np.percentile(plat_ms, 99)),
+                        "mismatches": bad})
+    srv.close()
+    return {"workload": "Poisson 50/50 compress/decompress, 64 text buffers log-uniform "
+                        "4 KiB-16 MiB, 8 GiB budget, 3 rounds in flight",
+            "mean_request_bytes": mean, "points": results}
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -261,6 +421,13 @@ def run_ours(args):
     clk = clocks.stop()
     if not ok:
         raise SystemExit("bench: end-to-end round trip failed")
+    del h_stream, h_out
+    batched = served = None
+    if rank == 0 and not args.no_batched:
+        batched = measure_batched(hg, synth, torch)
+    if rank == 0 and not args.no_served:
+        import oracle
+        served = measure_served(hg, synth, oracle, torch)
 
     if rank != 0:
         if dist is not None:
@@ -302,6 +469,8 @@ def run_ours(args):
                      "peak_source": f"{peak_src} copy bandwidth (MEASURED_PEAKS.json hbm_gbs)"
                      if peak_src == "measured" else "fallback 6.8 TB/s"},
         "kernels": kern,
+        "batched": batched,
+        "served": served,
         "cpu_baseline": base,
     }
     print(json.dumps(line), flush=True)
@@ -316,6 +485,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-baseline sample")
+    ap.add_argument("--no-batched", action="store_true", help="skip the batched measurement")
+    ap.add_argument("--no-served", action="store_true", help="skip the served measurement")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
