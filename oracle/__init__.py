@@ -10,6 +10,7 @@ paper is silent.
 """
 from __future__ import annotations
 
+import contextlib
 import ctypes
 import os
 import subprocess
@@ -44,35 +45,52 @@ def build(force: bool = False) -> str:
     return _LIB
 
 
+def _configure(lib):
+    u8p = ctypes.POINTER(ctypes.c_uint8)
+    u32p = ctypes.POINTER(ctypes.c_uint32)
+    u64p = ctypes.POINTER(ctypes.c_uint64)
+    u64 = ctypes.c_uint64
+    u32 = ctypes.c_uint32
+    lib.oracle_histogram.restype = None
+    lib.oracle_histogram.argtypes = [u8p, u64, u64p]
+    lib.oracle_code_lengths.restype = ctypes.c_int
+    lib.oracle_code_lengths.argtypes = [u64p, u8p]
+    lib.oracle_canonical_codes.restype = None
+    lib.oracle_canonical_codes.argtypes = [u8p, u32p]
+    lib.oracle_max_stream_size.restype = u64
+    lib.oracle_max_stream_size.argtypes = [u64, u32]
+    lib.oracle_chunk_offsets.restype = ctypes.c_int
+    lib.oracle_chunk_offsets.argtypes = [u8p, u64, u32, u8p, u64p, u64p]
+    lib.oracle_pack_bits.restype = ctypes.c_int
+    lib.oracle_pack_bits.argtypes = [u8p, u64, u8p, u32p, u64, u64p]
+    lib.oracle_encode.restype = ctypes.c_int
+    lib.oracle_encode.argtypes = [u8p, u64, u32, u8p, u8p, u64, u64p]
+    lib.oracle_compress.restype = ctypes.c_int
+    lib.oracle_compress.argtypes = [u8p, u64, u32, u8p, u64, u64p]
+    lib.oracle_decode.restype = ctypes.c_int
+    lib.oracle_decode.argtypes = [u8p, u64, u8p, u64, u64p]
+    return lib
+
+
 def _load():
     global _lib
     if _lib is None:
-        lib = ctypes.CDLL(build())
-        u8p = ctypes.POINTER(ctypes.c_uint8)
-        u32p = ctypes.POINTER(ctypes.c_uint32)
-        u64p = ctypes.POINTER(ctypes.c_uint64)
-        u64 = ctypes.c_uint64
-        u32 = ctypes.c_uint32
-        lib.oracle_histogram.restype = None
-        lib.oracle_histogram.argtypes = [u8p, u64, u64p]
-        lib.oracle_code_lengths.restype = ctypes.c_int
-        lib.oracle_code_lengths.argtypes = [u64p, u8p]
-        lib.oracle_canonical_codes.restype = None
-        lib.oracle_canonical_codes.argtypes = [u8p, u32p]
-        lib.oracle_max_stream_size.restype = u64
-        lib.oracle_max_stream_size.argtypes = [u64, u32]
-        lib.oracle_chunk_offsets.restype = ctypes.c_int
-        lib.oracle_chunk_offsets.argtypes = [u8p, u64, u32, u8p, u64p, u64p]
-        lib.oracle_pack_bits.restype = ctypes.c_int
-        lib.oracle_pack_bits.argtypes = [u8p, u64, u8p, u32p, u64, u64p]
-        lib.oracle_encode.restype = ctypes.c_int
-        lib.oracle_encode.argtypes = [u8p, u64, u32, u8p, u8p, u64, u64p]
-        lib.oracle_compress.restype = ctypes.c_int
-        lib.oracle_compress.argtypes = [u8p, u64, u32, u8p, u64, u64p]
-        lib.oracle_decode.restype = ctypes.c_int
-        lib.oracle_decode.argtypes = [u8p, u64, u8p, u64, u64p]
-        _lib = lib
+        _lib = _configure(ctypes.CDLL(build()))
     return _lib
+
+
+@contextlib.contextmanager
+def use_library(path: str):
+    """Route every call of this module to another build of ``huff_oracle.c``
+    (the mutation tests compile copies with one planted mistake) for the
+    duration of the ``with`` block."""
+    global _lib
+    saved = _load()
+    _lib = _configure(ctypes.CDLL(path))
+    try:
+        yield
+    finally:
+        _lib = saved
 
 
 def _p(a: np.ndarray, ct):

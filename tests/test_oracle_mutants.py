@@ -1,0 +1,108 @@
+"""Mutation check of the oracle's pins.
+
+Each case copies ``oracle/huff_oracle.c``, plants one plausible mistake in the
+copy (a reversed tie-break, a transposed bit order, an off-by-one in the chunk
+table, a dropped or extra term, a weakened validation rule), builds it with
+gcc into a temporary library, routes the ``oracle`` module to it and runs the
+pins of ``test_oracle_pins.py``.  At least one pin must fail for every
+mutant; a mutant that passes them all would mean the pins cannot tell that
+mistake from the method.  The planted mistakes stay in the temporary copy and
+never touch the committed oracle.  Every mutant keeps the oracle's memory
+accesses within the buffers it is given.
+"""
+import os
+import subprocess
+
+import pytest
+
+import oracle
+import test_oracle_pins as pins
+
+_SRC = os.path.join(os.path.dirname(oracle.__file__), "huff_oracle.c")
+
+# (name, text in huff_oracle.c, replacement)
+MUTANTS = [
+    ("tie_break_reversed", "a.w == b.w && a.id < b.id", "a.w == b.w && a.id > b.id"),
+    ("merged_weight_plus_one", "{a.w + b.w, next_id++}", "{a.w + b.w + 1, next_id++}"),
+    ("histogram_drops_first_byte", "hist[x[i]] += 1;", "hist[x[i]] += (i > 0);"),
+    ("depth_from_one", "int depth = 0;", "int depth = 1;"),
+    ("length_limit_off_by_one", "depth > ORACLE_MAX_CODE_LEN", "depth >= ORACLE_MAX_CODE_LEN"),
+    ("single_symbol_length_two", "len[last_leaf] = 1;", "len[last_leaf] = 2;"),
+    ("canonical_skips_codes", "next += 1;", "next += 1 + (L > 3);"),
+    ("canonical_shift_off", "next <<= (L - prev);", "next <<= (L - prev) + (L > 2);"),
+    ("pack_lsb_first", "words[pos >> 5] |= 1u << (31 - (pos & 31));",
+     "words[pos >> 5] |= 1u << (pos & 31);"),
+    ("chunk_offset_off_by_one", "off[i / cs] = pos;", "off[i / cs] = pos + (i > 0);"),
+    ("header_longest_field", "put_u32le(out + 268, max_len);", "put_u32le(out + 268, max_len + 1);"),
+    ("header_fields_swapped", "put_u32le(out + 264, cs);", "put_u32le(out + 264, (uint32_t)n);"),
+    ("decode_lsb_first", "((word >> (31 - (pos & 31))) & 1u)", "((word >> (pos & 31)) & 1u)"),
+    ("decode_kraft_only_upper", "if (kraft != ((uint64_t)1 << 32))", "if (kraft > ((uint64_t)1 << 32))"),
+    ("decode_no_longest_check", "if (max_len != max_field)", "if (0 && max_len != max_field)"),
+    ("decode_no_chunk_end_check", "if (c + 1 < chunks && pos != limit)", "if (0 && pos != limit)"),
+    ("decode_reports_n_minus_one", "*n_out = n;", "*n_out = n - (n > 0);"),
+]
+# Not listed: dropping the "offsets non-decreasing" rule is an equivalent
+# mutant -- a non-last chunk must end exactly on the next offset and holds at
+# least one code, so a decreasing offset is rejected by that rule anyway (with
+# the same status).  Loosening the capacity rule would let the copy write past
+# its output buffer, so it is not planted.
+
+
+def _pins():
+    """The pins, cheapest first; each is a zero-argument callable."""
+    out = [lambda nm=nm: pins.test_worked_example(nm) for nm in pins.all_names()]
+    out += [
+        pins.test_abracadabra_payload_bytes_little_endian,
+        lambda: pins.test_histogram_is_bincount(1000, 3),
+        pins.test_empty_and_single,
+        pins.test_fibonacci_length_boundary,
+        pins.test_kraft_equality,
+        pins.test_two_queue_equals_heap,
+        pins.test_canonical_matches_rfc1951_and_is_prefix_free,
+        lambda: pins.test_offsets_from_per_chunk_counts(1024),
+        pins.test_payload_independent_of_chunk_size,
+        pins.test_chunk_payload_equals_standalone_packing,
+        pins.test_capacity_errors,
+        pins.test_corrupt_streams,
+        pins.test_incomplete_code_is_rejected,
+        pins.test_single_symbol_stream_rejects_a_one_bit,
+        pins.test_shannon_bounds,
+    ]
+    out += [lambda c=c: pins.test_round_trip(c) for c in pins._inputs()]
+    out.append(pins.test_bruteforce_minimum_weighted_length)
+    return out
+
+
+def _build(tmp_path, name, old, new):
+    src = open(_SRC).read()
+    assert src.count(old) == 1, f"mutation site of {name} not unique"
+    d = tmp_path / name
+    d.mkdir()
+    c = d / "huff_oracle.c"
+    c.write_text(src.replace(old, new))
+    hdr = os.path.join(os.path.dirname(_SRC), "huff_oracle.h")
+    (d / "huff_oracle.h").write_text(open(hdr).read())
+    so = d / "libmutant.so"
+    subprocess.check_call(["gcc", "-O1", "-std=c99", "-fPIC", "-shared", "-o", str(so), str(c)])
+    return str(so)
+
+
+def test_unmutated_copy_passes_every_pin(tmp_path):
+    so = _build(tmp_path, "identity", "int depth = 0;", "int depth = 0;")
+    with oracle.use_library(so):
+        for pin in _pins():
+            pin()
+
+
+@pytest.mark.parametrize("name,old,new", MUTANTS, ids=[m[0] for m in MUTANTS])
+def test_mutant_fails_a_pin(tmp_path, name, old, new):
+    so = _build(tmp_path, name, old, new)
+    caught = None
+    with oracle.use_library(so):
+        for pin in _pins():
+            try:
+                pin()
+            except AssertionError as e:
+                caught = e
+                break
+    assert caught is not None, f"mutant {name} passes every pin"

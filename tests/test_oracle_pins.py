@@ -344,6 +344,20 @@ def test_corrupt_streams():
         assert st == oracle.ERR_CORRUPT, i
 
 
+def test_incomplete_code_is_rejected():
+    # a = "0", b = "10": Kraft sum 3/4 < 1.  The stream is otherwise well
+    # formed (every code read is a valid one), so only the rule "two or more
+    # codes fill the code space exactly" rejects it.
+    x = np.frombuffer(b"abbaab" * 5, dtype=np.uint8)
+    ln = np.zeros(256, dtype=np.uint8)
+    ln[ord("a")] = 1
+    ln[ord("b")] = 2
+    st, s, _ = oracle.encode(x, ln, 16)
+    assert st == oracle.OK
+    st, _, _ = oracle.decode(s)
+    assert st == oracle.ERR_CORRUPT
+
+
 def test_single_symbol_stream_rejects_a_one_bit():
     x = synth.single(100, 0x61)
     st, s = oracle.compress(x)
