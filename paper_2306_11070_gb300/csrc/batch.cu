@@ -349,7 +349,8 @@ __global__ void __launch_bounds__(kBatchBlock, 2) k_batch_decompress(BatchArgs a
         if (b != have) {
             __syncthreads();
             ready = dec::prepare<kBatchBlock>(B.in, B.in_bytes, B.out, B.out_cap, B.out_bytes,
-                                              B.status, it == a.dec_items[b] && tid == 0, sh, si);
+                                              B.status, it == a.dec_items[b] && tid == 0, sh,
+                                              reinterpret_cast<uint16_t *>(in_ring), si);
             if (ready)
                 S = dec::pick_split(si.chunks, a.min_lanes);
             have = b;

@@ -4,9 +4,9 @@
 //
 // Every CTA validates the header and builds the canonical decode tables in
 // shared memory from the 256 stored lengths:
-//  - a 2^12-entry lookup table; an entry holds up to two symbols whose codes
-//    both fit in the 12-bit window (sym0 | sym1 << 8 | len0 << 16 |
-//    total << 24 | count << 30), so text decodes ~1.8 symbols per lookup;
+//  - a 2^12-entry lookup table; an entry holds the bytes of up to three codes
+//    that fit in the 12-bit window, their total length, 8 x their number and
+//    the length of the first one, so text decodes ~2.3 symbols per lookup;
 //  - per length, the first canonical code and the index of its first symbol,
 //    for codes longer than 12 bits (searched by length).
 //
@@ -27,14 +27,18 @@
 //     offset; the last one takes the rest of the chunk's symbols;
 //  4. each sub-segment decodes its symbols again on the true path, checking
 //     every code and the chunk's bit limit.
-// Counting (1) and decoding (4) run in windows of 8 lookups with no per-lane
-// branching inside a window (only predication), so the 32 independent bit
-// streams of a warp stay converged.  Between windows each lane tops up a
+// Counting (1) and decoding (4) run in windows of 16 lookups.  A window far
+// from every lane's segment end runs with no checks and no per-lane branch
+// (warp-uniform); the others check each code.  Per lookup the unchecked
+// window does one shared-memory load of the table entry, two funnel shifts
+// to drop the bits (the entry word itself is the shift amount), and appends
+// the entry's symbol bytes to a register word that is stored to the lane's
+// output ring when it is complete.  Between windows each lane tops up a
 // 32-word input ring in shared memory with cp.async (4-byte copies, laid out
-// [word][lane] so a warp's reads and writes never share a bank) and flushes
-// a completed 16-byte half of its 32-byte output ring (same layout) with one
-// 16-byte global store.  The next input word is always preloaded, so the
-// shared-memory latency stays off the per-codeword dependency chain.  The
+// [word][lane] so a warp's reads and writes never share a bank) and stores
+// every completed 16-byte group of its 64-byte output ring (same layout)
+// with one 16-byte global store.  The next input word is always preloaded,
+// so the ring's latency stays off the per-codeword dependency chain.  The
 // decoded codeword sequence is exactly the sequential one, so the stream
 // checks are those of a sequential decoder.
 #include "decode_impl.cuh"
@@ -44,7 +48,7 @@ namespace {
 
 using namespace dec;
 
-constexpr int kDecBlock = 128;
+constexpr int kDecBlock = 256;
 
 struct DecodeArgs {
     const uint8_t *stream;
@@ -79,7 +83,8 @@ __global__ void __launch_bounds__(kDecBlock) k_decode(DecodeArgs a)
     }
     StreamInfo si;
     if (!prepare<kDecBlock>(a.stream, a.bytes, a.out, a.cap, a.d_n, a.status,
-                 blockIdx.x == 0 && threadIdx.x == 0, sh, si))
+                            blockIdx.x == 0 && threadIdx.x == 0, sh,
+                            reinterpret_cast<uint16_t *>(in_ring), si))
         return;
     const uint32_t S = pick_split(si.chunks, a.min_chains);
     const uint64_t tasks = (si.chunks + (32 / S) - 1) / (32 / S);

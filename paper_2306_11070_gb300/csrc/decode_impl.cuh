@@ -10,12 +10,21 @@ namespace dec {
 constexpr int kLutBits = 12;
 constexpr int kLutSize = 1 << kLutBits;
 constexpr int kInRing = 32;   // input ring: words per lane
-constexpr int kOutRing = 8;   // output ring: 32 bytes per lane
-constexpr int kWindow = 8;    // lookups between ring maintenance
+constexpr int kOutRing = 16;  // output ring: 64 bytes per lane
+constexpr int kWindow = 16;   // lookups between ring maintenance
+constexpr int kMaxPerLookup = 3;
+constexpr uint32_t kFull = 0xffffffffu;
 
-
+// Lookup table entry for a 12-bit window (first stream bit = MSB):
+//   .x  the bytes of up to three whole codes in the window, first code in
+//       the low byte, zero above the last one;
+//   .y  L | 8*ns << 8 | L0 << 16, with L the total length of the ns codes
+//       and L0 the length of the first one; 0 when the first code is longer
+//       than 12 bits (or the window starts with no code at all).
+// L sits in the low five bits so that .y can be passed as it is to a
+// wrap-mode funnel shift (which reads only those bits).
 struct Tables {
-    const uint32_t *lut;
+    const uint2 *lut;
     const uint32_t *count;
     const uint32_t *first;
     const uint32_t *start;
@@ -25,7 +34,7 @@ struct Tables {
 
 // Shared-memory state of one stream's decode tables.
 struct DecodeShared {
-    uint32_t lut[kLutSize];
+    uint2 lut[kLutSize];
     uint8_t len_s[256];
     uint8_t sorted[256];
     uint32_t count[kMaxCodeLen + 1];
@@ -49,10 +58,16 @@ struct StreamInfo {
     Tables T;
 };
 
-// Codes longer than the table: canonical search by length on a 32-bit window.
-__device__ __forceinline__ bool long_code(const Tables &T, uint64_t buf, uint32_t &L, uint32_t &sym)
+__device__ __forceinline__ uint2 lut_at(const uint2 *lut, uint32_t bh)
 {
-    const uint32_t v = (uint32_t)(buf >> 32);
+    // byte offset of entry (bh >> 20): one shift and one mask
+    const uint32_t off = (bh >> (32 - kLutBits - 3)) & ((kLutSize - 1) << 3);
+    return *reinterpret_cast<const uint2 *>(reinterpret_cast<const char *>(lut) + off);
+}
+
+// Codes longer than the table: canonical search by length on a 32-bit window.
+__device__ __forceinline__ bool long_code(const Tables &T, uint32_t v, uint32_t &L, uint32_t &sym)
+{
     for (uint32_t l = kLutBits + 1; l <= T.max_len; ++l) {
         const uint32_t cv = v >> (32 - l);
         if (T.count[l] && cv - T.first[l] < T.count[l]) {
@@ -64,10 +79,9 @@ __device__ __forceinline__ bool long_code(const Tables &T, uint64_t buf, uint32_
     return false;
 }
 
-// Bit reader over the payload's u32 words.  Words come in blocks of four
-// (two 8-byte loads); the block after the current one is always in flight,
-// so a register is never read right after its load was issued, and an L2
-// prefetch runs 256 bytes ahead.  Words past the payload read as zero.
+// Bit reader over the payload's u32 words straight from global memory (used
+// by the short settle walks).  Words come in blocks of four; the block after
+// the current one is always in flight.  Words past the payload read as zero.
 struct Reader {
     const uint2 *pairs;
     uint64_t nwords;
@@ -100,8 +114,6 @@ struct Reader {
             c1 = n1;
             load_block(next_blk, n0, n1);
             ++next_blk;
-            if ((next_blk & 7) == 0 && 4 * (next_blk + 16) < nwords)
-                asm volatile("prefetch.global.L2 [%0];" ::"l"(pairs + 2 * (next_blk + 16)));
         }
         return w;
     }
@@ -146,11 +158,19 @@ __device__ __forceinline__ void cp_async_wait()
 
 // Bit stream of one lane fed through its column of the warp's input ring
 // (word slot w of lane l at ring[w * 32 + l]).  Word indices are relative to
-// w0, the payload word that holds the chunk's first bit.  Invariants: after
-// every top-up at least 25 words are requested beyond the next one to read,
-// groups are 4 words, and the two most recent groups may still be in flight,
-// so the >= 9 words a window can touch have landed.
-struct RingStream {
+// w0, the payload word that holds the chunk's first bit.
+//
+// The bit buffer bh:bl holds `have` valid bits, left-aligned.  `have` is
+// kept in the low six bits of H (0 <= have <= 63); the bits above are junk:
+// consume() subtracts a whole table word whose low five bits are the length,
+// so the junk never reaches the low six bits, and the wrap-mode shifts read
+// only the low five.
+//
+// Ring invariant: after every top-up more than kInRing - 4 words are
+// requested beyond the next one to read, in groups of 4, and the two most
+// recent groups may still be in flight; so the 1 + 17 words that one window
+// (at most 16 codes of <= 32 bits) can touch have landed.
+struct Bits {
     uint32_t *col;          // this lane's column
     const uint32_t *words;  // payload
     uint64_t nwords;
@@ -158,8 +178,8 @@ struct RingStream {
     uint32_t widx;    // next word to move into the bit buffer
     uint32_t fidx;    // next word to request
     uint32_t nxt;     // word widx, preloaded
-    uint32_t bh, bl;  // bit buffer, valid bits left-aligned in bh:bl
-    int have;
+    uint32_t bh, bl;  // bit buffer
+    uint32_t H;       // have in the low six bits
 
     __device__ __forceinline__ void fetch4()
     {
@@ -174,9 +194,7 @@ struct RingStream {
     }
     __device__ __forceinline__ void top_up()
     {
-        if (fidx - widx <= kInRing - 8)
-            fetch4();
-        if (fidx - widx <= kInRing - 8)
+        while (fidx - widx <= (uint32_t)kInRing - 4)
             fetch4();
     }
     // start at bit `pbit` counted from the first bit of word w0
@@ -196,74 +214,100 @@ struct RingStream {
         const uint32_t sh = pbit & 31;
         bh = col[(widx & (kInRing - 1)) * 32] << sh;
         bl = 0;
-        have = 32 - (int)sh;
+        H = 32 - sh;
         ++widx;
         nxt = col[(widx & (kInRing - 1)) * 32];
     }
-    // top the buffer up to more than 32 valid bits
+    __device__ __forceinline__ uint32_t have() const { return H & 63u; }
+    // stream bits consumed so far, counted from the first bit of word w0
+    __device__ __forceinline__ uint32_t bitpos() const { return 32 * widx - have(); }
+    // top the buffer up to at least 32 valid bits
     __device__ __forceinline__ void refill()
     {
-        if (have <= 32) {
-            bh |= __funnelshift_rc(nxt, 0u, (uint32_t)have);  // nxt >> have (0 at 32)
-            bl |= nxt << (32 - have);
-            have += 32;
+        if ((H & 32u) == 0) {  // have < 32
+            bh |= __funnelshift_r(nxt, 0u, H);  // nxt >> have
+            bl |= __funnelshift_r(0u, nxt, H);  // nxt << (32 - have), 0 at have = 0
+            H += 32;
             ++widx;
             nxt = col[(widx & (kInRing - 1)) * 32];
         }
     }
-    __device__ __forceinline__ uint32_t peek12() const { return bh >> (32 - kLutBits); }
-    __device__ __forceinline__ uint64_t buf64() const { return ((uint64_t)bh << 32) | bl; }
-    // drop L < 32 bits
-    __device__ __forceinline__ void consume_small(uint32_t L)
+    // drop the L = (t & 31) bits of a table word t (1 <= L <= 31)
+    __device__ __forceinline__ void consume_t(uint32_t t)
     {
-        bh = __funnelshift_l(bl, bh, L);
-        bl <<= L;
-        have -= (int)L;
+        bh = __funnelshift_l(bl, bh, t);
+        bl = __funnelshift_l(0u, bl, t);
+        H -= t;
     }
     // drop L <= 32 bits
     __device__ __forceinline__ void consume(uint32_t L)
     {
         bh = __funnelshift_lc(bl, bh, L);
         bl = L >= 32 ? 0u : bl << L;
-        have -= (int)L;
+        H -= L;
+    }
+};
+
+// Output bytes of one lane assembled in a register and stored to its column
+// of the warp's output ring one word at a time (row r of lane l at
+// ring[r * 32 + l]; the ring holds kOutRing words).  `lo` holds the bytes of
+// the word being filled at its low end, `sh` = 8 * (bytes in lo), `R` = 32 *
+// (ring row of that word).  Bytes above the filled ones are zero.
+struct OutWord {
+    uint32_t lo, sh, R;
+
+    __device__ __forceinline__ void start(uint32_t q)
+    {
+        lo = 0;
+        sh = (q & 3u) * 8;
+        R = ((q >> 2) & (kOutRing - 1)) * 32;
+    }
+    // append the bytes of y (zero above its ns8/8 bytes)
+    __device__ __forceinline__ void emit(uint32_t *col, uint32_t y, uint32_t ns8)
+    {
+        lo |= __funnelshift_l(0u, y, sh);        // y << sh
+        const uint32_t hi = __funnelshift_l(y, 0u, sh);  // y >> (32 - sh), 0 at sh = 0
+        sh += ns8;
+        col[R] = lo;
+        const uint32_t t = sh & 32u;  // 32 when the word is complete
+        lo = __funnelshift_rc(lo, hi, t);
+        R = (R + t) & (kOutRing * 32 - 1);
+        sh ^= t;
+    }
+    // output position, given the position q0 and ring row R0 at some earlier
+    // point less than kOutRing words back
+    __device__ __forceinline__ uint32_t pos_from(uint32_t q0, uint32_t R0) const
+    {
+        const uint32_t rows = ((R - R0) & (kOutRing * 32 - 1)) >> 5;
+        return ((q0 >> 2) + rows) * 4 + (sh >> 3);
     }
 };
 
 // Count codewords from bit `pos` (relative to the chunk's first bit `cbase`)
-// until the first boundary at or past `stop`.  Bit i of bmap is set when a
-// codeword starts at pos0 + i (i < 64).  Invalid bits (possible off the true
-// path) count as 1-bit codewords.
+// until the first boundary at or past `stop`, from global memory.  Invalid
+// bits (possible off the true path) count as 1-bit codewords.
 __device__ __forceinline__ void count_codes(const Tables &T, const uint8_t *pay, uint64_t nw,
                                             uint64_t cbase, uint32_t pos, uint32_t stop,
-                                            uint32_t &n, uint32_t &e, uint64_t &bmap)
+                                            uint32_t &n, uint32_t &e)
 {
-    const uint32_t pos0 = pos;
     uint32_t cnt = 0;
-    bmap = 1;
     if (pos < stop) {
         Reader rd;
         rd.init(pay, nw, cbase + pos);
         while (pos < stop) {
             rd.refill();
-            const uint32_t ent = T.lut[rd.buf >> (64 - kLutBits)];
-            uint32_t ns = ent >> 30, L = (ent >> 24) & 31u;
-            if (ns == 0) {
+            const uint2 ent = T.lut[rd.buf >> (64 - kLutBits)];
+            uint32_t L = ent.y & 31u, ns = (ent.y >> 11) & 31u;
+            if (ent.y == 0) {
                 uint32_t sym;
-                if (!long_code(T, rd.buf, L, sym))
+                if (!long_code(T, (uint32_t)(rd.buf >> 32), L, sym))
                     L = 1;
                 ns = 1;
-            } else if (ns == 2) {
-                const uint32_t L0 = (ent >> 16) & 31u;
-                if (pos + L0 >= stop) {
-                    ns = 1;
-                    L = L0;
-                } else if (pos + L0 - pos0 < 64) {
-                    bmap |= 1ull << (pos + L0 - pos0);
-                }
+            } else if (ns > 1 && pos + L >= stop) {  // later codes may start past stop
+                L = (ent.y >> 16) & 31u;
+                ns = 1;
             }
             pos += L;
-            if (pos - pos0 < 64)
-                bmap |= 1ull << (pos - pos0);
             cnt += ns;
             rd.consume(L);
         }
@@ -272,7 +316,7 @@ __device__ __forceinline__ void count_codes(const Tables &T, const uint8_t *pay,
     e = pos;
 }
 
-// Sub-segment [g, stop) was counted from g (cnt codewords, exit e, early
+// Sub-segment [g, stop) was counted from g (cnt1 codewords, exit e1, early
 // boundaries bmap).  Given its true entry point, walk the true path one
 // codeword at a time until it lands on one of the recorded boundaries: from
 // there both paths are the same codeword sequence, so only the codewords
@@ -305,28 +349,30 @@ __device__ __forceinline__ void settle_segment(const Tables &T, const uint8_t *p
             started = true;
         }
         rd.refill();
-        const uint32_t ent = T.lut[rd.buf >> (64 - kLutBits)];
-        uint32_t L = (ent >> 16) & 31u;  // first code only: every boundary matters
-        if ((ent >> 30) == 0) {
+        const uint2 ent = T.lut[rd.buf >> (64 - kLutBits)];
+        uint32_t L = (ent.y >> 16) & 31u;  // first code only: every boundary matters
+        if (ent.y == 0) {
             uint32_t sym;
-            if (!long_code(T, rd.buf, L, sym))
+            if (!long_code(T, (uint32_t)(rd.buf >> 32), L, sym))
                 L = 1;
         }
         pos += L;
         ++steps;
         rd.consume(L);
     }
-    uint64_t unused;
-    count_codes(T, pay, nw, cbase, entry, stop, cnt, e, unused);
+    count_codes(T, pay, nw, cbase, entry, stop, cnt, e);
 }
 
 // Validate the stream header and build the decode tables of one stream in
 // shared memory (all NT threads of the CTA take part; `reporter` writes *d_n
-// and the header errors).  Returns true when there are chunks to decode.
+// and the header errors).  `scratch` is shared memory for kLutSize u16 that
+// is free while the tables are built.  Returns true when there are chunks to
+// decode.
 template <int NT>
 __device__ __forceinline__ bool prepare(const uint8_t *stream_in, uint64_t bytes, uint8_t *out,
                                         uint64_t cap, unsigned long long *d_n, int32_t *status,
-                                        bool reporter, DecodeShared &sh, StreamInfo &si)
+                                        bool reporter, DecodeShared &sh, uint16_t *scratch,
+                                        StreamInfo &si)
 {
     const int tid = threadIdx.x;
     const uint8_t *stream = stream_in;
@@ -414,42 +460,44 @@ __device__ __forceinline__ bool prepare(const uint8_t *stream_in, uint64_t bytes
         }
     }
     __syncthreads();
-    // pass 1: the sh.first code of every 12-bit window
+    // pass 1: the first code of every 12-bit window, sym | L << 8 (0: none)
     const uint32_t lut_len = max_len < (uint32_t)kLutBits ? max_len : (uint32_t)kLutBits;
     for (int v = tid; v < kLutSize; v += NT) {
         uint32_t ent = 0;
         for (uint32_t L = 1; L <= lut_len; ++L) {
             const uint32_t c = (uint32_t)v >> (kLutBits - L);
             if (sh.count[L] && c - sh.first[L] < sh.count[L]) {
-                ent = sh.sorted[sh.start[L] + c - sh.first[L]] | (L << 16) | (L << 24) | (1u << 30);
+                ent = sh.sorted[sh.start[L] + c - sh.first[L]] | (L << 8);
                 break;
             }
+        }
+        scratch[v] = (uint16_t)ent;
+    }
+    __syncthreads();
+    // pass 2: append the following codes while they fit in the window
+    for (int v = tid; v < kLutSize; v += NT) {
+        const uint32_t e0 = scratch[v];
+        uint2 ent = make_uint2(0u, 0u);
+        if (e0) {
+            const uint32_t L0 = e0 >> 8;
+            uint32_t syms = e0 & 0xffu, tot = L0, ns = 1;
+#pragma unroll
+            for (int k = 1; k < kMaxPerLookup; ++k) {
+                if (ns == (uint32_t)k && tot < (uint32_t)kLutBits) {
+                    const uint32_t e1 = scratch[((uint32_t)v << tot) & (kLutSize - 1)];
+                    const uint32_t L1 = e1 >> 8;
+                    if (e1 && tot + L1 <= (uint32_t)kLutBits) {
+                        syms |= (e1 & 0xffu) << (8 * k);
+                        tot += L1;
+                        ++ns;
+                    }
+                }
+            }
+            ent = make_uint2(syms, tot | ((8 * ns) << 8) | (L0 << 16));
         }
         sh.lut[v] = ent;
     }
     __syncthreads();
-    // pass 2: append a second code when it fits in the rest of the window
-    uint32_t ent2[kLutSize / NT];
-#pragma unroll
-    for (int i = 0; i < kLutSize / NT; ++i) {
-        const int v = tid + i * NT;
-        uint32_t ent = sh.lut[v];
-        const uint32_t L0 = (ent >> 16) & 31u;
-        if (ent && L0 < (uint32_t)kLutBits) {
-            const uint32_t nxt = sh.lut[((uint32_t)v << L0) & (kLutSize - 1)];
-            const uint32_t L1 = (nxt >> 16) & 31u;
-            if (nxt && L0 + L1 <= (uint32_t)kLutBits)
-                ent = (ent & 0xffu) | ((nxt & 0xffu) << 8) | (L0 << 16) | ((L0 + L1) << 24) |
-                      (2u << 30);
-        }
-        ent2[i] = ent;
-    }
-    __syncthreads();
-#pragma unroll
-    for (int i = 0; i < kLutSize / NT; ++i)
-        sh.lut[tid + i * NT] = ent2[i];
-    __syncthreads();
-
 
     const uint64_t pay_words = (bytes - kHeaderBytes - 8 * chunks) / 4;
     const uint64_t pbits = 32 * pay_words;
@@ -483,14 +531,33 @@ __device__ __forceinline__ uint32_t pick_split(uint64_t chunks, uint32_t min_cha
     return S;
 }
 
+// Store the complete 16-byte groups of [fl, q) from the output ring.
+__device__ __forceinline__ void flush_groups(uint8_t *ob, const uint32_t *col, uint32_t &fl,
+                                             uint32_t q)
+{
+    const uint8_t *colb = reinterpret_cast<const uint8_t *>(col);
+    uint32_t hs = fl & ~15u;
+    while (q >= hs + 16) {
+        if (fl == hs) {
+            const uint32_t *h = col + ((hs >> 2) & (kOutRing - 1)) * 32;
+            *reinterpret_cast<uint4 *>(ob + hs) = make_uint4(h[0], h[32], h[64], h[96]);
+        } else {
+            for (uint32_t b = fl; b < hs + 16; ++b)
+                ob[b] = colb[((b >> 2) & (kOutRing - 1)) * 128 + (b & 3u)];
+        }
+        hs += 16;
+        fl = hs;
+    }
+}
+
 // Decode warp task `task` of stream si with S lanes per chunk (32/S chunks
 // per warp).  in_col / out_col: this lane's column of the warp's rings.
 // Returns true (warp-uniform) if the stream is corrupt.
 __device__ __forceinline__ bool decode_task(const StreamInfo &si, uint32_t S, uint64_t task,
-                                        uint32_t *in_col, uint32_t *out_col)
+                                            uint32_t *in_col, uint32_t *out_col)
 {
     const Tables &T = si.T;
-    const uint32_t *lut = T.lut;
+    const uint2 *lut = T.lut;
     const uint64_t n = si.n, chunks = si.chunks, pbits = si.pbits, pay_words = si.pay_words;
     const uint32_t cs = si.cs;
     const uint64_t *offs = si.offs;
@@ -499,7 +566,7 @@ __device__ __forceinline__ bool decode_task(const StreamInfo &si, uint32_t S, ui
     const uint32_t G = 32 / S;
     const uint32_t k = (uint32_t)lane & (S - 1);
     const uint32_t grp = (uint32_t)lane / S;
-    uint8_t *out_colb = reinterpret_cast<uint8_t *>(out_col);
+    const uint8_t *out_colb = reinterpret_cast<const uint8_t *>(out_col);
     const uint64_t c = task * G + grp;
     const bool valid = c < chunks;
     bool bad = false;
@@ -521,58 +588,97 @@ __device__ __forceinline__ bool decode_task(const StreamInfo &si, uint32_t S, ui
         }
     }
     const bool work = valid && !bad;
+    const uint32_t *pw = reinterpret_cast<const uint32_t *>(pay);
+    const uint32_t b0 = (uint32_t)(cbase & 31);  // chunk bit 0 within word w0
 
     // 1. count each sub-segment but the last from its cut point
     uint32_t cnt1 = 0, e1 = g;
     uint64_t bmap = 1;
     if (S > 1) {  // uniform: every lane of the warp takes this branch
-        RingStream rs;
+        Bits rs = {};
         bool act = work && k + 1 < S && g < stop;
         if (act)
-            rs.init(in_col, reinterpret_cast<const uint32_t *>(pay), pay_words, cbase >> 5,
-                    (uint32_t)(cbase & 31) + g);
+            rs.init(in_col, pw, pay_words, cbase >> 5, b0 + g);
         uint32_t pos = g;
-        while (__any_sync(0xffffffffu, act)) {
-#pragma unroll
-            for (int j = 0; j < kWindow; ++j) {
-                if (act) {
-                    if ((j & 1) == 0)
-                        rs.refill();  // two table codes use at most 24 of > 32 bits
-                    const uint32_t ent = lut[rs.peek12()];
-                    uint32_t ns = ent >> 30, L = (ent >> 24) & 31u;
-                    if (ns == 0) {  // longer than the table (rare)
-                        rs.refill();
-                        uint32_t sym;
-                        if (!long_code(T, rs.buf64(), L, sym))
-                            L = 1;
-                        ns = 1;
-                        rs.consume(L);
-                        rs.refill();  // keep >= 12 bits for the next lookup
-                    } else {
-                        if (ns == 2) {
-                            const uint32_t L0 = (ent >> 16) & 31u;
-                            if (pos + L0 >= stop) {
-                                ns = 1;
-                                L = L0;
-                            } else if (pos + L0 - g < 64) {
-                                bmap |= 1ull << (pos + L0 - g);
-                            }
-                        }
-                        rs.consume_small(L);
-                    }
-                    pos += L;
-                    if (pos - g < 64)
-                        bmap |= 1ull << (pos - g);
-                    cnt1 += ns;
-                    act = pos < stop;
+        // 1a. code by code through the first 64 bits, recording the boundaries
+        bool head = act;
+        while (__any_sync(kFull, head)) {
+            if (head) {
+                rs.refill();
+                const uint2 ent = lut_at(lut, rs.bh);
+                uint32_t L = (ent.y >> 16) & 31u;
+                if (ent.y == 0) {
+                    uint32_t sym;
+                    if (!long_code(T, rs.bh, L, sym))
+                        L = 1;
                 }
+                rs.consume(L);
+                rs.refill();
+                pos += L;
+                ++cnt1;
+                if (pos - g < 64)
+                    bmap |= 1ull << (pos - g);
+                head = pos - g < 64 && pos < stop;
+                act = pos < stop;
+            }
+        }
+        // 1b. windows of table lookups, several codes per lookup
+        uint32_t cnt8 = 0;
+        while (__any_sync(kFull, act)) {
+            const bool easy = stop - pos >= 32 * kWindow;
+            if (__all_sync(kFull, easy || !act)) {
+#pragma unroll
+                for (int j = 0; j < kWindow; ++j) {
+                    if (act) {
+                        if ((j & 1) == 0)
+                            rs.refill();  // two lookups use at most 24 of >= 32 bits
+                        const uint2 ent = lut_at(lut, rs.bh);
+                        if (ent.y == 0) {  // longer than the table (rare)
+                            rs.refill();
+                            uint32_t L, sym;
+                            if (!long_code(T, rs.bh, L, sym))
+                                L = 1;
+                            rs.consume(L);
+                            rs.refill();
+                            cnt8 += 8;
+                        } else {
+                            rs.consume_t(ent.y);
+                            cnt8 += __byte_perm(ent.y, 0u, 0x4441);  // 8 * ns
+                        }
+                    }
+                }
+            } else {
+#pragma unroll 1
+                for (int j = 0; j < kWindow; ++j) {
+                    if (act) {
+                        rs.refill();
+                        const uint2 ent = lut_at(lut, rs.bh);
+                        uint32_t L = (ent.y >> 16) & 31u;  // one code at a time
+                        if (ent.y == 0) {
+                            rs.refill();
+                            uint32_t sym;
+                            if (!long_code(T, rs.bh, L, sym))
+                                L = 1;
+                        }
+                        rs.consume(L);
+                        cnt8 += 8;
+                        act = rs.bitpos() - b0 < stop;
+                    }
+                }
+            }
+            if (act) {
+                pos = rs.bitpos() - b0;
+                act = pos < stop;
             }
             if (act)
                 rs.top_up();
             cp_async_wait<2>();
         }
         cp_async_wait<0>();  // the ring is reused below
-        e1 = pos;
+        if (work && k + 1 < S && g < stop) {
+            cnt1 += cnt8 >> 3;
+            e1 = rs.bitpos() - b0;
+        }
     }
     uint32_t cnt = cnt1, e = e1;
     // 2. settle the entry points: all at once on the exits just counted,
@@ -581,9 +687,9 @@ __device__ __forceinline__ bool decode_task(const StreamInfo &si, uint32_t S, ui
     uint32_t used = g;
     bool first = true;
     for (;;) {
-        const uint32_t pe = __shfl_up_sync(0xffffffffu, e, 1, S);
+        const uint32_t pe = __shfl_up_sync(kFull, e, 1, S);
         const bool redo = work && k > 0 && (first || pe != used);
-        if (!__any_sync(0xffffffffu, redo))
+        if (!__any_sync(kFull, redo))
             break;
         if (redo) {
             used = pe;
@@ -598,7 +704,7 @@ __device__ __forceinline__ bool decode_task(const StreamInfo &si, uint32_t S, ui
     const uint32_t own = (work && k + 1 < S) ? cnt : 0u;
     uint32_t x = own;
     for (uint32_t d = 1; d < S; d <<= 1) {
-        const uint32_t y = __shfl_up_sync(0xffffffffu, x, d, S);
+        const uint32_t y = __shfl_up_sync(kFull, x, d, S);
         if (k >= d)
             x += y;
     }
@@ -610,85 +716,103 @@ __device__ __forceinline__ bool decode_task(const StreamInfo &si, uint32_t S, ui
 
     // 4. decode on the true path and write the bytes
     {
-        RingStream rs;
+        Bits rs = {};
+        OutWord ow = {};
         bool act = todo > 0;
         uint8_t *const ob = si.out + c * cs;  // chunk output, 16-byte aligned
         const uint32_t qend = O + todo;
         uint32_t pos = entry, q = O, fl = O;  // q: next byte, fl: first unflushed byte
+        ow.start(O);
         if (act)
-            rs.init(in_col, reinterpret_cast<const uint32_t *>(pay), pay_words, cbase >> 5,
-                    (uint32_t)(cbase & 31) + entry);
-        while (__any_sync(0xffffffffu, act)) {
-            // a window far from the segment's end needs no per-code checks:
-            // at most 16 symbols and 8 x 32 bits
-            const bool easy = act && qend - q >= 2 * kWindow && lim - pos >= 32 * kWindow;
+            rs.init(in_col, pw, pay_words, cbase >> 5, b0 + entry);
+        while (__any_sync(kFull, act)) {
+            // far from the segment's end a window needs no per-code checks:
+            // at most 3 * 16 symbols and 16 x 32 bits.  The unchecked window
+            // runs only when every lane of the warp is in that state, so it
+            // needs no per-lane predicate either.
+            const bool easy =
+                act && qend - q >= kMaxPerLookup * kWindow && lim - pos >= 32 * kWindow;
+            const uint32_t q0 = q, R0 = ow.R;
+            if (__all_sync(kFull, easy)) {
 #pragma unroll
-            for (int j = 0; j < kWindow; ++j) {
-                if (act) {
+                for (int j = 0; j < kWindow; ++j) {
                     if ((j & 1) == 0)
-                        rs.refill();  // two table codes use at most 24 of > 32 bits
-                    const uint32_t ent = lut[rs.peek12()];
-                    uint32_t ns = ent >> 30, L = (ent >> 24) & 31u, sy = ent;
-                    if (ns == 0) {  // longer than the table (rare)
+                        rs.refill();  // two lookups use at most 24 of >= 32 bits
+                    const uint2 ent = lut_at(lut, rs.bh);
+                    if (ent.y == 0) {  // longer than the table (rare)
                         rs.refill();
-                        uint32_t sym = 0;
-                        if (!long_code(T, rs.buf64(), L, sym)) {
-                            bad = true;
-                            L = 0;
+                        uint32_t L = 0, sym = 0;
+                        if (!long_code(T, rs.bh, L, sym)) {
+                            bad = true;  // the rest of the window is not flushed
+                            act = false;
                         }
-                        ns = 1;
-                        sy = sym;
-                        if (!easy && pos + L > lim)
-                            bad = true;
                         rs.consume(L);
-                        rs.refill();  // keep >= 12 bits for the next lookup
+                        rs.refill();
+                        ow.emit(out_col, sym, 8);
                     } else {
-                        if (!easy && ns == 2 && (qend - q < 2 || pos + L > lim)) {
-                            ns = 1;
-                            L = (ent >> 16) & 31u;
-                        }
-                        if (!easy && pos + L > lim)
-                            bad = true;
-                        rs.consume_small(L);
+                        rs.consume_t(ent.y);
+                        ow.emit(out_col, ent.x, __byte_perm(ent.y, 0u, 0x4441));
                     }
-                    // both bytes always: an unused second byte is overwritten
-                    // by the next symbol and never flushed
-                    const uint32_t q1 = q + 1;
-                    out_colb[((q & 31u) >> 2) * 128 + (q & 3u)] = (uint8_t)sy;
-                    out_colb[((q1 & 31u) >> 2) * 128 + (q1 & 3u)] = (uint8_t)(sy >> 8);
-                    q += ns;
-                    pos += L;
-                    if (!easy)
+                }
+            } else {
+#pragma unroll 1
+                for (int j = 0; j < kWindow; ++j) {
+                    if (act) {
+                        rs.refill();
+                        const uint2 ent = lut_at(lut, rs.bh);
+                        uint32_t L, ns8, y;
+                        if (ent.y == 0) {
+                            rs.refill();
+                            uint32_t sym = 0;
+                            L = 0;
+                            if (!long_code(T, rs.bh, L, sym))
+                                bad = true;
+                            ns8 = 8;
+                            y = sym;
+                        } else {
+                            L = ent.y & 31u;
+                            ns8 = (ent.y >> 8) & 0xffu;
+                            y = ent.x;
+                            if (q + (ns8 >> 3) > qend || pos + L > lim) {  // first code only
+                                L = (ent.y >> 16) & 31u;
+                                ns8 = 8;
+                                y &= 0xffu;
+                            }
+                        }
+                        if (pos + L > lim)
+                            bad = true;
+                        if (!bad) {
+                            rs.consume(L);
+                            ow.emit(out_col, y, ns8);
+                            q += ns8 >> 3;
+                            pos += L;
+                        }
                         act = !bad && q < qend;
+                    }
                 }
             }
-            if (easy)
-                act = !bad && q < qend;
-            if (act)
-                rs.top_up();
+            q = ow.pos_from(q0, R0);
+            pos = rs.bitpos() - b0;
+            if (act) {
+                act = q < qend;
+                if (act)
+                    rs.top_up();
+            }
             cp_async_wait<2>();
-            // flush the half that holds `fl` once it is complete
-            const uint32_t hs = fl & ~15u;
-            if (!bad && q >= hs + 16) {
-                if (fl == hs) {
-                    const uint32_t *h = out_col + ((hs & 31u) >> 2) * 32;
-                    *reinterpret_cast<uint4 *>(ob + hs) = make_uint4(h[0], h[32], h[64], h[96]);
-                } else {
-                    for (uint32_t b = fl; b < hs + 16; ++b)
-                        ob[b] = out_colb[((b & 31u) >> 2) * 128 + (b & 3u)];
-                }
-                fl = hs + 16;
-            }
+            if (!bad)
+                flush_groups(ob, out_col, fl, q);
         }
         cp_async_wait<0>();
         if (!bad) {
+            if (todo)
+                out_col[ow.R] = ow.lo;  // bytes carried over by the last emit
             for (uint32_t b = fl; b < q; ++b)
-                ob[b] = out_colb[((b & 31u) >> 2) * 128 + (b & 3u)];
+                ob[b] = out_colb[((b >> 2) & (kOutRing - 1)) * 128 + (b & 3u)];
             if (todo && final_seg && c + 1 < chunks && pos != lim)
                 bad = true;
         }
     }
-    return __any_sync(0xffffffffu, bad);
+    return __any_sync(kFull, bad);
 }
 
 }  // namespace dec
