@@ -5,8 +5,9 @@
 // Every CTA validates the header and builds the canonical decode tables in
 // shared memory from the 256 stored lengths:
 //  - a 2^12-entry lookup table; an entry holds the bytes of up to three codes
-//    that fit in the 12-bit window, their total length, 8 x their number and
-//    the length of the first one, so text decodes ~2.3 symbols per lookup;
+//    that fit in the 12-bit window, their total length and their number, so
+//    text decodes ~2.3 symbols per lookup; a byte table beside it holds the
+//    length of the first code alone;
 //  - per length, the first canonical code and the index of its first symbol,
 //    for codes longer than 12 bits (searched by length).
 //
@@ -27,17 +28,19 @@
 //     offset; the last one takes the rest of the chunk's symbols;
 //  4. each sub-segment decodes its symbols again on the true path, checking
 //     every code and the chunk's bit limit.
-// Counting (1) and decoding (4) run in windows of 16 lookups.  A window far
-// from every lane's segment end runs with no checks and no per-lane branch
-// (warp-uniform); the others check each code.  Per lookup the unchecked
-// window does one shared-memory load of the table entry, two funnel shifts
-// to drop the bits (the entry word itself is the shift amount), and appends
-// the entry's symbol bytes to a register word that is stored to the lane's
-// output ring when it is complete.  Between windows each lane tops up a
-// 32-word input ring in shared memory with cp.async (4-byte copies, laid out
-// [word][lane] so a warp's reads and writes never share a bank) and stores
-// every completed 16-byte group of its 64-byte output ring (same layout)
-// with one 16-byte global store.  The next input word is always preloaded,
+// Counting (1) and decoding (4) run in windows of lookups.  A window far
+// from every lane's segment end (32 lookups) runs with no checks and no
+// branch (warp-uniform); the others (16 lookups) check each code.  Per
+// lookup the unchecked window does one 4-byte shared-memory load of the table
+// entry, two funnel shifts to drop the bits (entry >> 24 is the shift
+// amount), and appends the entry's symbol bytes to a register word that is
+// stored to the lane's output ring when it is complete.  A code longer than
+// the table has an all-zero entry, which consumes and emits nothing: the
+// lane waits on it until the next window resolves it.  Between windows each
+// lane tops up a 32-word input ring in shared memory with cp.async (4-byte
+// copies, laid out [word][lane] so a warp's reads and writes never share a
+// bank) and stores every completed 16-byte group of its 128-byte output ring
+// (same layout) with one 16-byte global store.  The next input word is always preloaded,
 // so the ring's latency stays off the per-codeword dependency chain.  The
 // decoded codeword sequence is exactly the sequential one, so the stream
 // checks are those of a sequential decoder.

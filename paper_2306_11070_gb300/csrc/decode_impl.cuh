@@ -10,21 +10,24 @@ namespace dec {
 constexpr int kLutBits = 12;
 constexpr int kLutSize = 1 << kLutBits;
 constexpr int kInRing = 32;   // input ring: words per lane
-constexpr int kOutRing = 16;  // output ring: 64 bytes per lane
-constexpr int kWindow = 16;   // lookups between ring maintenance
+constexpr int kOutRing = 32;  // output ring: 128 bytes per lane
+constexpr int kWindow = 32;   // table lookups per unchecked window
+constexpr int kCheckedWindow = 12;  // lookups per checked window
 constexpr int kMaxPerLookup = 3;
 constexpr uint32_t kFull = 0xffffffffu;
 
-// Lookup table entry for a 12-bit window (first stream bit = MSB):
-//   .x  the bytes of up to three whole codes in the window, first code in
-//       the low byte, zero above the last one;
-//   .y  L | 8*ns << 8 | L0 << 16, with L the total length of the ns codes
-//       and L0 the length of the first one; 0 when the first code is longer
-//       than 12 bits (or the window starts with no code at all).
-// L sits in the low five bits so that .y can be passed as it is to a
-// wrap-mode funnel shift (which reads only those bits).
+// Lookup table entry for a 12-bit window (first stream bit = MSB), 32 bits:
+//   bits  0..23  the bytes of up to three whole codes in the window, first
+//                code in the low byte, zero above the last one;
+//   bits 24..29  L, the total length of those codes (1..12);
+//   bits 30..31  ns, their number (1..3);
+// and 0 when the window starts with a code longer than 12 bits (or with no
+// code at all).  So entry >> 24 = L + 64 * ns: its low five bits are L, as a
+// wrap-mode funnel shift wants them, and the rest is a multiple of 64.  The
+// length of the first code alone is in a second, byte-wide table.
 struct Tables {
-    const uint2 *lut;
+    const uint32_t *lut;
+    const uint8_t *len0;
     const uint32_t *count;
     const uint32_t *first;
     const uint32_t *start;
@@ -34,7 +37,8 @@ struct Tables {
 
 // Shared-memory state of one stream's decode tables.
 struct DecodeShared {
-    uint2 lut[kLutSize];
+    uint32_t lut[kLutSize];
+    uint8_t len0[kLutSize];
     uint8_t len_s[256];
     uint8_t sorted[256];
     uint32_t count[kMaxCodeLen + 1];
@@ -58,11 +62,60 @@ struct StreamInfo {
     Tables T;
 };
 
-__device__ __forceinline__ uint2 lut_at(const uint2 *lut, uint32_t bh)
+// Integer constants read from the constant bank.  A multiply by one of them
+// is an IMAD, which runs on the FMA pipe; adds, conditional adds and
+// constant shifts written that way leave the ALU pipe (which executes the
+// shifts, logic ops and compares, at half a warp per cycle) to the work only
+// it can do.  The values are not visible to the compiler, so it cannot turn
+// the multiplies back into shifts and adds.
+enum { kOne, kMinus1, kFour, kEight, k32, kMinus32, k128, kMinusTop8, kNumConst };
+static __constant__ uint32_t kc[kNumConst] = {1u, 0xffffffffu, 4u, 8u, 32u, 0xffffffe0u,
+                                              128u, 0xff000000u};
+__device__ __forceinline__ uint32_t imad(uint32_t a, uint32_t b, uint32_t c) { return a * b + c; }
+
+// Shared-memory accesses by 32-bit shared address.  The rings are accessed
+// only through these volatile forms (and cp.async), so their order is kept.
+__device__ __forceinline__ uint32_t lds(uint32_t a)
 {
-    // byte offset of entry (bh >> 20): one shift and one mask
-    const uint32_t off = (bh >> (32 - kLutBits - 3)) & ((kLutSize - 1) << 3);
-    return *reinterpret_cast<const uint2 *>(reinterpret_cast<const char *>(lut) + off);
+    uint32_t v;
+    asm volatile("ld.shared.u32 %0, [%1];" : "=r"(v) : "r"(a));
+    return v;
+}
+__device__ __forceinline__ uint32_t lds_u8(uint32_t a)
+{
+    uint32_t v;
+    asm volatile("ld.shared.u8 %0, [%1];" : "=r"(v) : "r"(a));
+    return v;
+}
+__device__ __forceinline__ void sts(uint32_t a, uint32_t v)
+{
+    asm volatile("st.shared.u32 [%0], %1;" ::"r"(a), "r"(v));
+}
+// predicated forms: the access happens only when `k` is nonzero (no branch)
+__device__ __forceinline__ void lds_if(uint32_t k, uint32_t a, uint32_t &v)
+{
+    asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.u32 p, %2, 0;\n\t@p ld.shared.u32 %0, [%1];\n\t}"
+                 : "+r"(v)
+                 : "r"(a), "r"(k));
+}
+__device__ __forceinline__ void sts_if(uint32_t k, uint32_t a, uint32_t v)
+{
+    asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.u32 p, %2, 0;\n\t@p st.shared.u32 [%0], %1;\n\t}"
+                 ::"r"(a), "r"(v), "r"(k));
+}
+// table entry of the 12-bit window at the top of bh.  Volatile like the ring
+// accesses, so that the order written below (each lookup's table load
+// before the previous lookup's ring store) reaches the compiled code:
+// a load cannot be moved above a shared store it might alias.
+__device__ __forceinline__ uint32_t lut_ld(uint32_t lut_s, uint32_t bh)
+{
+    uint32_t v;
+    asm volatile("ld.shared.u32 %0, [%1];" : "=r"(v) : "r"(imad(bh >> (32 - kLutBits), kc[kFour], lut_s)));
+    return v;
+}
+__device__ __forceinline__ uint32_t len0_at(const uint8_t *len0, uint32_t bh)
+{
+    return len0[bh >> (32 - kLutBits)];
 }
 
 // Codes longer than the table: canonical search by length on a 32-bit window.
@@ -143,9 +196,9 @@ struct Reader {
     }
 };
 
-__device__ __forceinline__ void cp_async4(uint32_t *dst, const uint32_t *src, bool valid)
+__device__ __forceinline__ void cp_async4(uint32_t dst, const uint32_t *src, bool valid)
 {
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(smem_u32(dst)), "l"(src),
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(dst), "l"(src),
                  "r"(valid ? 4 : 0)
                  : "memory");
 }
@@ -167,11 +220,15 @@ __device__ __forceinline__ void cp_async_wait()
 // only the low five.
 //
 // Ring invariant: after every top-up more than kInRing - 4 words are
-// requested beyond the next one to read, in groups of 4, and the two most
-// recent groups may still be in flight; so the 1 + 17 words that one window
-// (at most 16 codes of <= 32 bits) can touch have landed.
+// requested beyond the next one to read, in groups of 4, and the three most
+// recent groups may still be in flight; so the next 1 + 16 words have
+// landed, and one window moves at most 14 words into the bit buffer (a
+// checked window reads at most 12 codes of <= 32 bits, an unchecked one at
+// most one such code and 32 of <= 12 bits, and the buffer holds < 64 bits).
+// Requests never reach the slot of a word that has not been read.  Each
+// top-up also asks L2 for the line 64 words past the requests.
 struct Bits {
-    uint32_t *col;          // this lane's column
+    uint32_t col;           // shared address of this lane's column
     const uint32_t *words;  // payload
     uint64_t nwords;
     uint64_t w0;
@@ -181,13 +238,25 @@ struct Bits {
     uint32_t bh, bl;  // bit buffer
     uint32_t H;       // have in the low six bits
 
+    __device__ __forceinline__ uint32_t slot(uint32_t w) const { return col + (w & (kInRing - 1)) * 128; }
+    // request words fidx .. fidx+3 (fidx is a multiple of 4, so they fill
+    // ring rows (fidx & 31) .. +3 without wrapping)
     __device__ __forceinline__ void fetch4()
     {
+        const uint32_t d = slot(fidx);
+        const uint64_t aw = w0 + fidx;
+        if (aw + 4 <= nwords) {
+            const uint32_t *src = words + aw;
+            cp_async4(d, src, true);
+            cp_async4(d + 128, src + 1, true);
+            cp_async4(d + 256, src + 2, true);
+            cp_async4(d + 384, src + 3, true);
+        } else {
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            const uint64_t aw = w0 + fidx + j;
-            const bool ok = aw < nwords;
-            cp_async4(col + ((fidx + j) & (kInRing - 1)) * 32, words + (ok ? aw : 0), ok);
+            for (int j = 0; j < 4; ++j) {
+                const bool ok = aw + j < nwords;
+                cp_async4(d + 128 * j, words + (ok ? aw + j : 0), ok);
+            }
         }
         fidx += 4;
         cp_async_commit();
@@ -196,9 +265,12 @@ struct Bits {
     {
         while (fidx - widx <= (uint32_t)kInRing - 4)
             fetch4();
+        const uint64_t pf = w0 + fidx + 64;
+        if (pf < nwords)
+            asm volatile("prefetch.global.L2 [%0];" ::"l"(words + pf));
     }
     // start at bit `pbit` counted from the first bit of word w0
-    __device__ __forceinline__ void init(uint32_t *column, const uint32_t *pay, uint64_t nw,
+    __device__ __forceinline__ void init(uint32_t column, const uint32_t *pay, uint64_t nw,
                                          uint64_t word0, uint32_t pbit)
     {
         col = column;
@@ -206,38 +278,41 @@ struct Bits {
         nwords = nw;
         w0 = word0;
         widx = pbit >> 5;
-        fidx = widx;
+        fidx = widx & ~3u;
 #pragma unroll
         for (int r = 0; r < kInRing / 4; ++r)
             fetch4();
         cp_async_wait<0>();
         const uint32_t sh = pbit & 31;
-        bh = col[(widx & (kInRing - 1)) * 32] << sh;
+        bh = lds(slot(widx)) << sh;
         bl = 0;
         H = 32 - sh;
         ++widx;
-        nxt = col[(widx & (kInRing - 1)) * 32];
+        nxt = lds(slot(widx));
     }
     __device__ __forceinline__ uint32_t have() const { return H & 63u; }
     // stream bits consumed so far, counted from the first bit of word w0
     __device__ __forceinline__ uint32_t bitpos() const { return 32 * widx - have(); }
-    // top the buffer up to at least 32 valid bits
+    // top the buffer up to at least 32 valid bits.  Straight-line code: k is
+    // 1 when have < 32, else 0, every update is a multiply-add by k (the
+    // buffer's free bits are zero, so adding is or-ing) and the next word is
+    // loaded under a predicate.
     __device__ __forceinline__ void refill()
     {
-        if ((H & 32u) == 0) {  // have < 32
-            bh |= __funnelshift_r(nxt, 0u, H);  // nxt >> have
-            bl |= __funnelshift_r(0u, nxt, H);  // nxt << (32 - have), 0 at have = 0
-            H += 32;
-            ++widx;
-            nxt = col[(widx & (kInRing - 1)) * 32];
-        }
+        const uint32_t k = (~H >> 5) & 1u;
+        bh = imad(k, __funnelshift_r(nxt, 0u, H), bh);  // nxt >> have
+        bl = imad(k, __funnelshift_r(0u, nxt, H), bl);  // nxt << (32 - have), 0 at have = 0
+        H = imad(k, kc[k32], H);
+        widx = imad(k, kc[kOne], widx);
+        lds_if(k, imad(widx & (kInRing - 1), kc[k128], col), nxt);
     }
-    // drop the L = (t & 31) bits of a table word t (1 <= L <= 31)
+    // drop the L = (t & 31) bits of t = entry >> 24 (1 <= L <= 31); the rest
+    // of t is a multiple of 64 and never reaches have
     __device__ __forceinline__ void consume_t(uint32_t t)
     {
         bh = __funnelshift_l(bl, bh, t);
         bl = __funnelshift_l(0u, bl, t);
-        H -= t;
+        H = imad(t, kc[kMinus1], H);
     }
     // drop L <= 32 bits
     __device__ __forceinline__ void consume(uint32_t L)
@@ -249,37 +324,52 @@ struct Bits {
 };
 
 // Output bytes of one lane assembled in a register and stored to its column
-// of the warp's output ring one word at a time (row r of lane l at
-// ring[r * 32 + l]; the ring holds kOutRing words).  `lo` holds the bytes of
-// the word being filled at its low end, `sh` = 8 * (bytes in lo), `R` = 32 *
-// (ring row of that word).  Bytes above the filled ones are zero.
+// of the warp's output ring one completed word at a time (row r of lane l at byte
+// r * 128 + 4 * l of the warp's ring; the ring holds kOutRing words).
+// `lo` holds the bytes of the word being filled at its low end, `sh` = 8 *
+// (bytes in lo) and R = 128 * (number of the word being filled), of which
+// the row is R mod (128 * kOutRing).  Bytes above the filled ones are zero,
+// so appending is adding.
 struct OutWord {
+    uint32_t col;  // shared address of this lane's column
     uint32_t lo, sh, R;
 
-    __device__ __forceinline__ void start(uint32_t q)
+    __device__ __forceinline__ void start(uint32_t column, uint32_t q)
     {
+        col = column;
         lo = 0;
         sh = (q & 3u) * 8;
-        R = ((q >> 2) & (kOutRing - 1)) * 32;
+        R = (q >> 2) * 128;
     }
-    // append the bytes of y (zero above its ns8/8 bytes)
-    __device__ __forceinline__ void emit(uint32_t *col, uint32_t y, uint32_t ns8)
+    __device__ __forceinline__ uint32_t addr() const
     {
-        lo |= __funnelshift_l(0u, y, sh);        // y << sh
-        const uint32_t hi = __funnelshift_l(y, 0u, sh);  // y >> (32 - sh), 0 at sh = 0
-        sh += ns8;
-        col[R] = lo;
-        const uint32_t t = sh & 32u;  // 32 when the word is complete
-        lo = __funnelshift_rc(lo, hi, t);
-        R = (R + t) & (kOutRing * 32 - 1);
-        sh ^= t;
+        return imad(R & ((kOutRing - 1) * 128), kc[kOne], col);
     }
-    // output position, given the position q0 and ring row R0 at some earlier
-    // point less than kOutRing words back
+    // append the ns bytes of y (zero above them); a completed word is stored
+    __device__ __forceinline__ void emit(uint32_t y, uint32_t ns)
+    {
+        const uint32_t hi = __funnelshift_l(y, 0u, sh);  // y >> (32 - sh), 0 at sh = 0
+        lo = imad(y, 1u << sh, lo);                      // lo | y << sh
+        sh = imad(ns, kc[kEight], sh);
+        const uint32_t full = sh >> 5;                   // the word is complete
+        sts_if(full, addr(), lo);
+        lo = imad(full, imad(lo, kc[kMinus1], hi), lo);  // full ? hi : lo
+        R = imad(full, kc[k128], R);
+        sh = imad(full, kc[kMinus32], sh);
+    }
+    // output position, given the position q0 and value R0 of R at some
+    // earlier point
     __device__ __forceinline__ uint32_t pos_from(uint32_t q0, uint32_t R0) const
     {
-        const uint32_t rows = ((R - R0) & (kOutRing * 32 - 1)) >> 5;
-        return ((q0 >> 2) + rows) * 4 + (sh >> 3);
+        return ((q0 >> 2) + ((R - R0) >> 7)) * 4 + (sh >> 3);
+    }
+    __device__ __forceinline__ uint32_t byte_at(uint32_t b) const
+    {
+        return lds_u8(col + ((b >> 2) & (kOutRing - 1)) * 128 + (b & 3u));
+    }
+    __device__ __forceinline__ uint32_t word_row(uint32_t w) const
+    {
+        return lds(col + (w & (kOutRing - 1)) * 128);
     }
 };
 
@@ -296,15 +386,16 @@ __device__ __forceinline__ void count_codes(const Tables &T, const uint8_t *pay,
         rd.init(pay, nw, cbase + pos);
         while (pos < stop) {
             rd.refill();
-            const uint2 ent = T.lut[rd.buf >> (64 - kLutBits)];
-            uint32_t L = ent.y & 31u, ns = (ent.y >> 11) & 31u;
-            if (ent.y == 0) {
+            const uint32_t idx = (uint32_t)(rd.buf >> (64 - kLutBits));
+            const uint32_t ent = T.lut[idx];
+            uint32_t L = (ent >> 24) & 31u, ns = ent >> 30;
+            if (ent == 0) {
                 uint32_t sym;
                 if (!long_code(T, (uint32_t)(rd.buf >> 32), L, sym))
                     L = 1;
                 ns = 1;
             } else if (ns > 1 && pos + L >= stop) {  // later codes may start past stop
-                L = (ent.y >> 16) & 31u;
+                L = T.len0[idx];
                 ns = 1;
             }
             pos += L;
@@ -349,9 +440,9 @@ __device__ __forceinline__ void settle_segment(const Tables &T, const uint8_t *p
             started = true;
         }
         rd.refill();
-        const uint2 ent = T.lut[rd.buf >> (64 - kLutBits)];
-        uint32_t L = (ent.y >> 16) & 31u;  // first code only: every boundary matters
-        if (ent.y == 0) {
+        const uint32_t idx = (uint32_t)(rd.buf >> (64 - kLutBits));
+        uint32_t L = T.len0[idx];  // first code only: every boundary matters
+        if (T.lut[idx] == 0) {
             uint32_t sym;
             if (!long_code(T, (uint32_t)(rd.buf >> 32), L, sym))
                 L = 1;
@@ -477,7 +568,7 @@ __device__ __forceinline__ bool prepare(const uint8_t *stream_in, uint64_t bytes
     // pass 2: append the following codes while they fit in the window
     for (int v = tid; v < kLutSize; v += NT) {
         const uint32_t e0 = scratch[v];
-        uint2 ent = make_uint2(0u, 0u);
+        uint32_t ent = 0, first_len = 0;
         if (e0) {
             const uint32_t L0 = e0 >> 8;
             uint32_t syms = e0 & 0xffu, tot = L0, ns = 1;
@@ -493,9 +584,11 @@ __device__ __forceinline__ bool prepare(const uint8_t *stream_in, uint64_t bytes
                     }
                 }
             }
-            ent = make_uint2(syms, tot | ((8 * ns) << 8) | (L0 << 16));
+            ent = syms | (tot << 24) | (ns << 30);
+            first_len = L0;
         }
         sh.lut[v] = ent;
+        sh.len0[v] = (uint8_t)first_len;
     }
     __syncthreads();
 
@@ -514,6 +607,7 @@ __device__ __forceinline__ bool prepare(const uint8_t *stream_in, uint64_t bytes
     si.offs = offs;
     si.pay = pay;
     si.T.lut = sh.lut;
+    si.T.len0 = sh.len0;
     si.T.count = sh.count;
     si.T.first = sh.first;
     si.T.start = sh.start;
@@ -532,18 +626,18 @@ __device__ __forceinline__ uint32_t pick_split(uint64_t chunks, uint32_t min_cha
 }
 
 // Store the complete 16-byte groups of [fl, q) from the output ring.
-__device__ __forceinline__ void flush_groups(uint8_t *ob, const uint32_t *col, uint32_t &fl,
+__device__ __forceinline__ void flush_groups(uint8_t *ob, const OutWord &ow, uint32_t &fl,
                                              uint32_t q)
 {
-    const uint8_t *colb = reinterpret_cast<const uint8_t *>(col);
     uint32_t hs = fl & ~15u;
     while (q >= hs + 16) {
         if (fl == hs) {
-            const uint32_t *h = col + ((hs >> 2) & (kOutRing - 1)) * 32;
-            *reinterpret_cast<uint4 *>(ob + hs) = make_uint4(h[0], h[32], h[64], h[96]);
+            const uint32_t w = hs >> 2;
+            *reinterpret_cast<uint4 *>(ob + hs) =
+                make_uint4(ow.word_row(w), ow.word_row(w + 1), ow.word_row(w + 2), ow.word_row(w + 3));
         } else {
             for (uint32_t b = fl; b < hs + 16; ++b)
-                ob[b] = colb[((b >> 2) & (kOutRing - 1)) * 128 + (b & 3u)];
+                ob[b] = (uint8_t)ow.byte_at(b);
         }
         hs += 16;
         fl = hs;
@@ -557,7 +651,9 @@ __device__ __forceinline__ bool decode_task(const StreamInfo &si, uint32_t S, ui
                                             uint32_t *in_col, uint32_t *out_col)
 {
     const Tables &T = si.T;
-    const uint2 *lut = T.lut;
+    const uint32_t lut_s = smem_u32(T.lut);
+    const uint8_t *len0 = T.len0;
+    const uint32_t in_s = smem_u32(in_col), out_s = smem_u32(out_col);
     const uint64_t n = si.n, chunks = si.chunks, pbits = si.pbits, pay_words = si.pay_words;
     const uint32_t cs = si.cs;
     const uint64_t *offs = si.offs;
@@ -566,7 +662,6 @@ __device__ __forceinline__ bool decode_task(const StreamInfo &si, uint32_t S, ui
     const uint32_t G = 32 / S;
     const uint32_t k = (uint32_t)lane & (S - 1);
     const uint32_t grp = (uint32_t)lane / S;
-    const uint8_t *out_colb = reinterpret_cast<const uint8_t *>(out_col);
     const uint64_t c = task * G + grp;
     const bool valid = c < chunks;
     bool bad = false;
@@ -598,16 +693,15 @@ __device__ __forceinline__ bool decode_task(const StreamInfo &si, uint32_t S, ui
         Bits rs = {};
         bool act = work && k + 1 < S && g < stop;
         if (act)
-            rs.init(in_col, pw, pay_words, cbase >> 5, b0 + g);
+            rs.init(in_s, pw, pay_words, cbase >> 5, b0 + g);
         uint32_t pos = g;
         // 1a. code by code through the first 64 bits, recording the boundaries
         bool head = act;
         while (__any_sync(kFull, head)) {
             if (head) {
                 rs.refill();
-                const uint2 ent = lut_at(lut, rs.bh);
-                uint32_t L = (ent.y >> 16) & 31u;
-                if (ent.y == 0) {
+                uint32_t L = len0_at(len0, rs.bh);
+                if (L == 0) {
                     uint32_t sym;
                     if (!long_code(T, rs.bh, L, sym))
                         L = 1;
@@ -623,45 +717,48 @@ __device__ __forceinline__ bool decode_task(const StreamInfo &si, uint32_t S, ui
             }
         }
         // 1b. windows of table lookups, several codes per lookup
-        uint32_t cnt8 = 0;
+        uint32_t cnt = 0;
         while (__any_sync(kFull, act)) {
-            const bool easy = stop - pos >= 32 * kWindow;
+            // an unchecked window reads at most one long code plus 16 table
+            // lookups of <= 12 bits
+            const bool easy = stop - pos >= 32 + kLutBits * kWindow;
             if (__all_sync(kFull, easy || !act)) {
+                if (act) {
+                    rs.refill();
+                    if (lut_ld(lut_s, rs.bh) == 0) {  // a long code (rare)
+                        uint32_t L, sym;
+                        if (!long_code(T, rs.bh, L, sym))
+                            L = 1;
+                        rs.consume(L);
+                        rs.refill();
+                        ++cnt;
+                    }
+                }
 #pragma unroll
                 for (int j = 0; j < kWindow; ++j) {
                     if (act) {
-                        if ((j & 1) == 0)
+                        if ((j & 1) == 0 && j > 0)
                             rs.refill();  // two lookups use at most 24 of >= 32 bits
-                        const uint2 ent = lut_at(lut, rs.bh);
-                        if (ent.y == 0) {  // longer than the table (rare)
-                            rs.refill();
-                            uint32_t L, sym;
-                            if (!long_code(T, rs.bh, L, sym))
-                                L = 1;
-                            rs.consume(L);
-                            rs.refill();
-                            cnt8 += 8;
-                        } else {
-                            rs.consume_t(ent.y);
-                            cnt8 += __byte_perm(ent.y, 0u, 0x4441);  // 8 * ns
-                        }
+                        // a long code's entry is all zero: the lane stays on
+                        // it for the rest of the window
+                        const uint32_t ent = lut_ld(lut_s, rs.bh);
+                        rs.consume_t(ent >> 24);
+                        cnt += ent >> 30;
                     }
                 }
             } else {
 #pragma unroll 1
-                for (int j = 0; j < kWindow; ++j) {
+                for (int j = 0; j < kCheckedWindow; ++j) {
                     if (act) {
                         rs.refill();
-                        const uint2 ent = lut_at(lut, rs.bh);
-                        uint32_t L = (ent.y >> 16) & 31u;  // one code at a time
-                        if (ent.y == 0) {
-                            rs.refill();
+                        uint32_t L = len0_at(len0, rs.bh);  // one code at a time
+                        if (L == 0) {
                             uint32_t sym;
                             if (!long_code(T, rs.bh, L, sym))
                                 L = 1;
                         }
                         rs.consume(L);
-                        cnt8 += 8;
+                        ++cnt;
                         act = rs.bitpos() - b0 < stop;
                     }
                 }
@@ -672,11 +769,11 @@ __device__ __forceinline__ bool decode_task(const StreamInfo &si, uint32_t S, ui
             }
             if (act)
                 rs.top_up();
-            cp_async_wait<2>();
+            cp_async_wait<3>();
         }
         cp_async_wait<0>();  // the ring is reused below
         if (work && k + 1 < S && g < stop) {
-            cnt1 += cnt8 >> 3;
+            cnt1 += cnt;
             e1 = rs.bitpos() - b0;
         }
     }
@@ -722,46 +819,58 @@ __device__ __forceinline__ bool decode_task(const StreamInfo &si, uint32_t S, ui
         uint8_t *const ob = si.out + c * cs;  // chunk output, 16-byte aligned
         const uint32_t qend = O + todo;
         uint32_t pos = entry, q = O, fl = O;  // q: next byte, fl: first unflushed byte
-        ow.start(O);
+        ow.start(out_s, O);
         if (act)
-            rs.init(in_col, pw, pay_words, cbase >> 5, b0 + entry);
+            rs.init(in_s, pw, pay_words, cbase >> 5, b0 + entry);
         while (__any_sync(kFull, act)) {
             // far from the segment's end a window needs no per-code checks:
             // at most 3 * 16 symbols and 16 x 32 bits.  The unchecked window
             // runs only when every lane of the warp is in that state, so it
             // needs no per-lane predicate either.
-            const bool easy =
-                act && qend - q >= kMaxPerLookup * kWindow && lim - pos >= 32 * kWindow;
+            // A window reads at most one long code (resolved first) plus 16
+            // table lookups of <= 12 bits and 3 symbols each.
+            const bool easy = act && qend - q >= 1 + kMaxPerLookup * kWindow &&
+                              lim - pos >= 32 + kLutBits * kWindow;
             const uint32_t q0 = q, R0 = ow.R;
             if (__all_sync(kFull, easy)) {
+                rs.refill();
+                if (lut_ld(lut_s, rs.bh) == 0) {  // a long code (rare)
+                    uint32_t L = 0, sym = 0;
+                    if (!long_code(T, rs.bh, L, sym)) {
+                        bad = true;  // nothing more is flushed
+                        act = false;
+                    }
+                    rs.consume(L);
+                    rs.refill();
+                    ow.emit(sym, 1);
+                }
+                // A long code's entry is all zero, so it consumes and emits
+                // nothing: the lane stays on it for the rest of the window
+                // and resolves it at the start of the next.  Software
+                // pipelined: lookup j+1's table load is issued before lookup
+                // j's output is appended.
+                uint32_t ent = lut_ld(lut_s, rs.bh);
 #pragma unroll
                 for (int j = 0; j < kWindow; ++j) {
-                    if ((j & 1) == 0)
-                        rs.refill();  // two lookups use at most 24 of >= 32 bits
-                    const uint2 ent = lut_at(lut, rs.bh);
-                    if (ent.y == 0) {  // longer than the table (rare)
-                        rs.refill();
-                        uint32_t L = 0, sym = 0;
-                        if (!long_code(T, rs.bh, L, sym)) {
-                            bad = true;  // the rest of the window is not flushed
-                            act = false;
-                        }
-                        rs.consume(L);
-                        rs.refill();
-                        ow.emit(out_col, sym, 8);
-                    } else {
-                        rs.consume_t(ent.y);
-                        ow.emit(out_col, ent.x, __byte_perm(ent.y, 0u, 0x4441));
+                    const uint32_t t = ent >> 24;
+                    rs.consume_t(t);
+                    uint32_t nxt_ent = 0;
+                    if (j + 1 < kWindow) {
+                        if ((j & 1) == 1)
+                            rs.refill();  // two lookups use at most 24 of >= 32 bits
+                        nxt_ent = lut_ld(lut_s, rs.bh);
                     }
+                    ow.emit(imad(t, kc[kMinusTop8], ent), t >> 6);  // the symbol bytes
+                    ent = nxt_ent;
                 }
             } else {
 #pragma unroll 1
-                for (int j = 0; j < kWindow; ++j) {
+                for (int j = 0; j < kCheckedWindow; ++j) {
                     if (act) {
                         rs.refill();
-                        const uint2 ent = lut_at(lut, rs.bh);
+                        const uint32_t ent = lut_ld(lut_s, rs.bh);
                         uint32_t L, ns8, y;
-                        if (ent.y == 0) {
+                        if (ent == 0) {
                             rs.refill();
                             uint32_t sym = 0;
                             L = 0;
@@ -770,11 +879,11 @@ __device__ __forceinline__ bool decode_task(const StreamInfo &si, uint32_t S, ui
                             ns8 = 8;
                             y = sym;
                         } else {
-                            L = ent.y & 31u;
-                            ns8 = (ent.y >> 8) & 0xffu;
-                            y = ent.x;
+                            L = (ent >> 24) & 31u;
+                            ns8 = (ent >> 30) << 3;
+                            y = ent & 0xffffffu;
                             if (q + (ns8 >> 3) > qend || pos + L > lim) {  // first code only
-                                L = (ent.y >> 16) & 31u;
+                                L = len0_at(len0, rs.bh);
                                 ns8 = 8;
                                 y &= 0xffu;
                             }
@@ -783,7 +892,7 @@ __device__ __forceinline__ bool decode_task(const StreamInfo &si, uint32_t S, ui
                             bad = true;
                         if (!bad) {
                             rs.consume(L);
-                            ow.emit(out_col, y, ns8);
+                            ow.emit(y, ns8 >> 3);
                             q += ns8 >> 3;
                             pos += L;
                         }
@@ -798,16 +907,16 @@ __device__ __forceinline__ bool decode_task(const StreamInfo &si, uint32_t S, ui
                 if (act)
                     rs.top_up();
             }
-            cp_async_wait<2>();
+            cp_async_wait<3>();
             if (!bad)
-                flush_groups(ob, out_col, fl, q);
+                flush_groups(ob, ow, fl, q);
         }
         cp_async_wait<0>();
         if (!bad) {
             if (todo)
-                out_col[ow.R] = ow.lo;  // bytes carried over by the last emit
+                sts(ow.addr(), ow.lo);  // bytes carried over by the last emit
             for (uint32_t b = fl; b < q; ++b)
-                ob[b] = out_colb[((b >> 2) & (kOutRing - 1)) * 128 + (b & 3u)];
+                ob[b] = (uint8_t)ow.byte_at(b);
             if (todo && final_seg && c + 1 < chunks && pos != lim)
                 bad = true;
         }
