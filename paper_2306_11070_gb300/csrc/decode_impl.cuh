@@ -62,47 +62,6 @@ struct StreamInfo {
     Tables T;
 };
 
-// Integer constants read from the constant bank.  A multiply by one of them
-// is an IMAD, which runs on the FMA pipe; adds, conditional adds and
-// constant shifts written that way leave the ALU pipe (which executes the
-// shifts, logic ops and compares, at half a warp per cycle) to the work only
-// it can do.  The values are not visible to the compiler, so it cannot turn
-// the multiplies back into shifts and adds.
-enum { kOne, kMinus1, kFour, kEight, k32, kMinus32, k128, kMinusTop8, kNumConst };
-static __constant__ uint32_t kc[kNumConst] = {1u, 0xffffffffu, 4u, 8u, 32u, 0xffffffe0u,
-                                              128u, 0xff000000u};
-__device__ __forceinline__ uint32_t imad(uint32_t a, uint32_t b, uint32_t c) { return a * b + c; }
-
-// Shared-memory accesses by 32-bit shared address.  The rings are accessed
-// only through these volatile forms (and cp.async), so their order is kept.
-__device__ __forceinline__ uint32_t lds(uint32_t a)
-{
-    uint32_t v;
-    asm volatile("ld.shared.u32 %0, [%1];" : "=r"(v) : "r"(a));
-    return v;
-}
-__device__ __forceinline__ uint32_t lds_u8(uint32_t a)
-{
-    uint32_t v;
-    asm volatile("ld.shared.u8 %0, [%1];" : "=r"(v) : "r"(a));
-    return v;
-}
-__device__ __forceinline__ void sts(uint32_t a, uint32_t v)
-{
-    asm volatile("st.shared.u32 [%0], %1;" ::"r"(a), "r"(v));
-}
-// predicated forms: the access happens only when `k` is nonzero (no branch)
-__device__ __forceinline__ void lds_if(uint32_t k, uint32_t a, uint32_t &v)
-{
-    asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.u32 p, %2, 0;\n\t@p ld.shared.u32 %0, [%1];\n\t}"
-                 : "+r"(v)
-                 : "r"(a), "r"(k));
-}
-__device__ __forceinline__ void sts_if(uint32_t k, uint32_t a, uint32_t v)
-{
-    asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.u32 p, %2, 0;\n\t@p st.shared.u32 [%0], %1;\n\t}"
-                 ::"r"(a), "r"(v), "r"(k));
-}
 // table entry of the 12-bit window at the top of bh.  Volatile like the ring
 // accesses, so that the order written below (each lookup's table load
 // before the previous lookup's ring store) reaches the compiled code:
