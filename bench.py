@@ -443,6 +443,7 @@ def run_ours(args):
             for i, nm in enumerate(names)}
     dom = max(range(4), key=lambda i: per_k[i])
     achieved = alg[dom] / (per_k[dom] * 1e-3) / 1e9
+    traffic = profiled_traffic("k_" + names[dom])
     line = {
         "metric": METRIC,
         "value": world * n / (ms_per_step * 1e-3) / 1e9,
@@ -465,7 +466,9 @@ def run_ours(args):
                 "d2h_bytes_per_step": nbytes + n + 8},
         "gpu_launches": launches_per_step * args.steps,
         "roofline": {"kernel": names[dom], "bound": "hbm", "achieved": achieved, "peak": peak,
-                     "unit": "GB/s", "frac": achieved / peak, "traffic": None,
+                     "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
+                     "traffic_source": "profiles/traffic_text_1g.txt (ncu dram bytes per launch)"
+                     if traffic is not None else "no capture of the current kernel source",
                      "peak_source": f"{peak_src} copy bandwidth (MEASURED_PEAKS.json hbm_gbs)"
                      if peak_src == "measured" else "fallback 6.8 TB/s"},
         "kernels": kern,
@@ -476,6 +479,28 @@ def run_ours(args):
     print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()
+
+
+def profiled_traffic(kernel):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary, or
+    None when the kernel's sources changed since the capture."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "traffic_text_1g.txt")
+    csrc = os.path.join(ROOT, "paper_2306_11070_gb300", "csrc")
+    try:
+        lines = open(path).read().splitlines()
+    except OSError:
+        return None
+    for ln in lines:
+        f = ln.split()
+        if not f or f[0].startswith("#") or f[0] != kernel:
+            continue
+        h = hashlib.sha256()
+        for name in f[3:]:
+            with open(os.path.join(csrc, name), "rb") as fh:
+                h.update(fh.read())
+        return int(f[1]) if h.hexdigest()[:16] == f[2] else None
+    return None
 
 
 def main():
