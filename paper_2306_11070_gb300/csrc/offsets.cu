@@ -20,7 +20,8 @@ namespace {
 
 constexpr int kDotBlock = 256;
 constexpr int kCountBlock = 256;
-constexpr int kScanBlock = 1024;
+constexpr int kScanBlock = 512;
+constexpr int kScanPer = 32;  // counts per thread and tile
 
 __global__ void __launch_bounds__(kDotBlock)
     k_unit_bits_hist(const uint16_t *__restrict__ unit_hist, uint64_t units,
@@ -103,32 +104,43 @@ __global__ void __launch_bounds__(kCountBlock)
     }
 }
 
-// One CTA scans the unit counts in tiles of 4096 (coalesced 16-byte loads,
-// four counts per thread), carrying the running total across tiles.
+// One CTA scans the unit counts in tiles of kScanBlock * kScanPer units:
+// each thread loads its kScanPer consecutive counts with 16-byte loads that
+// are all in flight at once, so a tile costs one memory round trip (1 GiB of
+// input is 4 tiles), then a block scan of the thread totals and a carry
+// across tiles.
 __global__ void __launch_bounds__(kScanBlock)
     k_scan_units(const uint32_t *__restrict__ unit_bits, uint64_t units,
                  unsigned long long *__restrict__ unit_off, const int32_t *status)
 {
     __shared__ unsigned long long s_warp[kScanBlock / 32];
+    __shared__ unsigned long long s_total;
     if (chain_failed(status))
         return;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     unsigned long long carry = 0;
-    for (uint64_t t0 = 0; t0 < units; t0 += 4 * kScanBlock) {
-        const uint64_t i = t0 + 4 * (uint64_t)tid;
-        uint32_t v[4];
-        if (i + 4 <= units && (units & 3) == 0) {
-            const uint4 q = *reinterpret_cast<const uint4 *>(unit_bits + i);
-            v[0] = q.x;
-            v[1] = q.y;
-            v[2] = q.z;
-            v[3] = q.w;
+    for (uint64_t t0 = 0; t0 < units; t0 += (uint64_t)kScanBlock * kScanPer) {
+        const uint64_t i = t0 + (uint64_t)kScanPer * tid;
+        uint32_t v[kScanPer];
+        if (i + kScanPer <= units) {  // i is a multiple of 32: 16-byte aligned
+            const uint4 *q = reinterpret_cast<const uint4 *>(unit_bits + i);
+#pragma unroll
+            for (int j = 0; j < kScanPer / 4; ++j) {
+                const uint4 x = q[j];
+                v[4 * j] = x.x;
+                v[4 * j + 1] = x.y;
+                v[4 * j + 2] = x.z;
+                v[4 * j + 3] = x.w;
+            }
         } else {
 #pragma unroll
-            for (int j = 0; j < 4; ++j)
+            for (int j = 0; j < kScanPer; ++j)
                 v[j] = i + j < units ? unit_bits[i + j] : 0u;
         }
-        const unsigned long long own = (unsigned long long)v[0] + v[1] + v[2] + v[3];
+        unsigned long long own = 0;
+#pragma unroll
+        for (int j = 0; j < kScanPer; ++j)
+            own += v[j];
         unsigned long long x = own;
 #pragma unroll
         for (int d = 1; d < 32; d <<= 1) {
@@ -140,7 +152,7 @@ __global__ void __launch_bounds__(kScanBlock)
             s_warp[warp] = x;
         __syncthreads();
         if (warp == 0) {
-            const unsigned long long w = s_warp[lane];
+            const unsigned long long w = lane < kScanBlock / 32 ? s_warp[lane] : 0ull;
             unsigned long long z = w;
 #pragma unroll
             for (int d = 1; d < 32; d <<= 1) {
@@ -148,24 +160,30 @@ __global__ void __launch_bounds__(kScanBlock)
                 if (lane >= d)
                     z += y;
             }
-            s_warp[lane] = z - w;
+            if (lane < kScanBlock / 32)
+                s_warp[lane] = z - w;
+            if (lane == 31)
+                s_total = z;  // the tile total
         }
         __syncthreads();
         unsigned long long run = carry + s_warp[warp] + x - own;
+        if (i + kScanPer <= units) {
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            if (i + j < units)
-                unit_off[i + j] = run;
-            run += v[j];
+            for (int j = 0; j < kScanPer; j += 2) {
+                const unsigned long long a = run;
+                run += v[j];
+                reinterpret_cast<ulonglong2 *>(unit_off + i)[j / 2] = make_ulonglong2(a, run);
+                run += v[j + 1];
+            }
+        } else {
+#pragma unroll
+            for (int j = 0; j < kScanPer; ++j) {
+                if (i + j < units)
+                    unit_off[i + j] = run;
+                run += v[j];
+            }
         }
-        // the tile total: last thread's inclusive value
-        const unsigned long long tile_total =
-            __shfl_sync(0xffffffffu, s_warp[kScanBlock / 32 - 1] + x, 31);
-        __syncthreads();
-        if (warp == kScanBlock / 32 - 1 && lane == 31)
-            s_warp[0] = tile_total;
-        __syncthreads();
-        carry += s_warp[0];
+        carry += s_total;
         __syncthreads();
     }
     if (tid == 0)
