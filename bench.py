@@ -47,6 +47,23 @@ def load_peaks():
         return 6800.0, "fallback"
 
 
+def max_over_ranks(x, dist, device):
+    """The largest of every rank's x (a time), via all-reduce; x itself on one
+    process.  Works with nccl (device tensor) and gloo (CPU tensor)."""
+    if dist is None:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_gbs(world, n_bytes, seconds):
+    """Whole-job throughput: every rank processes n_bytes per step, and the
+    job's step takes the slowest rank's time."""
+    return world * n_bytes / seconds / 1e9
+
+
 def rank_info():
     return (int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")),
             int(os.environ.get("LOCAL_RANK", "0")))
@@ -152,7 +169,8 @@ def cpu_baseline(x):
 
 def measure_batched(hg, synth, torch, count=4096):
     """Config 3: `count` independent text buffers (log-uniform 1 KiB..4 MiB,
-    per-buffer seeds), one fused launch per batch (CUDA graph) vs one plain
+    per-buffer seeds), one fused launch per batch (CUDA graph) with
+    autotuned chunk size, lanes per buffer and CTAs per SM, vs one plain
     call per buffer on one stream."""
     from concurrent.futures import ThreadPoolExecutor
     sizes = synth.log_uniform_sizes(count, seed=3, lo=1024, hi=4 << 20)
@@ -160,9 +178,15 @@ def measure_batched(hg, synth, torch, count=4096):
         xs = list(ex.map(lambda i: synth.text(int(sizes[i]), synth.batch_seed(i)), range(count)))
     total = float(sizes.sum())
     ins = [torch.from_numpy(x).cuda() for x in xs]
-    outs = [torch.empty(hg.huff_max_stream_size(x.size), dtype=torch.uint8, device="cuda")
+    # outputs sized for the smallest candidate chunk size, so the tuner may pick it
+    outs = [torch.empty(hg.huff_max_stream_size(x.size, 4096), dtype=torch.uint8, device="cuda")
             for x in xs]
-    plan = hg.BatchPlan(ins, outs, hg.HUFF_BATCH_COMPRESS)
+    t0 = time.perf_counter()
+    probe = hg.BatchPlan(ins, outs, hg.HUFF_BATCH_COMPRESS)
+    cbest = probe.autotune(flags=hg.HUFF_TUNE_ROUND_TRIP)
+    probe.close()
+    tune_c = time.perf_counter() - t0
+    plan = hg.BatchPlan(ins, outs, hg.HUFF_BATCH_COMPRESS, cbest)
 
     def t_ms(fn, reps, warm):
         for _ in range(warm):
@@ -181,7 +205,12 @@ def measure_batched(hg, synth, torch, count=4096):
     assert (plan.status.cpu().numpy() == 0).all()
     streams = [outs[i][:int(nb[i])] for i in range(count)]
     decs = [torch.empty(max(x.size, 16), dtype=torch.uint8, device="cuda") for x in xs]
-    dplan = hg.BatchPlan(streams, decs, hg.HUFF_BATCH_DECOMPRESS)
+    t0 = time.perf_counter()
+    probe = hg.BatchPlan(streams, decs, hg.HUFF_BATCH_DECOMPRESS)
+    dbest = probe.autotune()
+    probe.close()
+    tune_d = time.perf_counter() - t0
+    dplan = hg.BatchPlan(streams, decs, hg.HUFF_BATCH_DECOMPRESS, dbest)
     td = t_ms(dplan.run, 10, 3)
     assert (dplan.status.cpu().numpy() == 0).all()
     ok = all(torch.equal(decs[i][:xs[i].size], ins[i]) for i in range(count))
@@ -207,6 +236,11 @@ def measure_batched(hg, synth, torch, count=4096):
     dplan.close()
     return {"workload": f"{count} text buffers, log-uniform 1 KiB-4 MiB, {total / 2**30:.3f} GiB",
             "graph": info["graph"], "grid": info["grid"], "round_trip_ok": ok,
+            "autotuned": {"chunk_symbols": cbest.chunk_symbols,
+                          "compress_ctas_per_sm": cbest.ctas_per_sm,
+                          "decode_lanes": dbest.decode_lanes,
+                          "decompress_ctas_per_sm": dbest.ctas_per_sm,
+                          "tune_s": round(tune_c + tune_d, 2)},
             "compress_ms": tc, "compress_gbs": total / tc / 1e6,
             "decompress_ms": td, "decompress_gbs": total / td / 1e6,
             "plain_compress_ms": pc, "plain_decompress_ms": pd,
@@ -391,10 +425,7 @@ def run_ours(args):
     clocks.mark(False)
     elapsed_ms = t_start.elapsed_time(t_end)
     acc = [sum(ev[i].elapsed_time(ev[i + 1]) for ev in evs) for i in range(4)]
-    if dist is not None:
-        t = torch.tensor([elapsed_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        elapsed_ms = float(t.item())
+    elapsed_ms = max_over_ranks(elapsed_ms, dist, dev)
     ms_per_step = elapsed_ms / args.steps
 
     # end to end through the public API from pinned host memory
@@ -412,11 +443,7 @@ def run_ours(args):
         hg.huff_decode(out, size, d_out=dec, out_cap=n, d_n=dn, d_status=st)
         h_out.copy_(dec, non_blocking=True)
         torch.cuda.synchronize()
-    e2e_sec = (time.perf_counter() - t0) / e2e_steps
-    if dist is not None:
-        t = torch.tensor([e2e_sec], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_sec = float(t.item())
+    e2e_sec = max_over_ranks((time.perf_counter() - t0) / e2e_steps, dist, dev)
     ok = int(st.item()) == 0 and torch.equal(h_out, h_x)
     clk = clocks.stop()
     if not ok:
@@ -446,7 +473,7 @@ def run_ours(args):
     traffic = profiled_traffic("k_" + names[dom])
     line = {
         "metric": METRIC,
-        "value": world * n / (ms_per_step * 1e-3) / 1e9,
+        "value": job_gbs(world, n, ms_per_step * 1e-3),
         "unit": "GB/s",
         "n_gpus": world,
         "steps": args.steps,
@@ -462,7 +489,7 @@ def run_ours(args):
                    "l2": "inputs larger than L2 (1 GiB vs 129 MB), no flush",
                    "parallelism": f"replicas x{world}"},
         "clocks": clk,
-        "e2e": {"value": world * n / e2e_sec / 1e9, "unit": "GB/s", "h2d_bytes_per_step": n,
+        "e2e": {"value": job_gbs(world, n, e2e_sec), "unit": "GB/s", "h2d_bytes_per_step": n,
                 "d2h_bytes_per_step": nbytes + n + 8},
         "gpu_launches": launches_per_step * args.steps,
         "roofline": {"kernel": names[dom], "bound": "hbm", "achieved": achieved, "peak": peak,

@@ -230,11 +230,16 @@ typedef struct huff_batch_params {
     uint32_t ctas_per_sm;   /* persistent CTAs per SM, 0 = as many as fit     */
     uint32_t decode_lanes;  /* decompress: lanes to spread a buffer over      */
     uint32_t use_graph;     /* capture the launch in a CUDA graph (1) or not  */
+    uint32_t barrier_extra; /* test hook, 0 in use: nonzero makes the launch's
+                               grid barriers wait for that many CTAs more than
+                               exist, so every wait runs out and the buffers
+                               report HUFF_ERR_TIMEOUT (exercises the bounded
+                               waits without a GPU fault)                    */
 } huff_batch_params_t;
 
 typedef struct huff_batch_plan huff_batch_plan_t; /* opaque */
 
-/* Defaults: 16384-symbol chunks, full occupancy, 32 decode lanes, graph on. */
+/* Defaults: 16384-symbol chunks, full occupancy, 128 decode lanes, graph on. */
 void huff_batch_default_params(huff_batch_params_t *params);
 
 /* Plan a batch of `count` buffers for `op` (params may be NULL for the
@@ -256,6 +261,31 @@ huff_status_t huff_batch_run(huff_batch_plan_t *plan, huff_stream_t stream);
 /* The parameters a plan uses, its grid size and whether it runs as a graph. */
 huff_status_t huff_batch_info(const huff_batch_plan_t *plan, huff_batch_params_t *params,
                               uint32_t *grid, int32_t *used_graph);
+
+/* Autotuner.  Times candidate parameter sets on the caller's own batch and
+ * returns the fastest in *best; results are cached per device, operation
+ * and batch shape (buffer count, total and mean size in powers of two, and
+ * for decompression nothing else), so a later call for a batch of the same
+ * shape returns at once.  Candidates:
+ *   decompress: decode_lanes in {32, 64, 128, 256} x ctas_per_sm in
+ *               {as many as fit, 1};
+ *   compress:   chunk_symbols in {base, 4096} (the chunk size of every
+ *               stream; 4096 only if every out_cap holds
+ *               huff_max_stream_size(n, 4096)) x ctas_per_sm in {as many as
+ *               fit, 1}, with flags & HUFF_TUNE_ROUND_TRIP scored by the
+ *               compress time plus the best decompress time of the streams
+ *               it produced (decode_lanes tuned alongside), else by the
+ *               compress time alone.
+ * `base` (NULL = defaults) supplies everything not tuned.  Tuning RUNS the
+ * batch several times on `stream` (the outputs are overwritten with valid
+ * results each time) and synchronizes it; with HUFF_TUNE_ROUND_TRIP it also
+ * allocates, and frees again, scratch for the decoded bytes.  Errors: those
+ * of huff_batch_plan / huff_batch_run, HUFF_ERR_CUDA. */
+#define HUFF_TUNE_FORCE 1u      /* ignore the cache and tune again */
+#define HUFF_TUNE_ROUND_TRIP 2u /* compress: score by compress + decompress */
+huff_status_t huff_batch_autotune(const huff_batch_desc_t *descs, uint32_t count, huff_op_t op,
+                                  const huff_batch_params_t *base, uint32_t flags,
+                                  huff_batch_params_t *best, huff_stream_t stream);
 
 /* Free a plan (NULL is ignored).  Its runs must have completed. */
 void huff_batch_destroy(huff_batch_plan_t *plan);

@@ -38,6 +38,8 @@ _lib = None
 
 HUFF_BATCH_COMPRESS = 0
 HUFF_BATCH_DECOMPRESS = 1
+HUFF_TUNE_FORCE = 1
+HUFF_TUNE_ROUND_TRIP = 2
 
 
 class BatchDesc(ctypes.Structure):
@@ -50,7 +52,8 @@ class BatchDesc(ctypes.Structure):
 class BatchParams(ctypes.Structure):
     """huff_batch_params_t"""
     _fields_ = [("chunk_symbols", ctypes.c_uint32), ("ctas_per_sm", ctypes.c_uint32),
-                ("decode_lanes", ctypes.c_uint32), ("use_graph", ctypes.c_uint32)]
+                ("decode_lanes", ctypes.c_uint32), ("use_graph", ctypes.c_uint32),
+                ("barrier_extra", ctypes.c_uint32)]
 
 
 class ServerConfig(ctypes.Structure):
@@ -141,6 +144,10 @@ def lib() -> ctypes.CDLL:
                                       ctypes.POINTER(i32)]
         L.huff_batch_destroy.restype = None
         L.huff_batch_destroy.argtypes = [vp]
+        L.huff_batch_autotune.restype = i32
+        L.huff_batch_autotune.argtypes = [ctypes.POINTER(BatchDesc), u32, ctypes.c_int,
+                                          ctypes.POINTER(BatchParams), u32,
+                                          ctypes.POINTER(BatchParams), vp]
         _lib = L
     return _lib
 
@@ -388,6 +395,7 @@ class BatchPlan:
             descs[i] = BatchDesc(x.data_ptr() if x.numel() else 0, nb, y.data_ptr(), y.numel(),
                                  self.out_bytes.data_ptr() + 8 * i, self.status.data_ptr() + 4 * i)
         self._descs = descs
+        self.op = op
         h = ctypes.c_void_p(0)
         prm = ctypes.byref(params) if params is not None else None
         _check(lib().huff_batch_plan(descs, count, op, prm, ctypes.byref(h)), "huff_batch_plan")
@@ -395,6 +403,16 @@ class BatchPlan:
 
     def run(self, stream=None):
         _check(lib().huff_batch_run(self._h, _stream(stream)), "huff_batch_run")
+
+    def autotune(self, base: BatchParams | None = None, flags: int = 0, stream=None) -> BatchParams:
+        """huff_batch_autotune on this plan's buffers: the fastest parameters
+        (running the batch several times).  Build a new plan with them."""
+        best = BatchParams()
+        prm = ctypes.byref(base) if base is not None else None
+        _check(lib().huff_batch_autotune(self._descs, len(self.inputs), self.op, prm, flags,
+                                         ctypes.byref(best), _stream(stream)),
+               "huff_batch_autotune")
+        return best
 
     def info(self):
         p, g, used = BatchParams(), ctypes.c_uint32(0), ctypes.c_int32(0)

@@ -38,7 +38,7 @@ namespace {
 
 // Sense-free generation barrier over all CTAs of a cooperative launch.
 // Returns false (uniformly) when a wait gave up.
-__device__ bool grid_barrier(unsigned int *ctl, int32_t *fail)
+__device__ bool grid_barrier(unsigned int *ctl, int32_t *fail, uint32_t extra)
 {
     __shared__ int s_ok;
     __syncthreads();
@@ -48,7 +48,7 @@ __device__ bool grid_barrier(unsigned int *ctl, int32_t *fail)
         __threadfence();
         const unsigned int arrived = atomicAdd(ctl + kCtlArrive, 1u) + 1;
         int ok = 1;
-        if (arrived == gridDim.x) {
+        if (arrived == gridDim.x + extra) {
             ctl[kCtlArrive] = 0;
             __threadfence();
             atomicAdd(ctl + kCtlGen, 1u);
@@ -131,7 +131,7 @@ __global__ void __launch_bounds__(kBatchBlock, 3) k_batch_compress(BatchArgs a)
     // phase 0: clear the per-buffer statuses
     for (uint32_t b = blockIdx.x * kBatchBlock + tid; b < a.count; b += gridDim.x * kBatchBlock)
         *a.bufs[b].status = 0;
-    if (!grid_barrier(a.ctl, a.fail)) {
+    if (!grid_barrier(a.ctl, a.fail, a.barrier_extra)) {
         fail_all(a.bufs, a.count);
         return;
     }
@@ -168,7 +168,7 @@ __global__ void __launch_bounds__(kBatchBlock, 3) k_batch_compress(BatchArgs a)
             __syncthreads();
         }
     }
-    if (!grid_barrier(a.ctl, a.fail)) {
+    if (!grid_barrier(a.ctl, a.fail, a.barrier_extra)) {
         fail_all(a.bufs, a.count);
         return;
     }
@@ -232,7 +232,7 @@ __global__ void __launch_bounds__(kBatchBlock, 3) k_batch_compress(BatchArgs a)
             __syncthreads();
         }
     }
-    if (!grid_barrier(a.ctl, a.fail)) {
+    if (!grid_barrier(a.ctl, a.fail, a.barrier_extra)) {
         fail_all(a.bufs, a.count);
         return;
     }
@@ -302,7 +302,7 @@ __global__ void __launch_bounds__(kBatchBlock, 2) k_batch_decompress(BatchArgs a
         }
         a.dec_items[b] = items;
     }
-    if (!grid_barrier(a.ctl, a.fail)) {
+    if (!grid_barrier(a.ctl, a.fail, a.barrier_extra)) {
         fail_all(a.bufs, a.count);
         return;
     }
@@ -327,7 +327,7 @@ __global__ void __launch_bounds__(kBatchBlock, 2) k_batch_decompress(BatchArgs a
         if (tid == kBatchBlock - 1)
             a.dec_items[a.count] = before;
     }
-    if (!grid_barrier(a.ctl, a.fail)) {
+    if (!grid_barrier(a.ctl, a.fail, a.barrier_extra)) {
         fail_all(a.bufs, a.count);
         return;
     }
@@ -421,7 +421,8 @@ void batch_layout(const huff_batch_desc_t *descs, uint32_t count, huff_op_t op, 
     L.upload_bytes = L.o_di;
 }
 
-BatchArgs batch_args(const BatchLayout &L, void *d_block, uint32_t cs, uint32_t lanes)
+BatchArgs batch_args(const BatchLayout &L, void *d_block, uint32_t cs, uint32_t lanes,
+                     uint32_t barrier_extra)
 {
     uint8_t *blk = static_cast<uint8_t *>(d_block);
     BatchArgs a;
@@ -438,6 +439,7 @@ BatchArgs batch_args(const BatchLayout &L, void *d_block, uint32_t cs, uint32_t 
     a.min_lanes = lanes;
     a.ctl = reinterpret_cast<unsigned int *>(blk + L.o_ctl);
     a.fail = reinterpret_cast<int32_t *>(blk + L.o_ctl + sizeof(unsigned int) * kCtlWords);
+    a.barrier_extra = barrier_extra;
     return a;
 }
 
@@ -505,7 +507,7 @@ huff_status_t batch_check(const huff_batch_desc_t *descs, uint32_t count, huff_o
         return HUFF_ERR_INVALID_ARG;
     if (op == HUFF_BATCH_COMPRESS && !chunk_symbols_valid(prm.chunk_symbols))
         return HUFF_ERR_INVALID_ARG;
-    if (prm.decode_lanes == 0 || prm.decode_lanes > 1024)
+    if (prm.decode_lanes == 0 || prm.decode_lanes > 1024 || prm.barrier_extra > 65536)
         return HUFF_ERR_INVALID_ARG;
     for (uint32_t i = 0; i < count; ++i) {
         const huff_batch_desc_t &d = descs[i];
@@ -561,8 +563,9 @@ void huff_batch_default_params(huff_batch_params_t *params)
         return;
     params->chunk_symbols = HUFF_DEFAULT_CHUNK_SYMBOLS;
     params->ctas_per_sm = 0;  // as many as fit
-    params->decode_lanes = 32;
+    params->decode_lanes = 128;
     params->use_graph = 1;
+    params->barrier_extra = 0;
 }
 
 huff_status_t huff_batch_plan(const huff_batch_desc_t *descs, uint32_t count, huff_op_t op,
@@ -598,7 +601,7 @@ huff_status_t huff_batch_plan(const huff_batch_desc_t *descs, uint32_t count, hu
         free_plan(p);
         return HUFF_ERR_CUDA;
     }
-    p->args = batch_args(L, p->d_block, prm.chunk_symbols, prm.decode_lanes);
+    p->args = batch_args(L, p->d_block, prm.chunk_symbols, prm.decode_lanes, prm.barrier_extra);
     int per_sm = batch_occupancy(op);
     if (per_sm < 1) {
         free_plan(p);

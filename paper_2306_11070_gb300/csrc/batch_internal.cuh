@@ -38,6 +38,7 @@ struct BatchArgs {
     uint32_t min_lanes;             // decompress: lanes per buffer to aim for
     unsigned int *ctl;              // kCtlWords
     int32_t *fail;                  // whole-batch failure (barrier timeout)
+    uint32_t barrier_extra;         // test hook: CTAs the barriers wait for beyond the grid
 };
 
 // Host-side description of a batch's device block (see batch_layout).
@@ -52,7 +53,8 @@ struct BatchLayout {
 };
 
 void batch_layout(const huff_batch_desc_t *descs, uint32_t count, huff_op_t op, BatchLayout &L);
-BatchArgs batch_args(const BatchLayout &L, void *d_block, uint32_t cs, uint32_t lanes);
+BatchArgs batch_args(const BatchLayout &L, void *d_block, uint32_t cs, uint32_t lanes,
+                     uint32_t barrier_extra = 0);
 cudaError_t batch_upload(const BatchLayout &L, void *d_block, uint8_t *host, cudaStream_t s);
 int batch_occupancy(huff_op_t op);
 cudaError_t batch_launch(huff_op_t op, const BatchArgs &args, unsigned grid, cudaStream_t s);

@@ -181,9 +181,10 @@ __device__ __forceinline__ void cp_async_wait()
 // Ring invariant: after every top-up more than kInRing - 4 words are
 // requested beyond the next one to read, in groups of 4, and the three most
 // recent groups may still be in flight; so the next 1 + 16 words have
-// landed, and one window moves at most 14 words into the bit buffer (a
+// landed, and one window moves at most 15 words into the bit buffer (a
 // checked window reads at most 12 codes of <= 32 bits, an unchecked one at
-// most one such code and 32 of <= 12 bits, and the buffer holds < 64 bits).
+// most one such code and 32 of <= 12 bits plus one spare refill, and the
+// buffer holds < 64 bits).
 // Requests never reach the slot of a word that has not been read.  Each
 // top-up also asks L2 for the line 64 words past the requests.
 struct Bits {
@@ -808,19 +809,22 @@ __device__ __forceinline__ bool decode_task(const StreamInfo &si, uint32_t S, ui
                 // and resolves it at the start of the next.  Software
                 // pipelined: lookup j+1's table load is issued before lookup
                 // j's output is appended.
+                // Pairs of lookups: a refill (>= 32 bits) serves both, as
+                // two lookups use at most 24 bits.  The last pair's refill
+                // and table load for a lookup beyond the window are
+                // harmless (one more word at most, within the ring bound).
                 uint32_t ent = lut_ld(lut_s, rs.bh);
-#pragma unroll
-                for (int j = 0; j < kWindow; ++j) {
-                    const uint32_t t = ent >> 24;
-                    rs.consume_t(t);
-                    uint32_t nxt_ent = 0;
-                    if (j + 1 < kWindow) {
-                        if ((j & 1) == 1)
-                            rs.refill();  // two lookups use at most 24 of >= 32 bits
-                        nxt_ent = lut_ld(lut_s, rs.bh);
-                    }
-                    ow.emit(imad(t, kc[kMinusTop8], ent), t >> 6);  // the symbol bytes
-                    ent = nxt_ent;
+#pragma unroll 4
+                for (int p = 0; p < kWindow / 2; ++p) {
+                    const uint32_t t0 = ent >> 24;
+                    rs.consume_t(t0);
+                    const uint32_t ent1 = lut_ld(lut_s, rs.bh);
+                    ow.emit(imad(t0, kc[kMinusTop8], ent), t0 >> 6);  // the symbol bytes
+                    const uint32_t t1 = ent1 >> 24;
+                    rs.consume_t(t1);
+                    rs.refill();
+                    ent = lut_ld(lut_s, rs.bh);
+                    ow.emit(imad(t1, kc[kMinusTop8], ent1), t1 >> 6);
                 }
             } else {
 #pragma unroll 1

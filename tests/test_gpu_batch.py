@@ -8,6 +8,8 @@ its neighbours succeed) and, for decompression, corrupt streams whose
 statuses must match the oracle's.  Each plan runs twice to check that the
 runs are repeatable.
 """
+import time
+
 import numpy as np
 import pytest
 import torch
@@ -151,3 +153,68 @@ def test_batch_many_small_buffers_one_chunk_each():
         assert np.array_equal(dec[i][:x.size].cpu().numpy(), x), i
     plan.close()
     dplan.close()
+
+
+def test_barrier_timeout_reports_status_and_context_survives():
+    # The test hook makes every grid barrier wait for one CTA more than the
+    # grid holds: the bounded spins run out (no fault, no hang), every buffer
+    # reports HUFF_ERR_TIMEOUT, and the GPU context stays usable.
+    xs = [synth.text(20000 + 1000 * i, 900 + i) for i in range(8)]
+    params = hg.huff_batch_default_params()
+    params.barrier_extra = 1
+    plan, ins, outs = _compress_batch(xs, params=params)
+    t0 = time.time()
+    plan.run()
+    torch.cuda.synchronize()
+    assert time.time() - t0 < 120
+    assert (plan.status.cpu().numpy() == hg.HUFF_ERR_TIMEOUT).all()
+    plan.close()
+    plan2, _, outs2 = _compress_batch(xs)
+    plan2.run()
+    torch.cuda.synchronize()
+    st = plan2.status.cpu().numpy()
+    nb = plan2.out_bytes.cpu().numpy()
+    assert (st == 0).all()
+    for i in (0, 7):
+        ost, ref = oracle.compress(xs[i])
+        assert np.array_equal(outs2[i][:nb[i]].cpu().numpy(), ref)
+    plan2.close()
+
+
+def test_autotune_decompress_and_round_trip_compress():
+    xs = [synth.text(int(n), 700 + i) for i, n in
+          enumerate(synth.log_uniform_sizes(96, seed=11, lo=1024, hi=1 << 20))]
+    # compress, tuned by compress + decompress time; outputs hold the chosen
+    # setting's streams afterwards
+    plan, ins, outs = _compress_batch(xs, cs=4096)  # outputs sized for either chunk size
+    base = hg.huff_batch_default_params()
+    best = plan.autotune(base, flags=hg.HUFF_TUNE_ROUND_TRIP)
+    assert best.chunk_symbols in (16384, 4096)
+    assert best.decode_lanes in (32, 64, 128, 256)
+    plan.close()
+    plan2, _, outs2 = _compress_batch(xs, cs=best.chunk_symbols, params=best)
+    plan2.run()
+    torch.cuda.synchronize()
+    nb = plan2.out_bytes.cpu().numpy()
+    assert (plan2.status.cpu().numpy() == 0).all()
+    for i in range(0, len(xs), 7):
+        ost, ref = oracle.compress(xs[i], best.chunk_symbols)
+        assert np.array_equal(outs2[i][:nb[i]].cpu().numpy(), ref), i
+    # decompress, tuned on those streams; a second call is served from cache
+    streams = [outs2[i][:nb[i]].clone() for i in range(len(xs))]
+    dec = [torch.zeros(max(x.size, 16), dtype=torch.uint8, device="cuda") for x in xs]
+    dplan = hg.BatchPlan(streams, dec, hg.HUFF_BATCH_DECOMPRESS)
+    dbest = dplan.autotune()
+    t0 = time.time()
+    dbest2 = dplan.autotune()
+    assert time.time() - t0 < 0.05
+    assert (dbest2.decode_lanes, dbest2.ctas_per_sm) == (dbest.decode_lanes, dbest.ctas_per_sm)
+    dplan.close()
+    tuned = hg.BatchPlan(streams, dec, hg.HUFF_BATCH_DECOMPRESS, dbest)
+    tuned.run()
+    torch.cuda.synchronize()
+    assert (tuned.status.cpu().numpy() == 0).all()
+    for i, x in enumerate(xs):
+        assert np.array_equal(dec[i][:x.size].cpu().numpy(), x), i
+    tuned.close()
+    plan2.close()
