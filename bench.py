@@ -247,7 +247,8 @@ def measure_batched(hg, synth, torch, count=4096):
             "speedup_compress": pc / tc, "speedup_decompress": pd / td}
 
 
-def measure_served(hg, synth, oracle, torch, loads=(20.0, 100.0), seconds=1.5, max_requests=3000):
+def measure_served(hg, synth, oracle, torch, loads=(10.0, 20.0, 50.0, 100.0, 150.0, 200.0),
+                   seconds=1.0, max_requests=2000):
     """Config 5: open-loop Poisson arrivals of 50/50 compress/decompress
     requests over a pool of 64 text buffers with log-uniform sizes
     4 KiB..16 MiB (streams for decompression pre-made by the oracle), served

@@ -359,7 +359,7 @@ void huff_server_default_config(huff_server_cfg_t *cfg)
     cfg->max_rounds = 3;
     cfg->max_batch = 256;
     cfg->chunk_symbols = HUFF_DEFAULT_CHUNK_SYMBOLS;
-    cfg->decode_lanes = 32;
+    cfg->decode_lanes = 128;
 }
 
 huff_status_t huff_server_create(const huff_server_cfg_t *cfg, huff_server_t **out)
