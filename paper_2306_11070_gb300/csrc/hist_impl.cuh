@@ -34,14 +34,18 @@ __device__ __forceinline__ void count16(uint32_t col, uint4 v)
     count_word(col, v.w);
 }
 
-// Sum of bin `tid` over its 32 columns; the rotation keeps one warp's reads
-// in distinct banks.
+// Sum of bin `tid` over its 32 columns, in eight 16-byte loads.  The
+// rotation spreads one warp's loads over all eight 16-byte bank groups (four
+// lanes per group, the minimum for 512 bytes).
 __device__ __forceinline__ uint32_t fold_bin(const uint32_t *cnt, int tid)
 {
+    const uint4 *row = reinterpret_cast<const uint4 *>(cnt + (tid << 5));
     uint32_t s = 0;
 #pragma unroll
-    for (int l = 0; l < 32; ++l)
-        s += cnt[(tid << 5) + ((l + tid) & 31)];
+    for (int j = 0; j < 8; ++j) {
+        const uint4 v = row[(j + tid) & 7];
+        s += (v.x + v.y) + (v.z + v.w);
+    }
     return s;
 }
 

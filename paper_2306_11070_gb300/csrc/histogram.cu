@@ -27,7 +27,7 @@ __global__ void __launch_bounds__(kHistBlock)
     k_histogram(const uint8_t *__restrict__ in, uint64_t n, unsigned long long *__restrict__ hist,
                 uint16_t *__restrict__ unit_hist)
 {
-    __shared__ uint32_t cnt[256 * 32];
+    __shared__ __align__(16) uint32_t cnt[256 * 32];
     const int tid = threadIdx.x, lane = tid & 31;
     for (int i = tid; i < 256 * 32; i += kHistBlock)
         cnt[i] = 0;

@@ -189,9 +189,10 @@ def test_empty_input():
     assert st == 0 and n == 0
 
 
-@pytest.mark.parametrize("k", [25, 28, 30, 32])
+@pytest.mark.parametrize("k", [13, 17, 24, 25, 26, 28, 30, 32])
 def test_long_codes(k):
-    # Fibonacci counts give the deepest trees: codes up to k-1 bits
+    # Fibonacci counts give the deepest trees: codes up to k-1 bits (24 is
+    # the longest the fast encoder takes, 12 the longest the decode table holds)
     f = [1, 1]
     while len(f) < k:
         f.append(f[-1] + f[-2])
