@@ -55,6 +55,8 @@ def _configure(lib):
     lib.oracle_histogram.argtypes = [u8p, u64, u64p]
     lib.oracle_code_lengths.restype = ctypes.c_int
     lib.oracle_code_lengths.argtypes = [u64p, u8p]
+    lib.oracle_code_lengths_limited.restype = ctypes.c_int
+    lib.oracle_code_lengths_limited.argtypes = [u64p, u32, u8p]
     lib.oracle_canonical_codes.restype = None
     lib.oracle_canonical_codes.argtypes = [u8p, u32p]
     lib.oracle_max_stream_size.restype = u64
@@ -116,6 +118,17 @@ def code_lengths(hist):
     assert h.size == 256
     ln = np.zeros(256, dtype=np.uint8)
     st = _load().oracle_code_lengths(_p(h, ctypes.c_uint64), _p(ln, ctypes.c_uint8))
+    return st, ln
+
+
+def code_lengths_limited(hist, limit: int):
+    """(status, len u8[256]): optimal code lengths of at most `limit` bits
+    (the Huffman lengths when they fit, else package-merge)."""
+    h = np.ascontiguousarray(np.asarray(hist, dtype=np.uint64))
+    assert h.size == 256
+    ln = np.zeros(256, dtype=np.uint8)
+    st = _load().oracle_code_lengths_limited(_p(h, ctypes.c_uint64), limit,
+                                             _p(ln, ctypes.c_uint8))
     return st, ln
 
 

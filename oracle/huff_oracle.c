@@ -185,6 +185,105 @@ int oracle_code_lengths(const uint64_t hist[256], uint8_t len[256])
     return ORACLE_OK;
 }
 
+/* ---- step 2', length-limited: package-merge ---------------------------------
+ * Not in the paper: an extension of its tree step that keeps every code
+ * within `limit` bits (Larmore & Hirschberg, "A fast algorithm for optimal
+ * length-restricted Huffman codes", 1990).  Readings:
+ *   L1 when the Huffman lengths of step 2 already fit, they are the answer;
+ *   L2 otherwise the coin-collector construction: list 1 = the present
+ *      symbols sorted by (weight, byte); list i = list 1 merged with the
+ *      packages (sums of consecutive pairs) of list i-1, a symbol before a
+ *      package of equal weight; the first 2n-2 items of list `limit` are
+ *      taken, and each taken package takes its two items of the list below;
+ *      a symbol's length is the number of taken items that contain it;
+ *   L3 limit outside 1..32 is an invalid argument; more distinct symbols
+ *      than 2^limit cannot be coded (CODE_TOO_LONG); one symbol: length 1.
+ */
+typedef struct {
+    uint64_t w;
+    int leaf; /* index into the sorted symbols, or -1 for a package */
+} item_t;
+
+int oracle_code_lengths_limited(const uint64_t hist[256], uint32_t limit, uint8_t len[256])
+{
+    uint64_t sw[256];
+    int sid[256], n = 0;
+    if (limit < 1 || limit > ORACLE_MAX_CODE_LEN)
+        return ORACLE_ERR_INVALID_ARG;
+    int st = oracle_code_lengths(hist, len);
+    if (st == ORACLE_OK) {
+        uint32_t mx = 0;
+        for (int s = 0; s < 256; ++s)
+            if (len[s] > mx)
+                mx = len[s];
+        if (mx <= limit)
+            return ORACLE_OK; /* L1 */
+    }
+    memset(len, 0, 256);
+    /* the present symbols sorted by (weight, byte): insertion sort */
+    for (int s = 0; s < 256; ++s) {
+        if (!hist[s])
+            continue;
+        int j = n++;
+        while (j > 0 && (sw[j - 1] > hist[s] || (sw[j - 1] == hist[s] && sid[j - 1] > s))) {
+            sw[j] = sw[j - 1];
+            sid[j] = sid[j - 1];
+            --j;
+        }
+        sw[j] = hist[s];
+        sid[j] = s;
+    }
+    if (limit < 32 && (uint64_t)n > (1ull << limit))
+        return ORACLE_ERR_CODE_TOO_LONG; /* L3 */
+    /* lists 1..limit; list i has at most 2n - 1 items */
+    item_t *lists = (item_t *)malloc(sizeof(item_t) * (size_t)limit * 512);
+    int cnt[ORACLE_MAX_CODE_LEN + 1];
+    if (!lists)
+        return ORACLE_ERR_INVALID_ARG;
+    for (int j = 0; j < n; ++j) {
+        lists[j].w = sw[j];
+        lists[j].leaf = j;
+    }
+    cnt[1] = n;
+    for (uint32_t i = 2; i <= limit; ++i) {
+        const item_t *prev = lists + (size_t)(i - 2) * 512;
+        item_t *cur = lists + (size_t)(i - 1) * 512;
+        const int np = cnt[i - 1] / 2;
+        int a = 0, b = 0, k = 0;
+        while (a < n || b < np) {
+            const uint64_t pw = b < np ? prev[2 * b].w + prev[2 * b + 1].w : 0;
+            if (a < n && (b >= np || sw[a] <= pw)) { /* symbol first on a tie */
+                cur[k].w = sw[a];
+                cur[k].leaf = a;
+                ++a;
+            } else {
+                cur[k].w = pw;
+                cur[k].leaf = -1;
+                ++b;
+            }
+            ++k;
+        }
+        cnt[i] = k;
+    }
+    /* take the first 2n-2 items of the last list and walk down */
+    int take = 2 * n - 2;
+    for (uint32_t i = limit; i >= 1 && take > 0; --i) {
+        const item_t *cur = lists + (size_t)(i - 1) * 512;
+        int packages = 0;
+        for (int k = 0; k < take; ++k) {
+            if (cur[k].leaf >= 0)
+                len[sid[cur[k].leaf]] += 1;
+            else
+                ++packages;
+        }
+        take = 2 * packages;
+    }
+    free(lists);
+    if (n == 1)
+        len[sid[0]] = 1; /* L3 */
+    return ORACLE_OK;
+}
+
 /* ---- step 3: canonical codes (R5) ---------------------------------------- */
 void oracle_canonical_codes(const uint8_t len[256], uint32_t code[256])
 {

@@ -20,6 +20,7 @@
 
 void oracle_histogram(const uint8_t *x, uint64_t n, uint64_t hist[256]);
 int oracle_code_lengths(const uint64_t hist[256], uint8_t len[256]);
+int oracle_code_lengths_limited(const uint64_t hist[256], uint32_t limit, uint8_t len[256]);
 void oracle_canonical_codes(const uint8_t len[256], uint32_t code[256]);
 uint64_t oracle_max_stream_size(uint64_t n, uint32_t cs);
 int oracle_chunk_offsets(const uint8_t *x, uint64_t n, uint32_t cs, const uint8_t len[256],

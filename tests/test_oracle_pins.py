@@ -384,3 +384,83 @@ def test_entropy_of_text_workload_is_text_like():
     avg = float((oracle.histogram(x) * ln).sum()) / x.size
     assert 4.0 < avg < 5.0
     assert math.isclose(avg, 4.52, abs_tol=0.15)
+
+
+# ---------------------------------------------------------------- length-limited codes
+def test_limited_hand_example():
+    # weights 1,1,2,4: Huffman lengths 3,3,2,1; within 2 bits all four take 2
+    h = np.zeros(256, dtype=np.uint64)
+    h[:4] = [1, 1, 2, 4]
+    st, ln = oracle.code_lengths_limited(h, 2)
+    assert st == oracle.OK and list(ln[:4]) == [2, 2, 2, 2] and not ln[4:].any()
+    st, ln = oracle.code_lengths_limited(h, 3)
+    assert st == oracle.OK and list(ln[:4]) == [3, 3, 2, 1]
+
+
+def _min_cost_limited(w, limit):
+    k = len(w)
+    best = None
+    for lens in itertools.product(range(1, limit + 1), repeat=k):
+        if sum(2.0 ** -l for l in lens) <= 1.0 + 1e-12:
+            c = sum(a * b for a, b in zip(w, lens))
+            best = c if best is None else min(best, c)
+    return best
+
+
+def test_limited_bruteforce_optimal():
+    rng = np.random.default_rng(17)
+    for trial in range(40):
+        k = int(rng.integers(2, 8))
+        w = [int(v) for v in rng.integers(1, 60, size=k)]
+        if trial % 4 == 0:
+            w = [1 << min(j, 20) for j in range(k)]  # deep trees
+        h = np.zeros(256, dtype=np.uint64)
+        syms = rng.choice(256, size=k, replace=False)
+        h[syms] = w
+        for limit in range(max(1, math.ceil(math.log2(k))), k):
+            st, ln = oracle.code_lengths_limited(h, limit)
+            assert st == oracle.OK
+            assert int(ln.max()) <= limit and np.all(ln[h > 0] >= 1) and not ln[h == 0].any()
+            got = sum(int(h[s]) * int(ln[s]) for s in syms)
+            assert got == _min_cost_limited(w, limit), (w, limit)
+
+
+def test_limited_complete_and_monotone():
+    for h in _random_hists(120, 19):
+        st, hl = oracle.code_lengths(h)
+        k = int((h > 0).sum())
+        lo = max(1, math.ceil(math.log2(k)))
+        prev = None
+        for limit in range(lo, int(hl.max()) + 2):
+            st, ln = oracle.code_lengths_limited(h, limit)
+            assert st == oracle.OK and int(ln.max()) <= limit
+            if k >= 2:
+                assert sum(1 << (32 - int(v)) for v in ln[h > 0]) == 1 << 32
+            cost = int((h * ln).sum())
+            assert prev is None or cost <= prev
+            prev = cost
+        # a limit the Huffman code already meets leaves it unchanged
+        st, ln = oracle.code_lengths_limited(h, int(hl.max()))
+        assert np.array_equal(ln, hl)
+
+
+def test_limited_fibonacci_and_statuses():
+    h = np.zeros(256, dtype=np.uint64)
+    h[:34] = _fib(34)
+    assert oracle.code_lengths(h)[0] == oracle.ERR_CODE_TOO_LONG
+    st, ln = oracle.code_lengths_limited(h, 32)
+    assert st == oracle.OK and int(ln.max()) == 32
+    assert sum(1 << (32 - int(v)) for v in ln[:34]) == 1 << 32
+    st, ln = oracle.code_lengths_limited(h, 12)
+    assert st == oracle.OK and int(ln.max()) == 12
+    h = np.zeros(256, dtype=np.uint64)
+    h[:5] = 1
+    assert oracle.code_lengths_limited(h, 2)[0] == oracle.ERR_CODE_TOO_LONG   # 5 > 2^2
+    assert oracle.code_lengths_limited(h, 0)[0] == oracle.ERR_INVALID_ARG
+    assert oracle.code_lengths_limited(h, 33)[0] == oracle.ERR_INVALID_ARG
+    h = np.zeros(256, dtype=np.uint64)
+    h[9] = 3
+    st, ln = oracle.code_lengths_limited(h, 1)
+    assert st == oracle.OK and ln[9] == 1 and int(ln.sum()) == 1
+    st, ln = oracle.code_lengths_limited(np.zeros(256, dtype=np.uint64), 4)
+    assert st == oracle.OK and not ln.any()
