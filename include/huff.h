@@ -127,6 +127,18 @@ huff_status_t huff_histogram_units(const uint8_t *d_in, uint64_t n, uint64_t *d_
 huff_status_t huff_build_codebook(const uint64_t *d_hist, huff_codebook_t *d_cb,
                                   int32_t *d_status, huff_stream_t stream);
 
+/* Length-limited codebook (an extension of the tree step, not in the
+ * paper): the code lengths are the Huffman lengths of huff_build_codebook
+ * when none exceeds max_len, else the optimal lengths of at most max_len
+ * bits by package-merge (Larmore & Hirschberg 1990; the present bytes sorted
+ * by (weight, byte), a byte before a package of equal weight).  Canonical
+ * codes as above.  max_len in 1..32 (else HUFF_ERR_INVALID_ARG); more
+ * distinct bytes than 2^max_len is HUFF_ERR_CODE_TOO_LONG in *d_status.
+ * With max_len <= 12 every code fits the decoder's lookup table. */
+huff_status_t huff_build_codebook_limited(const uint64_t *d_hist, uint32_t max_len,
+                                          huff_codebook_t *d_cb, int32_t *d_status,
+                                          huff_stream_t stream);
+
 /* Encode d_in[0, n) with *d_cb into the stream layout above at d_out.
  * Method 1's coding step with Method 2's segments as chunks of
  * chunk_symbols bytes (a multiple of 16 in [16, 2^24]).

@@ -110,6 +110,8 @@ def lib() -> ctypes.CDLL:
         L.huff_encode_units.argtypes = [vp, u64, vp, vp, u32, vp, u64, vp, vp, u64, vp, vp]
         L.huff_build_codebook.restype = i32
         L.huff_build_codebook.argtypes = [vp, vp, vp, vp]
+        L.huff_build_codebook_limited.restype = i32
+        L.huff_build_codebook_limited.argtypes = [vp, u32, vp, vp, vp]
         L.huff_encode.restype = i32
         L.huff_encode.argtypes = [vp, u64, vp, u32, vp, u64, vp, vp, u64, vp, vp]
         L.huff_encode_noalloc.restype = i32
@@ -243,6 +245,19 @@ def huff_build_codebook(d_hist: torch.Tensor, d_cb: torch.Tensor | None = None,
         d_status = new_status(d_hist.device)
     _check(lib().huff_build_codebook(_ptr(d_hist), _ptr(d_cb), _ptr(d_status), _stream(stream)),
            "huff_build_codebook")
+    return d_cb, d_status
+
+
+def huff_build_codebook_limited(d_hist: torch.Tensor, max_len: int,
+                                d_cb: torch.Tensor | None = None,
+                                d_status: torch.Tensor | None = None, stream=None):
+    """(codebook bytes, status): codes of at most max_len bits."""
+    if d_cb is None:
+        d_cb = torch.empty(CODEBOOK_BYTES, dtype=torch.uint8, device=d_hist.device)
+    if d_status is None:
+        d_status = new_status(d_hist.device)
+    _check(lib().huff_build_codebook_limited(_ptr(d_hist), max_len, _ptr(d_cb), _ptr(d_status),
+                                             _stream(stream)), "huff_build_codebook_limited")
     return d_cb, d_status
 
 

@@ -119,6 +119,17 @@ huff_status_t huff_build_codebook(const uint64_t *d_hist, huff_codebook_t *d_cb,
                                              reinterpret_cast<cudaStream_t>(stream)));
 }
 
+huff_status_t huff_build_codebook_limited(const uint64_t *d_hist, uint32_t max_len,
+                                          huff_codebook_t *d_cb, int32_t *d_status,
+                                          huff_stream_t stream)
+{
+    if (!d_hist || !d_cb || !d_status || max_len < 1 || max_len > kMaxCodeLen)
+        return HUFF_ERR_INVALID_ARG;
+    return cuda_status(launch_build_codebook(reinterpret_cast<const unsigned long long *>(d_hist),
+                                             d_cb, d_status,
+                                             reinterpret_cast<cudaStream_t>(stream), max_len));
+}
+
 huff_status_t huff_encode(const uint8_t *d_in, uint64_t n, const huff_codebook_t *d_cb,
                           uint32_t chunk_symbols, uint8_t *d_out, uint64_t out_cap,
                           uint64_t *d_out_bytes, void *d_ws, uint64_t ws_bytes, int32_t *d_status,

@@ -22,18 +22,20 @@ constexpr int kCbBlock = 256;
 
 __global__ void __launch_bounds__(kCbBlock)
     k_build_codebook(const unsigned long long *__restrict__ hist, huff_codebook_t *__restrict__ cb,
-                     int32_t *status)
+                     int32_t *status, int limit, int limited)
 {
     __shared__ cbk::CodebookShared sh;
-    cbk::build_codebook(hist, cb, status, sh);
+    cbk::build_codebook(hist, cb, status, sh, limit, limited != 0);
 }
 
 }  // namespace
 
 cudaError_t launch_build_codebook(const unsigned long long *d_hist, huff_codebook_t *d_cb,
-                                  int32_t *d_status, cudaStream_t s)
+                                  int32_t *d_status, cudaStream_t s, uint32_t limit)
 {
-    k_build_codebook<<<1, kCbBlock, 0, s>>>(d_hist, d_cb, d_status);
+    const bool limited = limit != 0;
+    k_build_codebook<<<1, kCbBlock, 0, s>>>(d_hist, d_cb, d_status,
+                                            limited ? (int)limit : (int)kMaxCodeLen, limited);
     return cudaGetLastError();
 }
 

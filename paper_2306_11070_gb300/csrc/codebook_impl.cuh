@@ -10,6 +10,9 @@ namespace cbk {
 
 struct CodebookShared {
     unsigned long long w[256];
+    unsigned long long pm[2][512];             // package-merge: the previous and current list
+    uint16_t pos[kMaxCodeLen + 1][256];        // package-merge: position of each leaf per list
+    int pm_take[kMaxCodeLen + 1];              // package-merge: leaves taken from each list
     unsigned long long nw[511];  // [0,m): leaves by (weight, byte); [m,2m-1): merged
     int16_t par[511];
     int16_t dep[511];
@@ -21,11 +24,88 @@ struct CodebookShared {
     int s_max;
 };
 
-// Build *cb from hist (u64[256]); blockDim.x must be 256.  On a code longer
-// than 32 bits *cb is cleared and HUFF_ERR_CODE_TOO_LONG goes to *status.
+// Code lengths of at most `limit` bits for the m leaves nw[0..m) (sorted by
+// (weight, byte)), by package-merge (Larmore & Hirschberg 1990): list 1 =
+// the leaves; list i = the leaves merged with the packages (sums of
+// consecutive pairs) of list i-1, a leaf before a package of equal weight;
+// the first 2m-2 items of list `limit` are taken and each taken package takes
+// its two items of the list below.  A leaf's length is the number of lists
+// it is taken from, and the leaves taken from a list are a prefix of the
+// sorted leaves.  Every merge position is a binary search (one item per
+// thread); 2 <= m <= 2^limit.
+__device__ __forceinline__ void package_merge(int m, int limit, CodebookShared &sh)
+{
+    const int t = threadIdx.x;
+    int cnt = m;  // items in the previous list
+    if (t < m) {
+        sh.pm[0][t] = sh.nw[t];
+        sh.pos[1][t] = (uint16_t)t;
+    }
+    __syncthreads();
+    for (int i = 2; i <= limit; ++i) {
+        const unsigned long long *prev = sh.pm[(i - 2) & 1];
+        unsigned long long *cur = sh.pm[(i - 1) & 1];
+        const int np = cnt >> 1;
+        if (t < m) {  // leaf t goes after the packages lighter than it
+            const unsigned long long w = sh.nw[t];
+            int lo = 0, hi = np;
+            while (lo < hi) {
+                const int mid = (lo + hi) >> 1;
+                if (prev[2 * mid] + prev[2 * mid + 1] < w)
+                    lo = mid + 1;
+                else
+                    hi = mid;
+            }
+            cur[t + lo] = w;
+            sh.pos[i][t] = (uint16_t)(t + lo);
+        }
+        if (t < np) {  // package t goes after the leaves not heavier than it
+            const unsigned long long w = prev[2 * t] + prev[2 * t + 1];
+            int lo = 0, hi = m;
+            while (lo < hi) {
+                const int mid = (lo + hi) >> 1;
+                if (sh.nw[mid] <= w)
+                    lo = mid + 1;
+                else
+                    hi = mid;
+            }
+            cur[t + lo] = w;
+        }
+        cnt = m + np;
+        __syncthreads();
+    }
+    if (t == 0) {  // walk down from the last list
+        int take = 2 * m - 2;
+        for (int i = limit; i >= 1; --i) {
+            int lo = 0, hi = m;  // leaves among the first `take` items
+            while (lo < hi) {
+                const int mid = (lo + hi) >> 1;
+                if ((int)sh.pos[i][mid] < take)
+                    lo = mid + 1;
+                else
+                    hi = mid;
+            }
+            sh.pm_take[i] = lo;
+            take = 2 * (take - lo);
+        }
+    }
+    __syncthreads();
+    if (t < m) {
+        int d = 0;
+        for (int i = 1; i <= limit; ++i)
+            d += t < sh.pm_take[i];
+        sh.dep[t] = (int16_t)d;
+    }
+}
+
+// Build *cb from hist (u64[256]); blockDim.x must be 256.  Huffman codes
+// longer than `limit` (1..32) bits: without `limited` that is an error (*cb
+// cleared, HUFF_ERR_CODE_TOO_LONG); with it the lengths are recomputed by
+// package-merge (the error only if the bytes present exceed 2^limit).
 __device__ __forceinline__ void build_codebook(const unsigned long long *__restrict__ hist,
                                                huff_codebook_t *__restrict__ cb, int32_t *status,
-                                               CodebookShared &sh)
+                                               CodebookShared &sh, int limit = (int)kMaxCodeLen,
+                                               bool limited = false)
 {
     if (chain_failed(status))
         return;
@@ -102,10 +182,21 @@ __device__ __forceinline__ void build_codebook(const unsigned long long *__restr
             }
             __syncthreads();
         }
+        // the Huffman lengths, unless a limit below 32 is exceeded
+        if (t < m)
+            atomicMax(&sh.s_max, (int)sh.dep[t]);
+        __syncthreads();
+        if (limited && sh.s_max > limit && (limit >= 9 || m <= (1 << limit))) {
+            __syncthreads();
+            if (t == 0)
+                sh.s_max = 0;
+            package_merge(m, limit, sh);
+            if (t < m)
+                atomicMax(&sh.s_max, (int)sh.dep[t]);
+        }
         if (t < m) {
             const int d = sh.dep[t];
             sh.len_s[sh.leaf_sym[t]] = (uint8_t)(d > 255 ? 255 : d);
-            atomicMax(&sh.s_max, d);
         }
     } else if (m == 1 && present) {
         sh.len_s[t] = 1;  // one distinct byte: the 1-bit code "0"
@@ -115,7 +206,7 @@ __device__ __forceinline__ void build_codebook(const unsigned long long *__restr
 
     // 4. length limit, then canonical codes
     const int max_len = sh.s_max;
-    if (max_len > (int)kMaxCodeLen) {
+    if (max_len > limit) {
         set_status(status, HUFF_ERR_CODE_TOO_LONG);
         cb->len[t] = 0;
         cb->code[t] = 0;

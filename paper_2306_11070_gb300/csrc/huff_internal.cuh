@@ -195,8 +195,10 @@ constexpr uint32_t kUnitSymbols = 16384;
 
 cudaError_t launch_histogram(const uint8_t *d_in, uint64_t n, unsigned long long *d_hist,
                              uint16_t *d_unit_hist, cudaStream_t s);
+// limit 0: plain Huffman (codes over 32 bits are an error); 1..32: codes of
+// at most `limit` bits (package-merge where the Huffman code exceeds it)
 cudaError_t launch_build_codebook(const unsigned long long *d_hist, huff_codebook_t *d_cb,
-                                  int32_t *d_status, cudaStream_t s);
+                                  int32_t *d_status, cudaStream_t s, uint32_t limit = 0);
 cudaError_t launch_unit_offsets(const uint8_t *d_in, uint64_t n, const uint16_t *d_unit_hist,
                                 const huff_codebook_t *d_cb, uint32_t *d_unit_bits,
                                 unsigned long long *d_unit_off, int32_t *d_status, cudaStream_t s);

@@ -339,3 +339,73 @@ def _full_size_check(x, cs=16384, samples=24):
 def test_full_size_workloads(name):
     x = synth.make(name)
     _full_size_check(x)
+
+
+# ------------------------------------------------------------------ length-limited codebook
+def _gpu_cb_limited(h, limit):
+    d = torch.from_numpy(np.asarray(h, dtype=np.int64)).cuda()
+    cb, st = hg.huff_build_codebook_limited(d, limit)
+    torch.cuda.synchronize()
+    return hg.parse_codebook(cb), int(st.item())
+
+
+def test_limited_codebook_matches_oracle():
+    rng = np.random.default_rng(23)
+    cases = 0
+    for trial in range(60):
+        k = int(rng.integers(2, 257))
+        h = np.zeros(256, dtype=np.uint64)
+        syms = rng.choice(256, size=k, replace=False)
+        kind = trial % 3
+        if kind == 0:
+            h[syms] = rng.integers(1, 5, size=k)
+        elif kind == 1:
+            h[syms] = np.floor(1e6 * rng.pareto(1.2, size=k)).astype(np.uint64) + 1
+        else:
+            h[syms] = (1 << np.minimum(np.arange(k), 40)).astype(np.uint64)  # deep trees
+        for limit in sorted({max(1, int(np.ceil(np.log2(k)))), 9, 12, 16, 32}):
+            (ln, code, nsym, mx), st = _gpu_cb_limited(h, limit)
+            ost, oln = oracle.code_lengths_limited(h, limit)
+            assert st == ost, (trial, limit)
+            if ost == 0:
+                assert np.array_equal(ln, oln), (trial, limit)
+                assert np.array_equal(code, oracle.canonical_codes(oln))
+                assert mx == int(oln.max()) <= limit
+                cases += 1
+    assert cases > 100
+
+
+def test_limited_codebook_fibonacci_and_errors():
+    f = [1, 1]
+    while len(f) < 34:
+        f.append(f[-1] + f[-2])
+    h = np.zeros(256, dtype=np.uint64)
+    h[:34] = f
+    for limit in (6, 12, 32):
+        (ln, code, nsym, mx), st = _gpu_cb_limited(h, limit)
+        ost, oln = oracle.code_lengths_limited(h, limit)
+        assert st == ost == 0 and np.array_equal(ln, oln) and mx == limit
+    (_, _, _, _), st = _gpu_cb_limited(h, 5)                 # 34 > 2^5 bytes
+    assert st == hg.HUFF_ERR_CODE_TOO_LONG == oracle.code_lengths_limited(h, 5)[0]
+    d = torch.zeros(256, dtype=torch.int64, device="cuda")
+    for bad in (0, 33):
+        with pytest.raises(hg.HuffError):
+            hg.huff_build_codebook_limited(d, bad)
+
+
+@pytest.mark.parametrize("gen", ["geometric", "text", "uniform"])
+def test_limited_stream_round_trip(gen):
+    # 12-bit limited codes: every code fits the decoder's table
+    x = GENS[gen](300007, 29)
+    d = dev(x)
+    h = hg.huff_histogram(d)
+    cb, st = hg.huff_build_codebook_limited(h, 12)
+    out, ob, st = hg.huff_encode(d, cb, d_status=st)
+    torch.cuda.synchronize()
+    nb = int(ob.item())
+    ost, oln = oracle.code_lengths_limited(oracle.histogram(x), 12)
+    ost, ref, need = oracle.encode(x, oln)
+    assert int(st.item()) == 0 and ost == 0 and nb == need
+    assert np.array_equal(out[:nb].cpu().numpy(), ref)
+    back, n, st = gpu_decode(out[:nb])
+    assert st == 0 and np.array_equal(back[:n].cpu().numpy(), x)
