@@ -274,6 +274,45 @@ huff_status_t huff_batch_run(huff_batch_plan_t *plan, huff_stream_t stream);
 huff_status_t huff_batch_info(const huff_batch_plan_t *plan, huff_batch_params_t *params,
                               uint32_t *grid, int32_t *used_graph);
 
+/* ---- segmented container: one codebook per segment ----------------------
+ * The paper's Method 2 taken literally (Section III-A): the input is cut into
+ * segments with ids, each segment is coded with its own tree, and the
+ * decoder reassembles them by id.  Container layout (all integers LE):
+ *   [0, 8)   n, the total number of bytes
+ *   [8, 16)  segment_bytes (a multiple of 16; the last segment may be shorter)
+ *   [16, 24) count = ceil(n / segment_bytes)
+ *   [24, 24 + 8 (count + 1))  start[i]: byte offset of segment i's stream;
+ *            start[count] is the container size
+ *   then the streams: segment i's stream (the layout above, its own lengths
+ *   and offsets) at start[i], a multiple of 16; start[0] = the header size
+ *   rounded up to 16; zero bytes between streams.
+ * Both calls run the batched engine (one fused launch) and SYNCHRONIZE the
+ * stream: they plan the batch on the host and free the plan afterwards. */
+uint64_t huff_segmented_max_size(uint64_t n, uint64_t segment_bytes, uint32_t chunk_symbols);
+/* Device scratch of huff_segmented_compress: the streams in worst-case
+ * slots, then per-segment sizes and statuses. */
+uint64_t huff_segmented_workspace_size(uint64_t n, uint64_t segment_bytes,
+                                       uint32_t chunk_symbols);
+/* Compress d_in[0, n) into the container at d_out.  *d_status is cleared
+ * first; *d_out_bytes receives the container size; device errors (the first
+ * of any segment, or HUFF_ERR_CAPACITY when the container exceeds out_cap)
+ * in *d_status.  out_cap must hold at least the header and start table.
+ * d_in, d_out, d_ws 16-byte aligned.  Host errors: HUFF_ERR_INVALID_ARG,
+ * HUFF_ERR_CUDA. */
+huff_status_t huff_segmented_compress(const uint8_t *d_in, uint64_t n, uint64_t segment_bytes,
+                                      uint32_t chunk_symbols, uint8_t *d_out, uint64_t out_cap,
+                                      uint64_t *d_out_bytes, void *d_ws, uint64_t ws_bytes,
+                                      int32_t *d_status, huff_stream_t stream);
+/* Decompress a container (read on the host first: header and start table)
+ * into d_out[0, n).  *d_n receives n once the header is valid.  A malformed
+ * header or table, or a segment that fails or decodes to a size other than
+ * its own, is HUFF_ERR_CORRUPT_STREAM in *d_status; n > out_cap is
+ * HUFF_ERR_CAPACITY.  d_in 16-byte aligned.  Host errors:
+ * HUFF_ERR_INVALID_ARG, HUFF_ERR_CUDA. */
+huff_status_t huff_segmented_decompress(const uint8_t *d_in, uint64_t in_bytes, uint8_t *d_out,
+                                        uint64_t out_cap, uint64_t *d_n, int32_t *d_status,
+                                        huff_stream_t stream);
+
 /* Autotuner.  Times candidate parameter sets on the caller's own batch and
  * returns the fastest in *best; results are cached per device, operation
  * and batch shape (buffer count, total and mean size in powers of two, and

@@ -206,3 +206,68 @@ def decode(stream, cap: int | None = None):
                                ctypes.byref(n))
     nn = int(n.value)
     return st, (out[:nn] if st == OK else out[:0]), nn
+
+
+# ---------------------------------------------------------------- segmented container
+def _al16(v: int) -> int:
+    return (v + 15) & ~15
+
+
+def segmented_compress(x, segment_bytes: int, cs: int = DEFAULT_CHUNK):
+    """(status, container bytes): the paper's Method 2 taken literally
+    (Section III-A) -- the input cut into segments with ids, each segment
+    compressed alone with its own codebook by `compress`, the streams laid
+    out behind a header and a start table (layout in include/huff.h:
+    n, segment_bytes, count, start[0..count], streams at multiples of 16,
+    zero bytes between them)."""
+    a = _bytes(x)
+    n = a.size
+    if segment_bytes < 16 or segment_bytes % 16:
+        return ERR_INVALID_ARG, np.zeros(0, dtype=np.uint8)
+    count = (n + segment_bytes - 1) // segment_bytes if n else 0
+    streams = []
+    for i in range(count):
+        st, s = compress(a[i * segment_bytes:(i + 1) * segment_bytes], cs)
+        if st != OK:
+            return st, np.zeros(0, dtype=np.uint8)
+        streams.append(s)
+    header = _al16(24 + 8 * (count + 1))
+    start = [header]
+    for s in streams:
+        start.append(start[-1] + _al16(s.size))
+    out = np.zeros(start[-1], dtype=np.uint8)
+    out[0:24] = np.frombuffer(np.array([n, segment_bytes, count], dtype="<u8").tobytes(),
+                              np.uint8)
+    out[24:24 + 8 * (count + 1)] = np.frombuffer(np.array(start, dtype="<u8").tobytes(),
+                                                 np.uint8)
+    for i, s in enumerate(streams):
+        out[start[i]:start[i] + s.size] = s
+    return OK, out
+
+
+def segmented_decompress(c, cap: int | None = None):
+    """(status, decoded bytes, n): validate the header and start table,
+    decode every segment with `decode` and check it decodes to its own
+    size; any failure is ERR_CORRUPT, n > cap is ERR_CAPACITY."""
+    c = _bytes(c)
+    empty = np.zeros(0, dtype=np.uint8)
+    if c.size < 32:
+        return ERR_CORRUPT, empty, 0
+    n, seg, count = (int(v) for v in np.frombuffer(c[:24].tobytes(), "<u8"))
+    if seg < 16 or seg % 16 or count != ((n + seg - 1) // seg if n else 0) or \
+            count > (c.size - 32) // 8:
+        return ERR_CORRUPT, empty, 0
+    start = [int(v) for v in np.frombuffer(c[24:24 + 8 * (count + 1)].tobytes(), "<u8")]
+    if start[0] != _al16(24 + 8 * (count + 1)) or start[-1] > c.size or \
+            any(s % 16 for s in start[:-1]) or any(b < a for a, b in zip(start, start[1:])):
+        return ERR_CORRUPT, empty, 0
+    if cap is not None and n > cap:
+        return ERR_CAPACITY, empty, n
+    out = np.zeros(n, dtype=np.uint8)
+    for i in range(count):
+        want = seg if i + 1 < count else n - (count - 1) * seg
+        st, back, m = decode(c[start[i]:start[i + 1]], cap=want)
+        if st != OK or m != want:
+            return ERR_CORRUPT, empty, n
+        out[i * seg:i * seg + want] = back
+    return OK, out, n

@@ -146,6 +146,14 @@ def lib() -> ctypes.CDLL:
                                       ctypes.POINTER(i32)]
         L.huff_batch_destroy.restype = None
         L.huff_batch_destroy.argtypes = [vp]
+        L.huff_segmented_max_size.restype = u64
+        L.huff_segmented_max_size.argtypes = [u64, u64, u32]
+        L.huff_segmented_workspace_size.restype = u64
+        L.huff_segmented_workspace_size.argtypes = [u64, u64, u32]
+        L.huff_segmented_compress.restype = i32
+        L.huff_segmented_compress.argtypes = [vp, u64, u64, u32, vp, u64, vp, vp, u64, vp, vp]
+        L.huff_segmented_decompress.restype = i32
+        L.huff_segmented_decompress.argtypes = [vp, u64, vp, u64, vp, vp, vp]
         L.huff_batch_autotune.restype = i32
         L.huff_batch_autotune.argtypes = [ctypes.POINTER(BatchDesc), u32, ctypes.c_int,
                                           ctypes.POINTER(BatchParams), u32,
@@ -446,6 +454,45 @@ class BatchPlan:
             self.close()
         except Exception:
             pass
+
+
+# ---------------------------------------------------------------- segmented container
+def huff_segmented_compress(d_in: torch.Tensor, segment_bytes: int,
+                            chunk_symbols: int = DEFAULT_CHUNK_SYMBOLS, stream=None):
+    """(container uint8 tensor, status int32[1]): one codebook per segment."""
+    n = d_in.numel()
+    L = lib()
+    cap = L.huff_segmented_max_size(n, segment_bytes, chunk_symbols)
+    wsb = L.huff_segmented_workspace_size(n, segment_bytes, chunk_symbols)
+    if cap == 0 or wsb == 0:
+        raise HuffError(HUFF_ERR_INVALID_ARG, "huff_segmented_compress")
+    dev = d_in.device
+    out = torch.empty(cap, dtype=torch.uint8, device=dev)
+    ws = torch.empty(wsb, dtype=torch.uint8, device=dev)
+    ob = torch.zeros(1, dtype=torch.int64, device=dev)
+    st = new_status(dev)
+    _check(L.huff_segmented_compress(_ptr(d_in) if n else None, n, segment_bytes, chunk_symbols,
+                                     _ptr(out), cap, _ptr(ob), _ptr(ws), wsb, _ptr(st),
+                                     _stream(stream)), "huff_segmented_compress")
+    size = int(ob.item())
+    return (out[:size] if int(st.item()) == 0 else out[:0]), st
+
+
+def huff_segmented_decompress(d_container: torch.Tensor, out_cap: int | None = None,
+                              stream=None):
+    """(decoded uint8 tensor, n, status int32[1])."""
+    dev = d_container.device
+    dn = torch.zeros(1, dtype=torch.int64, device=dev)
+    st = new_status(dev)
+    if out_cap is None:
+        out_cap = int.from_bytes(bytes(d_container[:8].cpu().numpy()), "little") \
+            if d_container.numel() >= 8 else 0
+    out = torch.empty(max(out_cap, 16), dtype=torch.uint8, device=dev)
+    _check(lib().huff_segmented_decompress(_ptr(d_container), d_container.numel(), _ptr(out),
+                                           out_cap, _ptr(dn), _ptr(st), _stream(stream)),
+           "huff_segmented_decompress")
+    n = int(dn.item())
+    return out[:n], n, st
 
 
 # ---------------------------------------------------------------- served path

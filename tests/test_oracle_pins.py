@@ -464,3 +464,47 @@ def test_limited_fibonacci_and_statuses():
     assert st == oracle.OK and ln[9] == 1 and int(ln.sum()) == 1
     st, ln = oracle.code_lengths_limited(np.zeros(256, dtype=np.uint64), 4)
     assert st == oracle.OK and not ln.any()
+
+
+# ---------------------------------------------------------------- segmented container
+def test_segmented_container_layout():
+    x = np.frombuffer(b"abracadabra, the quick brown fox jumps!!", dtype=np.uint8)  # 40 bytes
+    st, c = oracle.segmented_compress(x, 16)
+    assert st == oracle.OK
+    n, seg, count = np.frombuffer(c[:24].tobytes(), "<u8")
+    assert (n, seg, count) == (40, 16, 3)
+    start = list(np.frombuffer(c[24:56].tobytes(), "<u8"))
+    assert start[0] == 64 and all(s % 16 == 0 for s in start[:3]) and start[3] == c.size
+    assert not c[56:64].any()
+    for i in range(3):
+        seg_bytes = x[16 * i:16 * (i + 1)]
+        ost, alone = oracle.compress(seg_bytes)
+        assert np.array_equal(c[start[i]:start[i] + alone.size], alone)   # its own codebook
+        assert not c[start[i] + alone.size:start[i + 1]].any()
+        st2, back, m = oracle.decode(c[start[i]:start[i + 1]])
+        assert st2 == oracle.OK and bytes(back) == bytes(seg_bytes)
+    st, back, n = oracle.segmented_decompress(c)
+    assert st == oracle.OK and bytes(back) == bytes(x)
+
+
+@pytest.mark.parametrize("n,seg", [(0, 16), (5, 16), (4096, 4096), (100003, 16384), (70000, 4096)])
+def test_segmented_round_trip(n, seg):
+    x = synth.text(n, 31)
+    st, c = oracle.segmented_compress(x, seg)
+    assert st == oracle.OK
+    st, back, m = oracle.segmented_decompress(c)
+    assert st == oracle.OK and m == n and np.array_equal(back, x)
+
+
+def test_segmented_corrupt_containers():
+    x = synth.text(50000, 32)
+    st, c = oracle.segmented_compress(x, 16384)
+    bad = []
+    t = c.copy(); t[16:24] = np.frombuffer((5).to_bytes(8, "little"), np.uint8); bad.append(t)   # count
+    t = c.copy(); t[8:16] = np.frombuffer((100).to_bytes(8, "little"), np.uint8); bad.append(t)  # segment
+    t = c.copy(); t[32:40] = np.frombuffer((int.from_bytes(bytes(t[32:40]), "little") + 16)
+                                           .to_bytes(8, "little"), np.uint8); bad.append(t)
+    bad.append(c[:-16])                                                                        # cut short
+    for i, t in enumerate(bad):
+        assert oracle.segmented_decompress(t)[0] == oracle.ERR_CORRUPT, i
+    assert oracle.segmented_decompress(c, cap=49999)[0] == oracle.ERR_CAPACITY
