@@ -49,7 +49,7 @@ struct EncodeArgs {
     int32_t *status;
 };
 
-__global__ void __launch_bounds__(kEncBlock, 2) k_encode(EncodeArgs a)
+__global__ void __launch_bounds__(kEncBlock, 3) k_encode(EncodeArgs a)
 {
     extern __shared__ uint4 smem_raw[];
     uint32_t *tbl = reinterpret_cast<uint32_t *>(smem_raw);  // [256][32] or 2 x [256][16]
