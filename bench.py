@@ -169,6 +169,24 @@ def cpu_baseline(x):
     return line
 
 
+def cpu_model():
+    """The host CPU's model name (lscpu, else /proc/cpuinfo), or ''."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.startswith("Model name:"):
+                return ln.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    try:
+        for ln in open("/proc/cpuinfo"):
+            if ln.lower().startswith("model name"):
+                return ln.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return ""
+
+
 def cpu_segmented(sample):
     """Reported only: the paper's Method 2 on this host -- the sample cut into
     one segment per core, each compressed with its own codebook and decoded
@@ -191,7 +209,7 @@ def cpu_segmented(sample):
     dt = time.perf_counter() - t
     assert ok
     return {"value": sample.size / dt / 1e9, "unit": "GB/s", "cores": cores,
-            "machine": platform.machine(),
+            "machine": platform.machine(), "cpu_model": cpu_model(),
             "sample": f"same sample in {len(parts)} segments with their own codebooks, "
                       f"{cores} threads, {dt:.1f} s"}
 
