@@ -178,6 +178,13 @@ def test_chunk_sizes(cs):
     _check_roundtrip(synth.zipf_ascii(3 * 65536 + 5, 6), cs)
 
 
+@pytest.mark.parametrize("cs", [1 << 20, 1 << 24])
+def test_largest_chunks(cs):
+    # one or two chunks of up to the largest size: the decoder splits each
+    # into 32 self-synchronising sub-segments of up to 512 Ki symbols
+    _check_roundtrip(synth.text((1 << 24) + 12345, 8), cs)
+
+
 def test_empty_input():
     x = np.zeros(0, dtype=np.uint8)
     d, h, cb, st = gpu_codebook(x)
