@@ -19,7 +19,7 @@
 // sub-segment, S consecutive lanes per chunk:
 //  1. every sub-segment but the last counts codewords from its cut point up
 //     to the first codeword boundary at or past the next cut, remembering
-//     which of its first 64 bits started a codeword;
+//     which of its first 256 bits started a codeword;
 //  2. sub-segment k's true entry point is where k-1 exits; if that bit is one
 //     of k's own early boundaries, k's path has already joined the true one
 //     and only its count is corrected, otherwise k re-counts from the entry

@@ -367,15 +367,52 @@ __device__ __forceinline__ void count_codes(const Tables &T, const uint8_t *pay,
     e = pos;
 }
 
+// Codeword boundaries seen in the first kSyncBits bits of a sub-segment's
+// count (bit d set: a codeword starts d bits after the cut), kept in four
+// named registers (the word is picked by selects, never by an array index,
+// which would put the map in local memory).  256 bits: a Huffman decode
+// started off the true path almost always rejoins it within that distance,
+// so the settle walk below rarely has to recount a whole sub-segment.
+constexpr uint32_t kSyncBits = 256;
+struct SyncMap {
+    uint64_t w0, w1, w2, w3;
+    __device__ __forceinline__ void clear()
+    {
+        w0 = 1;  // the cut itself
+        w1 = w2 = w3 = 0;
+    }
+    __device__ __forceinline__ void set(uint32_t d)
+    {
+        const uint64_t b = 1ull << (d & 63);
+        const uint32_t j = d >> 6;
+        w0 |= j == 0 ? b : 0;
+        w1 |= j == 1 ? b : 0;
+        w2 |= j == 2 ? b : 0;
+        w3 |= j == 3 ? b : 0;
+    }
+    __device__ __forceinline__ uint64_t word(uint32_t j) const
+    {
+        return j == 0 ? w0 : j == 1 ? w1 : j == 2 ? w2 : w3;
+    }
+    __device__ __forceinline__ bool test(uint32_t d) const { return (word(d >> 6) >> (d & 63)) & 1; }
+    // boundaries before d (d < kSyncBits)
+    __device__ __forceinline__ uint32_t below(uint32_t d) const
+    {
+        const uint32_t j = d >> 6;
+        return (j > 0 ? __popcll(w0) : 0) + (j > 1 ? __popcll(w1) : 0) + (j > 2 ? __popcll(w2) : 0) +
+               __popcll(word(j) & ((1ull << (d & 63)) - 1));
+    }
+};
+
 // Sub-segment [g, stop) was counted from g (cnt1 codewords, exit e1, early
 // boundaries bmap).  Given its true entry point, walk the true path one
 // codeword at a time until it lands on one of the recorded boundaries: from
 // there both paths are the same codeword sequence, so only the codewords
 // before the meeting point change.  If they do not meet within the recorded
-// 64 bits, recount from the entry point.
+// kSyncBits bits, recount from the entry point.
 __device__ __forceinline__ void settle_segment(const Tables &T, const uint8_t *pay, uint64_t nw,
                                                uint64_t cbase, uint32_t g, uint32_t stop,
-                                               uint32_t entry, uint64_t bmap, uint32_t cnt1,
+                                               uint32_t entry, const SyncMap &bmap, uint32_t cnt1,
                                                uint32_t e1, uint32_t &cnt, uint32_t &e)
 {
     uint32_t pos = entry, steps = 0;
@@ -383,8 +420,8 @@ __device__ __forceinline__ void settle_segment(const Tables &T, const uint8_t *p
     bool started = false;
     for (;;) {
         const uint32_t d = pos - g;
-        if (d < 64 && ((bmap >> d) & 1)) {  // met: same path from here on
-            cnt = steps + cnt1 - __popcll(bmap & ((1ull << d) - 1));
+        if (d < kSyncBits && bmap.test(d)) {  // met: same path from here on
+            cnt = steps + cnt1 - bmap.below(d);
             e = e1;
             return;
         }
@@ -393,7 +430,7 @@ __device__ __forceinline__ void settle_segment(const Tables &T, const uint8_t *p
             e = pos;
             return;
         }
-        if (d >= 64)
+        if (d >= kSyncBits)
             break;
         if (!started) {
             rd.init(pay, nw, cbase + pos);
@@ -606,10 +643,13 @@ __device__ __forceinline__ void flush_groups(uint8_t *ob, const OutWord &ow, uin
 
 // Decode warp task `task` of stream si with S lanes per chunk (32/S chunks
 // per warp).  in_col / out_col: this lane's column of the warp's rings.
-// Returns true (warp-uniform) if the stream is corrupt.
-__device__ __forceinline__ bool decode_task(const StreamInfo &si, uint32_t S, uint64_t task,
-                                            uint32_t *in_col, uint32_t *out_col)
+// Returns true (warp-uniform) if the stream is corrupt.  kWhole: S == 1, one
+// lane per chunk, compiled without the count / settle / scan phases.
+template <bool kWhole>
+__device__ __forceinline__ bool decode_task_s(const StreamInfo &si, uint32_t S_arg, uint64_t task,
+                                              uint32_t *in_col, uint32_t *out_col)
 {
+    const uint32_t S = kWhole ? 1u : S_arg;
     const Tables &T = si.T;
     const uint32_t lut_s = smem_u32(T.lut);
     const uint8_t *len0 = T.len0;
@@ -648,14 +688,16 @@ __device__ __forceinline__ bool decode_task(const StreamInfo &si, uint32_t S, ui
 
     // 1. count each sub-segment but the last from its cut point
     uint32_t cnt1 = 0, e1 = g;
-    uint64_t bmap = 1;
+    SyncMap bmap;
+    bmap.clear();
     if (S > 1) {  // uniform: every lane of the warp takes this branch
         Bits rs = {};
         bool act = work && k + 1 < S && g < stop;
         if (act)
             rs.init(in_s, pw, pay_words, cbase >> 5, b0 + g);
         uint32_t pos = g;
-        // 1a. code by code through the first 64 bits, recording the boundaries
+        // 1a. code by code through the first kSyncBits bits, recording the
+        //     boundaries
         bool head = act;
         while (__any_sync(kFull, head)) {
             if (head) {
@@ -670,9 +712,9 @@ __device__ __forceinline__ bool decode_task(const StreamInfo &si, uint32_t S, ui
                 rs.refill();
                 pos += L;
                 ++cnt1;
-                if (pos - g < 64)
-                    bmap |= 1ull << (pos - g);
-                head = pos - g < 64 && pos < stop;
+                if (pos - g < kSyncBits)
+                    bmap.set(pos - g);
+                head = pos - g < kSyncBits && pos < stop;
                 act = pos < stop;
             }
         }
@@ -885,6 +927,13 @@ __device__ __forceinline__ bool decode_task(const StreamInfo &si, uint32_t S, ui
         }
     }
     return __any_sync(kFull, bad);
+}
+
+__device__ __forceinline__ bool decode_task(const StreamInfo &si, uint32_t S, uint64_t task,
+                                            uint32_t *in_col, uint32_t *out_col)
+{
+    return S == 1 ? decode_task_s<true>(si, 1, task, in_col, out_col)
+                  : decode_task_s<false>(si, S, task, in_col, out_col);
 }
 
 }  // namespace dec
