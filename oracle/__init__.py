@@ -4,9 +4,9 @@ Only ``tests/``, ``__graft_entry__.smoke()`` and ``bench.py``'s CPU-baseline
 and reference legs may import this package.  The CUDA library shares no code
 with it.  The arithmetic lives in plain C (``huff_oracle.c``), compiled with
 gcc into ``libhuff_oracle.so`` beside it; this module only marshals numpy
-arrays.  Each function follows the paper's Huffman Method 1 and Method 2
-(Section III-A); see the C file's header for the readings taken where the
-paper is silent.
+arrays.  Each function follows the paper's Huffman Method 1, Method 2 and
+Method 3 (Section III-A); see the C file's header for the readings taken
+where the paper is silent.
 """
 from __future__ import annotations
 
@@ -71,6 +71,10 @@ def _configure(lib):
     lib.oracle_compress.argtypes = [u8p, u64, u32, u8p, u64, u64p]
     lib.oracle_decode.restype = ctypes.c_int
     lib.oracle_decode.argtypes = [u8p, u64, u8p, u64, u64p]
+    lib.oracle_bwt.restype = ctypes.c_int
+    lib.oracle_bwt.argtypes = [u8p, u64, u32, u8p, u32p]
+    lib.oracle_ibwt.restype = ctypes.c_int
+    lib.oracle_ibwt.argtypes = [u8p, u64, u32, u32p, u8p]
     return lib
 
 
@@ -271,3 +275,88 @@ def segmented_decompress(c, cap: int | None = None):
             return ERR_CORRUPT, empty, n
         out[i * seg:i * seg + want] = back
     return OK, out, n
+
+
+def bwt(x, block: int):
+    """Method 3's block-sorting transform of every `block`-byte block:
+    (last column bytes, primary index per block)."""
+    a = _bytes(x)
+    n = a.size
+    count = (n + block - 1) // block if block > 0 else 0
+    L = np.zeros(n, dtype=np.uint8)
+    prim = np.zeros(max(count, 1), dtype=np.uint32)
+    st = _load().oracle_bwt(_p(a, ctypes.c_uint8), n, block, _p(L, ctypes.c_uint8),
+                            _p(prim, ctypes.c_uint32))
+    if st != OK:
+        raise ValueError(f"oracle_bwt status {st}")
+    return L, prim[:count]
+
+
+def ibwt(L, block: int, primary):
+    """Inverse of :func:`bwt`."""
+    a = _bytes(L)
+    n = a.size
+    count = (n + block - 1) // block if block > 0 else 0
+    prim = np.ascontiguousarray(primary, dtype=np.uint32)
+    if prim.size < count:
+        raise ValueError("one primary index per block is needed")
+    if prim.size == 0:
+        prim = np.zeros(1, dtype=np.uint32)
+    out = np.zeros(n, dtype=np.uint8)
+    st = _load().oracle_ibwt(_p(a, ctypes.c_uint8), n, block, _p(prim, ctypes.c_uint32),
+                             _p(out, ctypes.c_uint8))
+    if st != OK:
+        raise ValueError(f"oracle_ibwt status {st}")
+    return out
+
+
+# ---------------------------------------------------------------- Method 3 container
+def m3_compress(x, block: int, segment_bytes: int, cs: int = DEFAULT_CHUNK):
+    """(status, container bytes): Method 3 (Section III-A) -- the
+    block-sorting transform of every `block`-byte block, then Method 2's
+    segmented coder (one codebook per segment) over the transformed bytes.
+    Layout (include/huff.h): n (u64), block (u32), count (u32), one u32
+    primary index per block, zero bytes up to a multiple of 16, then the
+    segmented container."""
+    a = _bytes(x)
+    n = a.size
+    empty = np.zeros(0, dtype=np.uint8)
+    if block < 1 or block >= 1 << 32:
+        return ERR_INVALID_ARG, empty
+    L, prim = bwt(a, block)
+    st, seg = segmented_compress(L, segment_bytes, cs)
+    if st != OK:
+        return st, empty
+    count = prim.size
+    head = _al16(16 + 4 * count)
+    out = np.zeros(head + seg.size, dtype=np.uint8)
+    out[0:8] = np.frombuffer(np.array([n], dtype="<u8").tobytes(), np.uint8)
+    out[8:16] = np.frombuffer(np.array([block, count], dtype="<u4").tobytes(), np.uint8)
+    out[16:16 + 4 * count] = np.frombuffer(prim.astype("<u4").tobytes(), np.uint8)
+    out[head:] = seg
+    return OK, out
+
+
+def m3_decompress(c, cap: int | None = None):
+    """(status, bytes, n): validate the header, decode the segmented
+    container, check it holds n bytes and every primary index lies inside
+    its block, then invert the transform."""
+    c = _bytes(c)
+    empty = np.zeros(0, dtype=np.uint8)
+    if c.size < 16:
+        return ERR_CORRUPT, empty, 0
+    n = int(np.frombuffer(c[0:8].tobytes(), "<u8")[0])
+    block, count = (int(v) for v in np.frombuffer(c[8:16].tobytes(), "<u4"))
+    if block < 1 or count != (n + block - 1) // block or 16 + 4 * count > c.size:
+        return ERR_CORRUPT, empty, 0
+    if cap is not None and n > cap:
+        return ERR_CAPACITY, empty, n
+    prim = np.frombuffer(c[16:16 + 4 * count].tobytes(), "<u4").astype(np.uint32)
+    for i in range(count):
+        if int(prim[i]) >= min(block, n - i * block):
+            return ERR_CORRUPT, empty, n
+    head = _al16(16 + 4 * count)
+    st, L, m = segmented_decompress(c[head:], cap=n)
+    if st != OK or m != n:
+        return ERR_CORRUPT, empty, n
+    return OK, ibwt(L, block, prim), n

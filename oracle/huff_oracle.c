@@ -21,6 +21,9 @@
  *      starting bit offsets are recorded, so each chunk can be decoded on
  *      its own and the output reassembled in chunk order.     oracle_encode
  *   5. Decoding ("lossless") reverses 4 chunk by chunk.       oracle_decode
+ *   6. Method 3 first applies the block-sorting (Burrows-Wheeler) transform
+ *      to every block, and its inverse after decoding.
+ *                                                 oracle_bwt / oracle_ibwt
  *
  * Readings of points the paper leaves open:
  *   R1 tie-break: nodes are ordered by (weight, id); leaf id = byte value,
@@ -529,5 +532,130 @@ int oracle_decode(const uint8_t *s, uint64_t bytes, uint8_t *out, uint64_t cap, 
         if (c + 1 < chunks && pos != limit)
             return ORACLE_ERR_CORRUPT;
     }
+    return ORACLE_OK;
+}
+
+/* ---- Method 3: the block-sorting transform before Huffman coding ---------
+ * Method 3 (Section III-A) runs the Burrows-Wheeler transform over each
+ * block of the data set and then the parallel Huffman coder of Method 2 over
+ * the result.  The paper's one-line description of the transform (an order
+ * reversal done by a sort) is garbled; the reading taken is the transform of
+ * Burrows and Wheeler (SRC Research Report 124, 1994):
+ *   B1 a block is a run of `block` consecutive input bytes (the last block
+ *      may be shorter); blocks are transformed independently;
+ *   B2 the m cyclic rotations of a block are sorted lexicographically by
+ *      unsigned byte value; equal rotations (a periodic block) keep the
+ *      order of their starting positions;
+ *   B3 the block's output is the last byte of every rotation in sorted
+ *      order, and its primary index is the row of the rotation that starts
+ *      at the block's first byte.
+ * The inverse follows the same report: the last column, sorted stably,
+ * gives the first column, and the map from a row to the row of the rotation
+ * one byte earlier walks the block backwards from the primary row. */
+
+/* compare the rotations of b[0, m) starting at j and k */
+static int rotation_cmp(const uint8_t *b, uint32_t m, uint32_t j, uint32_t k)
+{
+    for (uint32_t t = 0; t < m; ++t) {
+        uint8_t u = b[(uint32_t)(((uint64_t)j + t) % m)];
+        uint8_t v = b[(uint32_t)(((uint64_t)k + t) % m)];
+        if (u != v)
+            return u < v ? -1 : 1;
+    }
+    return 0;
+}
+
+/* stable bottom-up merge sort of the rotation starts idx[0, m) */
+static void sort_rotations(const uint8_t *b, uint32_t m, uint32_t *idx, uint32_t *tmp)
+{
+    for (uint32_t w = 1; w < m; w *= 2) {
+        for (uint32_t lo = 0; lo < m; lo += 2 * w) {
+            uint32_t mid = lo + w < m ? lo + w : m;
+            uint32_t hi = lo + 2 * w < m ? lo + 2 * w : m;
+            uint32_t i = lo, j = mid, o = lo;
+            while (i < mid && j < hi)
+                tmp[o++] = rotation_cmp(b, m, idx[j], idx[i]) < 0 ? idx[j++] : idx[i++];
+            while (i < mid)
+                tmp[o++] = idx[i++];
+            while (j < hi)
+                tmp[o++] = idx[j++];
+        }
+        memcpy(idx, tmp, (size_t)m * sizeof(uint32_t));
+        if (w > m / 2)
+            break;
+    }
+}
+
+int oracle_bwt(const uint8_t *x, uint64_t n, uint32_t block, uint8_t *L, uint32_t *primary)
+{
+    if (n == 0)
+        return ORACLE_OK;
+    if (block == 0)
+        return ORACLE_ERR_INVALID_ARG;
+    uint32_t *idx = (uint32_t *)malloc((size_t)block * sizeof(uint32_t));
+    uint32_t *tmp = (uint32_t *)malloc((size_t)block * sizeof(uint32_t));
+    if (!idx || !tmp) {
+        free(idx);
+        free(tmp);
+        return ORACLE_ERR_CAPACITY;
+    }
+    uint64_t blocks = (n + block - 1) / block;
+    for (uint64_t c = 0; c < blocks; ++c) {
+        const uint8_t *b = x + c * block;
+        uint32_t m = (uint32_t)(n - c * block < block ? n - c * block : block);
+        for (uint32_t j = 0; j < m; ++j)
+            idx[j] = j;
+        sort_rotations(b, m, idx, tmp);
+        for (uint32_t r = 0; r < m; ++r) {
+            uint32_t j = idx[r];
+            L[c * block + r] = b[j == 0 ? m - 1 : j - 1];
+            if (j == 0)
+                primary[c] = r;
+        }
+    }
+    free(idx);
+    free(tmp);
+    return ORACLE_OK;
+}
+
+int oracle_ibwt(const uint8_t *L, uint64_t n, uint32_t block, const uint32_t *primary,
+                uint8_t *out)
+{
+    if (n == 0)
+        return ORACLE_OK;
+    if (block == 0)
+        return ORACLE_ERR_INVALID_ARG;
+    uint32_t *lf = (uint32_t *)malloc((size_t)block * sizeof(uint32_t));
+    if (!lf)
+        return ORACLE_ERR_CAPACITY;
+    uint64_t blocks = (n + block - 1) / block;
+    for (uint64_t c = 0; c < blocks; ++c) {
+        const uint8_t *l = L + c * block;
+        uint32_t m = (uint32_t)(n - c * block < block ? n - c * block : block);
+        if (primary[c] >= m) {
+            free(lf);
+            return ORACLE_ERR_CORRUPT;
+        }
+        /* first[v]: the first row of the sorted first column holding v */
+        uint64_t cnt[256] = {0}, first[256];
+        for (uint32_t p = 0; p < m; ++p)
+            ++cnt[l[p]];
+        uint64_t acc = 0;
+        for (int v = 0; v < 256; ++v) {
+            first[v] = acc;
+            acc += cnt[v];
+        }
+        /* the k-th occurrence of v in the last column is the k-th in the
+         * first column: row p's rotation, moved one byte back, is row lf[p] */
+        uint64_t seen[256] = {0};
+        for (uint32_t p = 0; p < m; ++p)
+            lf[p] = (uint32_t)(first[l[p]] + seen[l[p]]++);
+        uint32_t p = primary[c];
+        for (uint32_t t = 0; t < m; ++t) {
+            out[c * block + (m - 1 - t)] = l[p];
+            p = lf[p];
+        }
+    }
+    free(lf);
     return ORACLE_OK;
 }

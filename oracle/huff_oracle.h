@@ -33,4 +33,8 @@ int oracle_compress(const uint8_t *x, uint64_t n, uint32_t cs, uint8_t *out, uin
                     uint64_t *out_bytes);
 int oracle_decode(const uint8_t *s, uint64_t bytes, uint8_t *out, uint64_t cap,
                   uint64_t *n_out);
+/* Method 3: block-sorting transform (Burrows-Wheeler) per block */
+int oracle_bwt(const uint8_t *x, uint64_t n, uint32_t block, uint8_t *L, uint32_t *primary);
+int oracle_ibwt(const uint8_t *L, uint64_t n, uint32_t block, const uint32_t *primary,
+                uint8_t *out);
 #endif

@@ -16,6 +16,7 @@ import subprocess
 import pytest
 
 import oracle
+import test_oracle_bwt as bwt_pins
 import test_oracle_pins as pins
 
 _SRC = os.path.join(os.path.dirname(oracle.__file__), "huff_oracle.c")
@@ -42,6 +43,14 @@ MUTANTS = [
     ("decode_reports_n_minus_one", "*n_out = n;", "*n_out = n - (n > 0);"),
     ("limited_takes_one_item_less", "int take = 2 * n - 2;", "int take = 2 * n - 3;"),
     ("limited_counts_twice", "len[sid[cur[k].leaf]] += 1;", "len[sid[cur[k].leaf]] += 1 + (k == 0);"),
+    ("bwt_first_column", "L[c * block + r] = b[j == 0 ? m - 1 : j - 1];", "L[c * block + r] = b[j];"),
+    ("bwt_signed_order", "return u < v ? -1 : 1;", "return (int8_t)u < (int8_t)v ? -1 : 1;"),
+    ("bwt_equal_rotations_reversed", "rotation_cmp(b, m, idx[j], idx[i]) < 0 ?",
+     "rotation_cmp(b, m, idx[j], idx[i]) <= 0 ?"),
+    ("bwt_compares_half_rotation", "for (uint32_t t = 0; t < m; ++t) {\n        uint8_t u",
+     "for (uint32_t t = 0; t < m / 2 + 1; ++t) {\n        uint8_t u"),
+    ("ibwt_writes_forwards", "out[c * block + (m - 1 - t)] = l[p];", "out[c * block + t] = l[p];"),
+    ("ibwt_starts_next_row", "uint32_t p = primary[c];", "uint32_t p = (primary[c] + 1) % m;"),
 ]
 # Not listed: skipping the Huffman shortcut of the length-limited lengths
 # when the limit equals the Huffman maximum gave the same lengths on every
@@ -51,7 +60,11 @@ MUTANTS = [
 # mutant -- a non-last chunk must end exactly on the next offset and holds at
 # least one code, so a decreasing offset is rejected by that rule anyway (with
 # the same status).  Loosening the capacity rule would let the copy write past
-# its output buffer, so it is not planted.
+# its output buffer, so it is not planted; nor is dropping the inverse
+# transform's primary-index check, which would read past the block.
+# Comparing rotations over m - 1 bytes instead of m is an equivalent mutant
+# (two rotations of one block that agree on m - 1 bytes hold the same bytes,
+# so they agree on the last one as well).
 
 
 def _pins():
@@ -77,6 +90,14 @@ def _pins():
         pins.test_limited_fibonacci_and_statuses,
         pins.test_limited_complete_and_monotone,
         pins.test_limited_bruteforce_optimal,
+    ]
+    out += [lambda nm=nm: bwt_pins.test_golden(nm) for nm in bwt_pins.all_names()]
+    out += [
+        bwt_pins.test_unsigned_byte_order,
+        bwt_pins.test_periodic_blocks_keep_start_order,
+        bwt_pins.test_empty_and_bad_arguments,
+        lambda: bwt_pins.test_inverse_round_trip("text", 256),
+        bwt_pins.test_bruteforce_tiny_inputs,
     ]
     out += [lambda c=c: pins.test_round_trip(c) for c in pins._inputs()]
     out.append(pins.test_bruteforce_minimum_weighted_length)
