@@ -313,6 +313,58 @@ huff_status_t huff_segmented_decompress(const uint8_t *d_in, uint64_t in_bytes, 
                                         uint64_t out_cap, uint64_t *d_n, int32_t *d_status,
                                         huff_stream_t stream);
 
+/* ---- Method 3: block-sorting transform, then Method 2 ------------------
+ * Method 3 (Section III-A) runs the Burrows-Wheeler transform over each
+ * block of the data and then Method 2's coder over the result.  Reading of
+ * the transform (the paper's one-line description is garbled): blocks are
+ * runs of `block` consecutive bytes (the last may be shorter), transformed
+ * independently; a block's m cyclic rotations are sorted by unsigned byte
+ * value, equal rotations (periodic blocks) in the order of their starts;
+ * the output is the last byte of every rotation in sorted order and the
+ * primary index, the sorted row of the rotation starting at the block's
+ * first byte (Burrows and Wheeler, 1994).
+ * Limits: 1 <= block, n <= HUFF_BWT_MAX_N.  Both calls SYNCHRONIZE the
+ * stream (the forward transform reads a count back after every doubling
+ * round).  Device buffers: d_in / d_last n bytes, d_primary one u32 per
+ * block (ceil(n / block)); the workspace is huff_bwt_workspace_size bytes,
+ * 16-byte aligned, owned by the caller (about 60 n bytes).
+ * Errors: host HUFF_ERR_INVALID_ARG / HUFF_ERR_CUDA; the inverse puts
+ * HUFF_ERR_CORRUPT_STREAM in *d_status when a primary index lies outside
+ * its block (the output is then not written). */
+#define HUFF_BWT_MAX_N 2147483647ull
+uint64_t huff_bwt_workspace_size(uint64_t n, uint32_t block);
+huff_status_t huff_bwt_forward(const uint8_t *d_in, uint64_t n, uint32_t block, uint8_t *d_last,
+                               uint32_t *d_primary, void *d_ws, uint64_t ws_bytes,
+                               int32_t *d_status, huff_stream_t stream);
+huff_status_t huff_bwt_inverse(const uint8_t *d_last, uint64_t n, uint32_t block,
+                               const uint32_t *d_primary, uint8_t *d_out, void *d_ws,
+                               uint64_t ws_bytes, int32_t *d_status, huff_stream_t stream);
+/* Method 3 container (all integers LE):
+ *   [0, 8) n; [8, 12) block; [12, 16) count = ceil(n / block);
+ *   [16, 16 + 4 count) primary index of every block; zero bytes up to a
+ *   multiple of 16; then the segmented container (above) of the
+ *   transformed bytes, with its own segment size and chunk size.
+ * huff_m3_compress: *d_out_bytes receives the container size; workspace
+ * huff_m3_workspace_size (16-byte aligned, d_out too).  huff_m3_decompress
+ * reads the header on the host, decodes the segments into the workspace
+ * (huff_m3_decompress_workspace_size(n, block) bytes, n and block from the
+ * header) and inverts the transform into d_out; a malformed header, a
+ * segment error or a segmented container that does not hold n bytes is
+ * HUFF_ERR_CORRUPT_STREAM in *d_status, n > out_cap HUFF_ERR_CAPACITY.
+ * Both SYNCHRONIZE the stream. */
+uint64_t huff_m3_max_size(uint64_t n, uint32_t block, uint64_t segment_bytes,
+                          uint32_t chunk_symbols);
+uint64_t huff_m3_workspace_size(uint64_t n, uint32_t block, uint64_t segment_bytes,
+                                uint32_t chunk_symbols);
+huff_status_t huff_m3_compress(const uint8_t *d_in, uint64_t n, uint32_t block,
+                               uint64_t segment_bytes, uint32_t chunk_symbols, uint8_t *d_out,
+                               uint64_t out_cap, uint64_t *d_out_bytes, void *d_ws,
+                               uint64_t ws_bytes, int32_t *d_status, huff_stream_t stream);
+uint64_t huff_m3_decompress_workspace_size(uint64_t n, uint32_t block);
+huff_status_t huff_m3_decompress(const uint8_t *d_in, uint64_t in_bytes, uint8_t *d_out,
+                                 uint64_t out_cap, uint64_t *d_n, void *d_ws, uint64_t ws_bytes,
+                                 int32_t *d_status, huff_stream_t stream);
+
 /* Autotuner.  Times candidate parameter sets on the caller's own batch and
  * returns the fastest in *best; results are cached per device, operation
  * and batch shape (buffer count, total and mean size in powers of two, and

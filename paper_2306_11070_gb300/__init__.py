@@ -154,6 +154,22 @@ def lib() -> ctypes.CDLL:
         L.huff_segmented_compress.argtypes = [vp, u64, u64, u32, vp, u64, vp, vp, u64, vp, vp]
         L.huff_segmented_decompress.restype = i32
         L.huff_segmented_decompress.argtypes = [vp, u64, vp, u64, vp, vp, vp]
+        L.huff_bwt_workspace_size.restype = u64
+        L.huff_bwt_workspace_size.argtypes = [u64, u32]
+        L.huff_bwt_forward.restype = i32
+        L.huff_bwt_forward.argtypes = [vp, u64, u32, vp, vp, vp, u64, vp, vp]
+        L.huff_bwt_inverse.restype = i32
+        L.huff_bwt_inverse.argtypes = [vp, u64, u32, vp, vp, vp, u64, vp, vp]
+        L.huff_m3_max_size.restype = u64
+        L.huff_m3_max_size.argtypes = [u64, u32, u64, u32]
+        L.huff_m3_workspace_size.restype = u64
+        L.huff_m3_workspace_size.argtypes = [u64, u32, u64, u32]
+        L.huff_m3_compress.restype = i32
+        L.huff_m3_compress.argtypes = [vp, u64, u32, u64, u32, vp, u64, vp, vp, u64, vp, vp]
+        L.huff_m3_decompress_workspace_size.restype = u64
+        L.huff_m3_decompress_workspace_size.argtypes = [u64, u32]
+        L.huff_m3_decompress.restype = i32
+        L.huff_m3_decompress.argtypes = [vp, u64, vp, u64, vp, vp, u64, vp, vp]
         L.huff_batch_autotune.restype = i32
         L.huff_batch_autotune.argtypes = [ctypes.POINTER(BatchDesc), u32, ctypes.c_int,
                                           ctypes.POINTER(BatchParams), u32,
@@ -493,6 +509,95 @@ def huff_segmented_decompress(d_container: torch.Tensor, out_cap: int | None = N
            "huff_segmented_decompress")
     n = int(dn.item())
     return out[:n], n, st
+
+
+# ---------------------------------------------------------------- Method 3
+def _bwt_ws(n: int, block: int, dev, ws=None):
+    wsb = lib().huff_bwt_workspace_size(n, block)
+    if wsb == 0:
+        raise HuffError(HUFF_ERR_INVALID_ARG, "huff_bwt_workspace_size")
+    if ws is None or ws.numel() < wsb:
+        ws = torch.empty(wsb, dtype=torch.uint8, device=dev)
+    return ws, wsb
+
+
+def huff_bwt_forward(d_in: torch.Tensor, block: int, d_last=None, d_primary=None, ws=None,
+                     stream=None):
+    """(last column uint8[n], primary int32[blocks] holding u32, status int32[1]):
+    the block-sorting transform of every `block`-byte block (synchronizes)."""
+    x = _u8(d_in)
+    n = x.numel()
+    dev = x.device
+    blocks = (n + block - 1) // block if block > 0 else 0
+    if d_last is None:
+        d_last = torch.empty(max(n, 1), dtype=torch.uint8, device=dev)
+    if d_primary is None:
+        d_primary = torch.empty(max(blocks, 1), dtype=torch.int32, device=dev)
+    ws, wsb = _bwt_ws(n, block, dev, ws) if n else (None, 0)
+    st = new_status(dev)
+    _check(lib().huff_bwt_forward(_ptr(x) if n else None, n, block, _ptr(d_last),
+                                  _ptr(d_primary), _ptr(ws), wsb, _ptr(st), _stream(stream)),
+           "huff_bwt_forward")
+    return d_last[:n], d_primary[:blocks], st
+
+
+def huff_bwt_inverse(d_last: torch.Tensor, block: int, d_primary: torch.Tensor, d_out=None,
+                     ws=None, stream=None):
+    """(bytes uint8[n], status int32[1]): inverse of huff_bwt_forward."""
+    L = _u8(d_last)
+    n = L.numel()
+    dev = L.device
+    if d_out is None:
+        d_out = torch.empty(max(n, 1), dtype=torch.uint8, device=dev)
+    ws, wsb = _bwt_ws(n, block, dev, ws) if n else (None, 0)
+    st = new_status(dev)
+    _check(lib().huff_bwt_inverse(_ptr(L) if n else None, n, block, _ptr(d_primary),
+                                  _ptr(d_out), _ptr(ws), wsb, _ptr(st), _stream(stream)),
+           "huff_bwt_inverse")
+    return d_out[:n], st
+
+
+def huff_m3_compress(d_in: torch.Tensor, block: int, segment_bytes: int,
+                     chunk_symbols: int = DEFAULT_CHUNK_SYMBOLS, stream=None):
+    """(container uint8 tensor, status int32[1]): Method 3 -- the transform of
+    every block, then one codebook per segment."""
+    x = _u8(d_in)
+    n = x.numel()
+    L = lib()
+    cap = L.huff_m3_max_size(n, block, segment_bytes, chunk_symbols)
+    wsb = L.huff_m3_workspace_size(n, block, segment_bytes, chunk_symbols)
+    if cap == 0 or wsb == 0:
+        raise HuffError(HUFF_ERR_INVALID_ARG, "huff_m3_compress")
+    dev = x.device
+    out = torch.empty(cap, dtype=torch.uint8, device=dev)
+    ws = torch.empty(wsb, dtype=torch.uint8, device=dev)
+    ob = torch.zeros(1, dtype=torch.int64, device=dev)
+    st = new_status(dev)
+    _check(L.huff_m3_compress(_ptr(x) if n else None, n, block, segment_bytes, chunk_symbols,
+                              _ptr(out), cap, _ptr(ob), _ptr(ws), wsb, _ptr(st), _stream(stream)),
+           "huff_m3_compress")
+    size = int(ob.item())
+    return (out[:size] if int(st.item()) == 0 else out[:0]), st
+
+
+def huff_m3_decompress(d_container: torch.Tensor, out_cap: int | None = None, stream=None):
+    """(decoded uint8 tensor, n, status int32[1])."""
+    c = _u8(d_container)
+    dev = c.device
+    head = bytes(c[:16].cpu().numpy()) if c.numel() >= 16 else b"\0" * 16
+    n = int.from_bytes(head[:8], "little")
+    block = int.from_bytes(head[8:12], "little")
+    wsb = lib().huff_m3_decompress_workspace_size(n, block) if block else 0
+    ws = torch.empty(max(wsb, 16), dtype=torch.uint8, device=dev)
+    if out_cap is None:
+        out_cap = n
+    out = torch.empty(max(out_cap, 16), dtype=torch.uint8, device=dev)
+    dn = torch.zeros(1, dtype=torch.int64, device=dev)
+    st = new_status(dev)
+    _check(lib().huff_m3_decompress(_ptr(c), c.numel(), _ptr(out), out_cap, _ptr(dn), _ptr(ws),
+                                    wsb, _ptr(st), _stream(stream)), "huff_m3_decompress")
+    got = int(dn.item()) if int(st.item()) == 0 else 0
+    return out[:got], got, st
 
 
 # ---------------------------------------------------------------- served path

@@ -1,0 +1,701 @@
+// Method 3 (Section III-A): the block-sorting (Burrows-Wheeler) transform of
+// every block before Method 2's coder, its inverse, and the Method 3
+// container.
+//
+// Forward: the rotations of all blocks are sorted at once by prefix
+// doubling.  Every position i carries a rank RK[i] = the first sorted slot
+// of its group (the rotations that agree on the prefix compared so far);
+// slots of block b are [b * block, b * block + m_b), so ranks are global.
+//   round 0: sort all positions by (block, first 4 bytes of the rotation);
+//   round r: with h = 4 * 2^(r-1), the still-unresolved positions (groups of
+//            more than one) are sorted by (group, RK[i + h within the block])
+//            and their groups split where that second rank changes;
+// until no group has two members or the compared prefix covers the longest
+// block (then the remaining groups are equal rotations, already in start
+// order since every pass is stable and the first order is by position).
+// The sorts are stable LSD radix passes over only the key bits in use.
+//
+// Inverse: LF[p] = the slot of row p's last byte in a stable sort of the
+// last column by (block, byte); the block is the walk p -> LF[p] from the
+// primary row, emitted backwards.  The walk is cut at sample rows (every
+// 64th row and the primary rows): each sample walks to the next sample and
+// records the distance, list ranking by pointer jumping over the samples
+// gives each sample's distance from the primary row, and every sample then
+// re-walks its stretch writing the bytes in place.  A periodic block's walk
+// returns to the primary row after one period c; the rest of the block
+// repeats it.
+#include <vector>
+
+#include "sort_impl.cuh"
+
+namespace huff {
+namespace {
+
+using namespace srt;
+
+constexpr int kEw = 256;               // threads of the elementwise kernels
+constexpr uint32_t kSampleGap = 64;    // rows between regular samples
+constexpr uint32_t kNil = 0xffffffffu;
+
+unsigned ew_grid(uint64_t count)
+{
+    const uint64_t cap = (uint64_t)device_sm_count() * 16;
+    uint64_t g = (count + kEw - 1) / kEw;
+    if (g > cap)
+        g = cap;
+    return (unsigned)(g < 1 ? 1 : g);
+}
+
+uint32_t bit_width(uint64_t v)
+{
+    uint32_t b = 0;
+    while (v) {
+        ++b;
+        v >>= 1;
+    }
+    return b;
+}
+
+__device__ __forceinline__ void block_span(uint32_t i, uint32_t block, uint32_t n, uint32_t &s,
+                                           uint32_t &m)
+{
+    s = (i / block) * block;
+    m = n - s < block ? n - s : block;
+}
+
+// ---- forward --------------------------------------------------------------
+// round 0 keys: (block id, big-endian first 4 bytes of the rotation)
+__global__ void k_bwt_init(const uint8_t *x, uint32_t n, uint32_t block, uint64_t *key,
+                           uint32_t *val, uint32_t *act)
+{
+    for (uint32_t i = blockIdx.x * kEw + threadIdx.x; i < n; i += gridDim.x * kEw) {
+        uint32_t s, m;
+        block_span(i, block, n, s, m);
+        const uint32_t r = i - s;
+        uint32_t k = 0;
+#pragma unroll
+        for (uint32_t t = 0; t < 4; ++t)
+            k = (k << 8) | x[s + (uint32_t)(((uint64_t)r + t) % m)];
+        key[i] = ((uint64_t)(i / block) << 32) | k;
+        val[i] = i;
+        act[i] = i;
+    }
+}
+
+// round r keys: (group, rank of the rotation h bytes on, relative to the block)
+__global__ void k_bwt_round_keys(const uint32_t *sa, const uint32_t *rk, const uint32_t *act,
+                                 const uint32_t *grp, uint32_t count, uint32_t n, uint32_t block,
+                                 uint64_t h, uint64_t *key, uint32_t *val)
+{
+    for (uint32_t k = blockIdx.x * kEw + threadIdx.x; k < count; k += gridDim.x * kEw) {
+        const uint32_t i = sa[act[k]];
+        uint32_t s, m;
+        block_span(i, block, n, s, m);
+        const uint32_t j = s + (uint32_t)(((uint64_t)(i - s) + h) % m);
+        key[k] = ((uint64_t)grp[k] << 32) | (rk[j] - s);
+        val[k] = i;
+    }
+}
+
+// sorted slots back into SA; a group starts where the key changes
+__global__ void k_bwt_heads(const uint64_t *key, const uint32_t *val, const uint32_t *act,
+                            uint32_t count, uint32_t *sa, uint32_t *head)
+{
+    for (uint32_t k = blockIdx.x * kEw + threadIdx.x; k < count; k += gridDim.x * kEw) {
+        sa[act[k]] = val[k];
+        head[k] = (k == 0 || key[k] != key[k - 1]) ? 1u : 0u;
+    }
+}
+
+// gi = inclusive count of heads: group of k is gi[k] - 1
+__global__ void k_bwt_group_starts(const uint32_t *head, const uint32_t *gi, uint32_t count,
+                                   uint32_t *gstart)
+{
+    for (uint32_t k = blockIdx.x * kEw + threadIdx.x; k < count; k += gridDim.x * kEw) {
+        if (head[k])
+            gstart[gi[k] - 1] = k;
+        if (k + 1 == count)
+            gstart[gi[k]] = count;
+    }
+}
+
+__device__ __forceinline__ uint32_t group_size(const uint32_t *gstart, uint32_t g)
+{
+    return gstart[g + 1] - gstart[g];
+}
+
+// new ranks; flag = the element's group still has two members or more
+__global__ void k_bwt_rank(const uint32_t *val, const uint32_t *gi, const uint32_t *gstart,
+                           const uint32_t *act, uint32_t count, uint32_t *rk, uint32_t *flag)
+{
+    for (uint32_t k = blockIdx.x * kEw + threadIdx.x; k < count; k += gridDim.x * kEw) {
+        const uint32_t g = gi[k] - 1;
+        rk[val[k]] = act[gstart[g]];
+        flag[k] = group_size(gstart, g) > 1 ? 1u : 0u;
+    }
+}
+
+// keep the unresolved elements, in slot order, with their group numbers
+__global__ void k_bwt_compact(const uint32_t *gi, const uint32_t *gstart, const uint32_t *fpos,
+                              const uint32_t *act, uint32_t count, uint32_t *act2, uint32_t *grp2)
+{
+    for (uint32_t k = blockIdx.x * kEw + threadIdx.x; k < count; k += gridDim.x * kEw) {
+        const uint32_t g = gi[k] - 1;
+        if (group_size(gstart, g) > 1) {
+            act2[fpos[k]] = act[k];
+            grp2[fpos[k]] = g;
+        }
+    }
+}
+
+__global__ void k_bwt_output(const uint8_t *x, const uint32_t *sa, uint32_t n, uint32_t block,
+                             uint8_t *last, uint32_t *primary)
+{
+    for (uint32_t p = blockIdx.x * kEw + threadIdx.x; p < n; p += gridDim.x * kEw) {
+        const uint32_t i = sa[p];
+        uint32_t s, m;
+        block_span(p, block, n, s, m);
+        last[p] = x[i == s ? s + m - 1 : i - 1];
+        if (i == s)
+            primary[p / block] = p - s;
+    }
+}
+
+struct FwdWs {
+    uint32_t *sa, *rk, *act, *act2, *grp, *grp2, *head, *gi, *gstart, *scal;
+    uint64_t *k0, *k1;
+    uint32_t *v0, *v1;
+    void *radix, *part;
+    uint64_t bytes;
+};
+
+template <class T>
+T *carve(uint8_t *base, uint64_t &off, uint64_t bytes)
+{
+    T *p = reinterpret_cast<T *>(base ? base + off : nullptr);
+    off += (bytes + 255) & ~255ull;
+    return p;
+}
+
+FwdWs fwd_layout(uint8_t *base, uint64_t n)
+{
+    FwdWs w;
+    uint64_t off = 0;
+    w.sa = carve<uint32_t>(base, off, 4 * n);
+    w.rk = carve<uint32_t>(base, off, 4 * n);
+    w.act = carve<uint32_t>(base, off, 4 * n);
+    w.act2 = carve<uint32_t>(base, off, 4 * n);
+    w.grp = carve<uint32_t>(base, off, 4 * n);
+    w.grp2 = carve<uint32_t>(base, off, 4 * n);
+    w.head = carve<uint32_t>(base, off, 4 * n);
+    w.gi = carve<uint32_t>(base, off, 4 * n);
+    w.gstart = carve<uint32_t>(base, off, 4 * (n + 1));
+    w.scal = carve<uint32_t>(base, off, 16);
+    w.k0 = carve<uint64_t>(base, off, 8 * n);
+    w.k1 = carve<uint64_t>(base, off, 8 * n);
+    w.v0 = carve<uint32_t>(base, off, 4 * n);
+    w.v1 = carve<uint32_t>(base, off, 4 * n);
+    w.radix = carve<uint8_t>(base, off, radix_scratch_bytes(n));
+    w.part = carve<uint8_t>(base, off, scan_parts_bytes(n));
+    w.bytes = off;
+    return w;
+}
+
+// stable LSD over the key bits [0, lo_bits) and [32, 32 + hi_bits)
+cudaError_t sort_two_fields(FwdWs &w, uint32_t count, uint32_t lo_bits, uint32_t hi_bits,
+                            cudaStream_t s, uint64_t *&ks, uint32_t *&vs)
+{
+    bool f1 = false, f2 = false;
+    cudaError_t e = radix_sort_bits(w.k0, w.v0, w.k1, w.v1, count, 0, lo_bits, w.radix, s, f1);
+    if (e != cudaSuccess)
+        return e;
+    uint64_t *ka = f1 ? w.k1 : w.k0, *kb = f1 ? w.k0 : w.k1;
+    uint32_t *va = f1 ? w.v1 : w.v0, *vb = f1 ? w.v0 : w.v1;
+    e = radix_sort_bits(ka, va, kb, vb, count, 32, 32 + hi_bits, w.radix, s, f2);
+    ks = f2 ? kb : ka;
+    vs = f2 ? vb : va;
+    return e;
+}
+
+// split the groups of the sorted active list; returns the number still
+// unresolved and the number of groups of the list (host values)
+cudaError_t refine(FwdWs &w, const uint64_t *ks, const uint32_t *vs, uint32_t count,
+                   cudaStream_t s, uint32_t &n_act, uint32_t &groups)
+{
+    const unsigned g = ew_grid(count);
+    k_bwt_heads<<<g, kEw, 0, s>>>(ks, vs, w.act, count, w.sa, w.head);
+    cudaError_t e = scan_u32(w.head, w.gi, count, true, static_cast<uint32_t *>(w.part), w.scal, s);
+    if (e != cudaSuccess)
+        return e;
+    k_bwt_group_starts<<<g, kEw, 0, s>>>(w.head, w.gi, count, w.gstart);
+    k_bwt_rank<<<g, kEw, 0, s>>>(vs, w.gi, w.gstart, w.act, count, w.rk, w.head);
+    e = scan_u32(w.head, w.head, count, false, static_cast<uint32_t *>(w.part), w.scal + 1, s);
+    if (e != cudaSuccess)
+        return e;
+    k_bwt_compact<<<g, kEw, 0, s>>>(w.gi, w.gstart, w.head, w.act, count, w.act2, w.grp2);
+    uint32_t h[2];
+    if ((e = cudaGetLastError()) != cudaSuccess ||
+        (e = cudaMemcpyAsync(h, w.scal, sizeof(h), cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
+        (e = cudaStreamSynchronize(s)) != cudaSuccess)
+        return e;
+    groups = h[0];
+    n_act = h[1];
+    uint32_t *t = w.act;
+    w.act = w.act2;
+    w.act2 = t;
+    t = w.grp;
+    w.grp = w.grp2;
+    w.grp2 = t;
+    return cudaSuccess;
+}
+
+// ---- inverse --------------------------------------------------------------
+__global__ void k_lf_keys(const uint8_t *last, uint32_t n, uint32_t block, uint64_t *key,
+                          uint32_t *val)
+{
+    for (uint32_t p = blockIdx.x * kEw + threadIdx.x; p < n; p += gridDim.x * kEw) {
+        key[p] = ((uint64_t)(p / block) << 8) | last[p];
+        val[p] = p;
+    }
+}
+
+__global__ void k_lf_scatter(const uint32_t *vs, uint32_t n, uint32_t *lf)
+{
+    for (uint32_t q = blockIdx.x * kEw + threadIdx.x; q < n; q += gridDim.x * kEw)
+        lf[vs[q]] = q;
+}
+
+__global__ void k_check_primary(const uint32_t *primary, uint32_t n, uint32_t block,
+                                uint32_t blocks, int32_t *status)
+{
+    for (uint32_t b = blockIdx.x * kEw + threadIdx.x; b < blocks; b += gridDim.x * kEw) {
+        const uint32_t s = b * block;
+        const uint32_t m = n - s < block ? n - s : block;
+        if (primary[b] >= m)
+            set_status(status, HUFF_ERR_CORRUPT_STREAM);
+    }
+}
+
+struct Samples {
+    uint32_t n, block, regular;  // regular samples: rows 0, 64, 128, ...
+    const uint32_t *primary;
+    // sample id of row p, or kNil: a primary row is its block's extra
+    // sample (regular + block), even when it is also a multiple of 64
+    __device__ __forceinline__ uint32_t id_of(uint32_t p) const
+    {
+        const uint32_t b = p / block;
+        if (p - b * block == primary[b])
+            return regular + b;
+        return (p % kSampleGap) == 0 ? p / kSampleGap : kNil;
+    }
+    // row of sample id, or kNil for a regular sample that is a primary row
+    __device__ __forceinline__ uint32_t row_of(uint32_t id) const
+    {
+        if (id >= regular)
+            return (id - regular) * block + primary[id - regular];
+        const uint32_t p = id * kSampleGap;
+        const uint32_t b = p / block;
+        return p - b * block == primary[b] ? kNil : p;
+    }
+};
+
+// every sample walks to the next sample: link and length; the link into a
+// block's primary sample is cut (kNil), which turns the primary's cycle into
+// a list headed by the primary
+__global__ void k_walk_link(const uint32_t *lf, Samples S, uint32_t count, uint32_t *nxt,
+                            uint32_t *len, int32_t *status)
+{
+    if (chain_failed(status))
+        return;
+    for (uint32_t id = blockIdx.x * kEw + threadIdx.x; id < count; id += gridDim.x * kEw) {
+        const uint32_t p0 = S.row_of(id);
+        if (p0 == kNil) {
+            nxt[id] = kNil;
+            len[id] = 0;
+            continue;
+        }
+        uint32_t s, m;
+        block_span(p0, S.block, S.n, s, m);
+        uint32_t p = p0, t = 0, c;
+        do {  // ends on p0 at the latest: LF is a permutation of the block
+            p = lf[p];
+            ++t;
+            c = p < S.n ? S.id_of(p) : kNil;
+        } while (c == kNil && t < m && p < S.n);
+        if (c == kNil) {  // not a permutation: cannot happen for a sorted column
+            set_status(status, HUFF_ERR_CORRUPT_STREAM);
+            nxt[id] = kNil;
+            len[id] = 0;
+            continue;
+        }
+        const uint32_t b = p0 / S.block;
+        nxt[id] = c == S.regular + b ? kNil : c;
+        len[id] = t;
+    }
+}
+
+// one pointer-jumping step: sum[id] = stretch lengths from id to the list's
+// end after enough steps
+__global__ void k_jump(const uint32_t *nx_in, const uint32_t *sum_in, uint32_t count,
+                       uint32_t *nx_out, uint32_t *sum_out, const int32_t *status)
+{
+    if (chain_failed(status))
+        return;
+    for (uint32_t id = blockIdx.x * kEw + threadIdx.x; id < count; id += gridDim.x * kEw) {
+        const uint32_t x = nx_in[id];
+        if (x == kNil) {
+            nx_out[id] = kNil;
+            sum_out[id] = sum_in[id];
+        } else {
+            nx_out[id] = nx_in[x];
+            sum_out[id] = sum_in[id] + sum_in[x];
+        }
+    }
+}
+
+// samples on their block's primary list write their stretch: the primary's
+// sum is the cycle length c, a sample's distance from the primary is
+// c - its own sum
+__global__ void k_walk_emit(const uint32_t *lf, const uint8_t *last, Samples S, uint32_t count,
+                            const uint32_t *len, const uint32_t *nx, const uint32_t *sum,
+                            uint8_t *out, int32_t *status)
+{
+    if (chain_failed(status))
+        return;
+    for (uint32_t id = blockIdx.x * kEw + threadIdx.x; id < count; id += gridDim.x * kEw) {
+        const uint32_t L = len[id];
+        if (L == 0 || nx[id] != kNil)
+            continue;  // not a sample, or not on the primary's cycle
+        uint32_t p = S.row_of(id);
+        uint32_t s, m;
+        block_span(p, S.block, S.n, s, m);
+        const uint32_t c = sum[S.regular + p / S.block];
+        const uint32_t d = c - sum[id];
+        if (c > m || d + L > c) {
+            set_status(status, HUFF_ERR_CORRUPT_STREAM);
+            continue;
+        }
+        for (uint32_t t = 0; t < L && p < S.n; ++t) {
+            out[s + m - 1 - (d + t)] = last[p];
+            p = lf[p];
+        }
+    }
+}
+
+// a block whose walk closed after c < m rows repeats its last c bytes
+__global__ void k_periodic_fill(uint8_t *out, uint32_t n, uint32_t block, uint32_t regular,
+                                const uint32_t *sum, const int32_t *status)
+{
+    if (chain_failed(status))
+        return;
+    for (uint32_t q = blockIdx.x * kEw + threadIdx.x; q < n; q += gridDim.x * kEw) {
+        uint32_t s, m;
+        block_span(q, block, n, s, m);
+        const uint32_t c = sum[regular + q / block];
+        const uint32_t t = s + m - 1 - q;  // walk step of q
+        if (c < m && t >= c)
+            out[q] = out[s + m - 1 - t % c];
+    }
+}
+
+struct InvWs {
+    uint32_t *lf, *nxt, *len, *nx2, *sum, *sum2;
+    uint64_t *k0, *k1;
+    uint32_t *v0, *v1;
+    void *radix;
+    uint64_t bytes;
+};
+
+uint32_t sample_count(uint64_t n, uint32_t block)
+{
+    return (uint32_t)((n + kSampleGap - 1) / kSampleGap + (n + block - 1) / block);
+}
+
+InvWs inv_layout(uint8_t *base, uint64_t n, uint32_t block)
+{
+    InvWs w;
+    uint64_t off = 0;
+    const uint64_t S = sample_count(n, block);
+    w.lf = carve<uint32_t>(base, off, 4 * n);
+    w.nxt = carve<uint32_t>(base, off, 4 * S);
+    w.len = carve<uint32_t>(base, off, 4 * S);
+    w.nx2 = carve<uint32_t>(base, off, 4 * S);
+    w.sum = carve<uint32_t>(base, off, 4 * S);
+    w.sum2 = carve<uint32_t>(base, off, 4 * S);
+    w.k0 = carve<uint64_t>(base, off, 8 * n);
+    w.k1 = carve<uint64_t>(base, off, 8 * n);
+    w.v0 = carve<uint32_t>(base, off, 4 * n);
+    w.v1 = carve<uint32_t>(base, off, 4 * n);
+    w.radix = carve<uint8_t>(base, off, radix_scratch_bytes(n));
+    w.bytes = off;
+    return w;
+}
+
+bool bwt_args_ok(uint64_t n, uint32_t block)
+{
+    return block >= 1 && n <= HUFF_BWT_MAX_N;
+}
+
+inline bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
+__global__ void k_m3_header(uint8_t *out, uint64_t n, uint32_t block, uint32_t count, uint32_t head)
+{
+    for (uint32_t i = threadIdx.x; i < head; i += blockDim.x) {
+        if (i < 8)
+            out[i] = (uint8_t)(n >> (8 * i));
+        else if (i < 12)
+            out[i] = (uint8_t)(block >> (8 * (i - 8)));
+        else if (i < 16)
+            out[i] = (uint8_t)(count >> (8 * (i - 12)));
+        else if (i >= 16 + 4 * count)
+            out[i] = 0;
+    }
+}
+
+__global__ void k_add_u64(unsigned long long *p, uint64_t v, const int32_t *status)
+{
+    if (!chain_failed(status))
+        *p += v;
+}
+
+uint32_t m3_head_bytes(uint64_t count) { return (uint32_t)((16 + 4 * count + 15) & ~15ull); }
+
+}  // namespace
+}  // namespace huff
+
+using namespace huff;
+
+extern "C" {
+
+uint64_t huff_bwt_workspace_size(uint64_t n, uint32_t block)
+{
+    if (!bwt_args_ok(n, block))
+        return 0;
+    const uint64_t f = fwd_layout(nullptr, n).bytes;
+    const uint64_t i = inv_layout(nullptr, n, block).bytes;
+    return f > i ? f : i;
+}
+
+huff_status_t huff_bwt_forward(const uint8_t *d_in, uint64_t n, uint32_t block, uint8_t *d_last,
+                               uint32_t *d_primary, void *d_ws, uint64_t ws_bytes,
+                               int32_t *d_status, huff_stream_t stream)
+{
+    if (!bwt_args_ok(n, block) || !d_status || (n && (!d_in || !d_last || !d_primary || !d_ws)) ||
+        (n && ws_bytes < huff_bwt_workspace_size(n, block)) || (d_ws && !aligned16(d_ws)))
+        return HUFF_ERR_INVALID_ARG;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    if (cudaMemsetAsync(d_status, 0, sizeof(int32_t), s) != cudaSuccess)
+        return HUFF_ERR_CUDA;
+    if (n == 0)
+        return HUFF_OK;
+    const uint32_t N = (uint32_t)n;
+    FwdWs w = fwd_layout(static_cast<uint8_t *>(d_ws), n);
+    const uint64_t blocks = (n + block - 1) / block;
+    const uint64_t mmax = n < block ? n : block;
+    k_bwt_init<<<ew_grid(n), kEw, 0, s>>>(d_in, N, block, w.k0, w.v0, w.act);
+    uint64_t *ks;
+    uint32_t *vs;
+    if (sort_two_fields(w, N, 32, bit_width(blocks - 1), s, ks, vs) != cudaSuccess)
+        return HUFF_ERR_CUDA;
+    uint32_t n_act = 0, groups = 0;
+    if (refine(w, ks, vs, N, s, n_act, groups) != cudaSuccess)
+        return HUFF_ERR_CUDA;
+    for (uint64_t h = 4; n_act > 0 && h < mmax; h *= 2) {
+        k_bwt_round_keys<<<ew_grid(n_act), kEw, 0, s>>>(w.sa, w.rk, w.act, w.grp, n_act, N, block, h,
+                                                        w.k0, w.v0);
+        if (sort_two_fields(w, n_act, bit_width(mmax - 1), bit_width(groups - 1), s, ks, vs) !=
+            cudaSuccess)
+            return HUFF_ERR_CUDA;
+        if (refine(w, ks, vs, n_act, s, n_act, groups) != cudaSuccess)
+            return HUFF_ERR_CUDA;
+    }
+    k_bwt_output<<<ew_grid(n), kEw, 0, s>>>(d_in, w.sa, N, block, d_last, d_primary);
+    return cudaGetLastError() == cudaSuccess ? HUFF_OK : HUFF_ERR_CUDA;
+}
+
+huff_status_t huff_bwt_inverse(const uint8_t *d_last, uint64_t n, uint32_t block,
+                               const uint32_t *d_primary, uint8_t *d_out, void *d_ws,
+                               uint64_t ws_bytes, int32_t *d_status, huff_stream_t stream)
+{
+    if (!bwt_args_ok(n, block) || !d_status || (n && (!d_last || !d_primary || !d_out || !d_ws)) ||
+        (n && ws_bytes < huff_bwt_workspace_size(n, block)) || (d_ws && !aligned16(d_ws)))
+        return HUFF_ERR_INVALID_ARG;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    if (cudaMemsetAsync(d_status, 0, sizeof(int32_t), s) != cudaSuccess)
+        return HUFF_ERR_CUDA;
+    if (n == 0)
+        return HUFF_OK;
+    const uint32_t N = (uint32_t)n;
+    InvWs w = inv_layout(static_cast<uint8_t *>(d_ws), n, block);
+    const uint32_t blocks = (uint32_t)((n + block - 1) / block);
+    k_check_primary<<<ew_grid(blocks), kEw, 0, s>>>(d_primary, N, block, blocks, d_status);
+    k_lf_keys<<<ew_grid(n), kEw, 0, s>>>(d_last, N, block, w.k0, w.v0);
+    bool flip = false;
+    if (radix_sort_bits(w.k0, w.v0, w.k1, w.v1, N, 0, 8 + bit_width(blocks - 1), w.radix, s, flip) !=
+        cudaSuccess)
+        return HUFF_ERR_CUDA;
+    k_lf_scatter<<<ew_grid(n), kEw, 0, s>>>(flip ? w.v1 : w.v0, N, w.lf);
+    Samples S;
+    S.n = N;
+    S.block = block;
+    S.regular = (uint32_t)((n + kSampleGap - 1) / kSampleGap);
+    S.primary = d_primary;
+    const uint32_t count = sample_count(n, block);
+    k_walk_link<<<ew_grid(count), kEw, 0, s>>>(w.lf, S, count, w.nxt, w.len, d_status);
+    // the longest list is one block's samples
+    const uint64_t per_block = (uint64_t)((n < block ? n : block) + kSampleGap - 1) / kSampleGap + 1;
+    const uint32_t rounds = bit_width(per_block) + 1;
+    uint32_t *nx = w.nxt, *sm = w.len, *nx_o = w.nx2, *sm_o = w.sum;
+    for (uint32_t r = 0; r < rounds; ++r) {
+        k_jump<<<ew_grid(count), kEw, 0, s>>>(nx, sm, count, nx_o, sm_o, d_status);
+        if (r == 0) {  // len stays; later steps ping-pong between sum and sum2
+            nx = nx_o;
+            sm = sm_o;
+            nx_o = w.nxt;
+            sm_o = w.sum2;
+        } else {
+            uint32_t *t = nx;
+            nx = nx_o;
+            nx_o = t;
+            t = sm;
+            sm = sm_o;
+            sm_o = t;
+        }
+    }
+    k_walk_emit<<<ew_grid(count), kEw, 0, s>>>(w.lf, d_last, S, count, w.len, nx, sm, d_out,
+                                              d_status);
+    k_periodic_fill<<<ew_grid(n), kEw, 0, s>>>(d_out, N, block, S.regular, sm, d_status);
+    return cudaGetLastError() == cudaSuccess ? HUFF_OK : HUFF_ERR_CUDA;
+}
+
+uint64_t huff_m3_max_size(uint64_t n, uint32_t block, uint64_t segment_bytes,
+                          uint32_t chunk_symbols)
+{
+    if (!bwt_args_ok(n, block))
+        return 0;
+    const uint64_t seg = huff_segmented_max_size(n, segment_bytes, chunk_symbols);
+    return seg ? m3_head_bytes((n + block - 1) / block) + seg : 0;
+}
+
+uint64_t huff_m3_workspace_size(uint64_t n, uint32_t block, uint64_t segment_bytes,
+                                uint32_t chunk_symbols)
+{
+    if (!bwt_args_ok(n, block))
+        return 0;
+    const uint64_t seg = huff_segmented_workspace_size(n, segment_bytes, chunk_symbols);
+    if (!seg)
+        return 0;
+    const uint64_t b = huff_bwt_workspace_size(n, block);
+    return ((n + 255) & ~255ull) + (b > seg ? b : seg);
+}
+
+huff_status_t huff_m3_compress(const uint8_t *d_in, uint64_t n, uint32_t block,
+                               uint64_t segment_bytes, uint32_t chunk_symbols, uint8_t *d_out,
+                               uint64_t out_cap, uint64_t *d_out_bytes, void *d_ws,
+                               uint64_t ws_bytes, int32_t *d_status, huff_stream_t stream)
+{
+    const uint64_t need = huff_m3_workspace_size(n, block, segment_bytes, chunk_symbols);
+    const uint64_t count = block ? (n + block - 1) / block : 0;
+    const uint32_t head = m3_head_bytes(count);
+    if (!need || !d_out || !d_out_bytes || !d_status || !d_ws || ws_bytes < need ||
+        out_cap < head || (n && !d_in) || !aligned16(d_out) || !aligned16(d_ws))
+        return HUFF_ERR_INVALID_ARG;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    uint8_t *ws = static_cast<uint8_t *>(d_ws);
+    uint8_t *last = ws;
+    uint8_t *rest = ws + ((n + 255) & ~255ull);
+    huff_status_t st = huff_bwt_forward(d_in, n, block, last,
+                                        reinterpret_cast<uint32_t *>(d_out + 16), rest,
+                                        ws_bytes - (uint64_t)(rest - ws), d_status, stream);
+    if (st != HUFF_OK)
+        return st;
+    k_m3_header<<<1, 256, 0, s>>>(d_out, n, block, (uint32_t)count, head);
+    if (cudaGetLastError() != cudaSuccess)
+        return HUFF_ERR_CUDA;
+    st = huff_segmented_compress(last, n, segment_bytes, chunk_symbols, d_out + head,
+                                 out_cap - head, d_out_bytes, rest, ws_bytes - (uint64_t)(rest - ws),
+                                 d_status, stream);
+    if (st != HUFF_OK)
+        return st;
+    k_add_u64<<<1, 1, 0, s>>>(reinterpret_cast<unsigned long long *>(d_out_bytes), head, d_status);
+    return cudaGetLastError() == cudaSuccess ? HUFF_OK : HUFF_ERR_CUDA;
+}
+
+uint64_t huff_m3_decompress_workspace_size(uint64_t n, uint32_t block)
+{
+    if (!bwt_args_ok(n, block))
+        return 0;
+    return ((n + 255) & ~255ull) + huff_bwt_workspace_size(n, block);
+}
+
+huff_status_t huff_m3_decompress(const uint8_t *d_in, uint64_t in_bytes, uint8_t *d_out,
+                                 uint64_t out_cap, uint64_t *d_n, void *d_ws, uint64_t ws_bytes,
+                                 int32_t *d_status, huff_stream_t stream)
+{
+    if (!d_in || !d_n || !d_status || !aligned16(d_in) || (d_ws && !aligned16(d_ws)))
+        return HUFF_ERR_INVALID_ARG;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    if (cudaMemsetAsync(d_status, 0, sizeof(int32_t), s) != cudaSuccess)
+        return HUFF_ERR_CUDA;
+    uint8_t h[16];
+    uint64_t n = 0;
+    uint32_t block = 0, count = 0;
+    bool ok = in_bytes >= 16;
+    if (ok) {
+        if (cudaMemcpyAsync(h, d_in, 16, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+            cudaStreamSynchronize(s) != cudaSuccess)
+            return HUFF_ERR_CUDA;
+        for (int i = 7; i >= 0; --i)
+            n = (n << 8) | h[i];
+        for (int i = 11; i >= 8; --i)
+            block = (block << 8) | h[i];
+        for (int i = 15; i >= 12; --i)
+            count = (count << 8) | h[i];
+        ok = block >= 1 && n <= HUFF_BWT_MAX_N && count == (n + block - 1) / block &&
+             16 + 4ull * count <= in_bytes && m3_head_bytes(count) <= in_bytes;
+    }
+    if (!ok) {
+        static const int32_t corrupt = HUFF_ERR_CORRUPT_STREAM;
+        if (cudaMemcpyAsync(d_status, &corrupt, 4, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+            cudaStreamSynchronize(s) != cudaSuccess)
+            return HUFF_ERR_CUDA;
+        return HUFF_OK;
+    }
+    if (n > out_cap) {
+        static const int32_t cap = HUFF_ERR_CAPACITY;
+        if (cudaMemcpyAsync(d_status, &cap, 4, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+            cudaStreamSynchronize(s) != cudaSuccess)
+            return HUFF_ERR_CUDA;
+        return HUFF_OK;
+    }
+    if (!d_out || !d_ws || ws_bytes < huff_m3_decompress_workspace_size(n, block))
+        return HUFF_ERR_INVALID_ARG;
+    const uint32_t head = m3_head_bytes(count);
+    uint8_t *ws = static_cast<uint8_t *>(d_ws);
+    uint8_t *last = ws;
+    uint8_t *rest = ws + ((n + 255) & ~255ull);
+    huff_status_t st = huff_segmented_decompress(d_in + head, in_bytes - head, last, n, d_n,
+                                                 d_status, stream);
+    if (st != HUFF_OK)
+        return st;
+    // the segmented container must hold exactly n bytes
+    uint64_t got = 0;
+    int32_t sst = 0;
+    if (cudaMemcpyAsync(&got, d_n, 8, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaMemcpyAsync(&sst, d_status, 4, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
+        return HUFF_ERR_CUDA;
+    if (sst != 0)
+        return HUFF_OK;  // the segment error stays in *d_status
+    if (got != n) {
+        static const int32_t corrupt = HUFF_ERR_CORRUPT_STREAM;
+        if (cudaMemcpyAsync(d_status, &corrupt, 4, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+            cudaStreamSynchronize(s) != cudaSuccess)
+            return HUFF_ERR_CUDA;
+        return HUFF_OK;
+    }
+    return huff_bwt_inverse(last, n, block, reinterpret_cast<const uint32_t *>(d_in + 16), d_out,
+                            rest, ws_bytes - (uint64_t)(rest - ws), d_status, stream);
+}
+
+}  // extern "C"
