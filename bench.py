@@ -294,6 +294,71 @@ def measure_batched(hg, synth, torch, count=4096):
             "speedup_compress": pc / tc, "speedup_decompress": pd / td}
 
 
+def measure_method3(hg, synth, torch, oracle=None, n=256 << 20, block=1 << 20,
+                    segment=16384):
+    """Method 3 (NEXT row): the block-sorting transform of every 1 MiB block of
+    256 MiB of synthetic text, its inverse, and the Method 3 container (16 KiB
+    segments, one codebook each), timed with CUDA events around the
+    synchronous calls; the compression ratio against Method 2 at the same
+    segment size and against one codebook; the oracle's transform timed on a
+    sample of blocks on the host."""
+    x = torch.from_numpy(synth.text(n, 1)).cuda()
+    wsb = hg.lib().huff_bwt_workspace_size(n, block)
+    ws = torch.empty(wsb, dtype=torch.uint8, device="cuda")
+    last = torch.empty(n, dtype=torch.uint8, device="cuda")
+    prim = torch.empty((n + block - 1) // block, dtype=torch.int32, device="cuda")
+    back = torch.empty(n, dtype=torch.uint8, device="cuda")
+
+    def t_ms(fn, reps=3, warm=1):
+        for _ in range(warm):
+            fn()
+        torch.cuda.synchronize()
+        ts = []
+        for _ in range(reps):
+            s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            s.record()
+            fn()
+            e.record()
+            torch.cuda.synchronize()
+            ts.append(s.elapsed_time(e))
+        return float(statistics.median(ts))
+
+    tf = t_ms(lambda: hg.huff_bwt_forward(x, block, d_last=last, d_primary=prim, ws=ws))
+    ti = t_ms(lambda: hg.huff_bwt_inverse(last, block, prim, d_out=back, ws=ws))
+    ok = bool(torch.equal(back, x))
+    del ws
+    c, st = hg.huff_m3_compress(x, block, segment)
+    tc = t_ms(lambda: hg.huff_m3_compress(x, block, segment), reps=2)
+    y, m, st2 = hg.huff_m3_decompress(c)
+    td = t_ms(lambda: hg.huff_m3_decompress(c), reps=2)
+    ok = ok and int(st.item()) == 0 and int(st2.item()) == 0 and m == n and bool(torch.equal(y, x))
+    seg_c, _ = hg.huff_segmented_compress(x, segment)
+    one = hg.compress(x)
+    out = {"workload": f"synthetic text {n >> 20} MiB (seed 1), {block >> 20} MiB blocks, "
+                       f"{segment >> 10} KiB segments",
+           "round_trip_ok": ok,
+           "forward_ms": tf, "forward_gbs": n / tf / 1e6,
+           "inverse_ms": ti, "inverse_gbs": n / ti / 1e6,
+           "m3_compress_ms": tc, "m3_compress_gbs": n / tc / 1e6,
+           "m3_decompress_ms": td, "m3_decompress_gbs": n / td / 1e6,
+           "ratio_m3": c.numel() / n, "ratio_segmented_same_segments": seg_c.numel() / n,
+           "ratio_one_codebook": one.numel() / n,
+           "bound": "hbm (stable radix passes and random rank scatters); see "
+                    "profiles/k_radix_scatter_bwt_64m.md"}
+    if oracle is not None:
+        xs = x[:4 * block].cpu().numpy()
+        t0 = time.perf_counter()
+        L, P = oracle.bwt(xs, block)
+        t1 = time.perf_counter()
+        oracle.ibwt(L, block, P)
+        t2 = time.perf_counter()
+        out["cpu_baseline"] = {"kind": "oracle", "cores": 1,
+                               "sample": f"the first 4 blocks ({4 * block >> 20} MiB)",
+                               "forward_gbs": xs.size / (t1 - t0) / 1e9,
+                               "inverse_gbs": xs.size / (t2 - t1) / 1e9}
+    return out
+
+
 def measure_served(hg, synth, oracle, torch, loads=(10.0, 20.0, 50.0, 100.0, 150.0, 200.0),
                    seconds=1.0, max_requests=2000):
     """Config 5: open-loop Poisson arrivals of 50/50 compress/decompress
@@ -540,12 +605,17 @@ def run_ours(args):
     if not ok:
         raise SystemExit("bench: end-to-end round trip failed")
     del h_x
-    batched = served = None
+    batched = served = method3 = None
     if rank == 0 and not args.no_batched:
         batched = measure_batched(hg, synth, torch)
     if rank == 0 and not args.no_served:
         import oracle
         served = measure_served(hg, synth, oracle, torch)
+    if rank == 0 and not args.no_method3:
+        m3_oracle = None
+        if world == 1 and not args.no_cpu:
+            import oracle as m3_oracle
+        method3 = measure_method3(hg, synth, torch, m3_oracle)
 
     if rank != 0:
         if dist is not None:
@@ -596,6 +666,7 @@ def run_ours(args):
         "kernels": kern,
         "batched": batched,
         "served": served,
+        "method3": method3,
         "cpu_baseline": base,
     }
     print(json.dumps(line), flush=True)
@@ -634,6 +705,8 @@ def main():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-baseline sample")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched measurement")
     ap.add_argument("--no-served", action="store_true", help="skip the served measurement")
+    ap.add_argument("--no-method3", action="store_true",
+                    help="skip the Method 3 (block-sorting transform) measurement")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -82,17 +82,18 @@ __global__ void k_bwt_init(const uint8_t *x, uint32_t n, uint32_t block, uint64_
     }
 }
 
-// round r keys: (group, rank of the rotation h bytes on, relative to the block)
+// round r keys: (group, rank of the rotation h bytes on, relative to the
+// block), packed so that the passes cover only the bits in use
 __global__ void k_bwt_round_keys(const uint32_t *sa, const uint32_t *rk, const uint32_t *act,
                                  const uint32_t *grp, uint32_t count, uint32_t n, uint32_t block,
-                                 uint64_t h, uint64_t *key, uint32_t *val)
+                                 uint64_t h, uint32_t lo_bits, uint64_t *key, uint32_t *val)
 {
     for (uint32_t k = blockIdx.x * kEw + threadIdx.x; k < count; k += gridDim.x * kEw) {
         const uint32_t i = sa[act[k]];
         uint32_t s, m;
         block_span(i, block, n, s, m);
         const uint32_t j = s + (uint32_t)(((uint64_t)(i - s) + h) % m);
-        key[k] = ((uint64_t)grp[k] << 32) | (rk[j] - s);
+        key[k] = ((uint64_t)grp[k] << lo_bits) | (rk[j] - s);
         val[k] = i;
     }
 }
@@ -201,19 +202,14 @@ FwdWs fwd_layout(uint8_t *base, uint64_t n)
     return w;
 }
 
-// stable LSD over the key bits [0, lo_bits) and [32, 32 + hi_bits)
-cudaError_t sort_two_fields(FwdWs &w, uint32_t count, uint32_t lo_bits, uint32_t hi_bits,
-                            cudaStream_t s, uint64_t *&ks, uint32_t *&vs)
+// stable LSD over the key bits [0, bits)
+cudaError_t sort_keys(FwdWs &w, uint32_t count, uint32_t bits, cudaStream_t s, uint64_t *&ks,
+                      uint32_t *&vs)
 {
-    bool f1 = false, f2 = false;
-    cudaError_t e = radix_sort_bits(w.k0, w.v0, w.k1, w.v1, count, 0, lo_bits, w.radix, s, f1);
-    if (e != cudaSuccess)
-        return e;
-    uint64_t *ka = f1 ? w.k1 : w.k0, *kb = f1 ? w.k0 : w.k1;
-    uint32_t *va = f1 ? w.v1 : w.v0, *vb = f1 ? w.v0 : w.v1;
-    e = radix_sort_bits(ka, va, kb, vb, count, 32, 32 + hi_bits, w.radix, s, f2);
-    ks = f2 ? kb : ka;
-    vs = f2 ? vb : va;
+    bool f = false;
+    const cudaError_t e = radix_sort_bits(w.k0, w.v0, w.k1, w.v1, count, 0, bits, w.radix, s, f);
+    ks = f ? w.k1 : w.k0;
+    vs = f ? w.v1 : w.v0;
     return e;
 }
 
@@ -495,16 +491,16 @@ huff_status_t huff_bwt_forward(const uint8_t *d_in, uint64_t n, uint32_t block, 
     k_bwt_init<<<ew_grid(n), kEw, 0, s>>>(d_in, N, block, w.k0, w.v0, w.act);
     uint64_t *ks;
     uint32_t *vs;
-    if (sort_two_fields(w, N, 32, bit_width(blocks - 1), s, ks, vs) != cudaSuccess)
+    if (sort_keys(w, N, 32 + bit_width(blocks - 1), s, ks, vs) != cudaSuccess)
         return HUFF_ERR_CUDA;
     uint32_t n_act = 0, groups = 0;
     if (refine(w, ks, vs, N, s, n_act, groups) != cudaSuccess)
         return HUFF_ERR_CUDA;
     for (uint64_t h = 4; n_act > 0 && h < mmax; h *= 2) {
+        const uint32_t lo_bits = bit_width(mmax - 1);
         k_bwt_round_keys<<<ew_grid(n_act), kEw, 0, s>>>(w.sa, w.rk, w.act, w.grp, n_act, N, block, h,
-                                                        w.k0, w.v0);
-        if (sort_two_fields(w, n_act, bit_width(mmax - 1), bit_width(groups - 1), s, ks, vs) !=
-            cudaSuccess)
+                                                        lo_bits, w.k0, w.v0);
+        if (sort_keys(w, n_act, lo_bits + bit_width(groups - 1), s, ks, vs) != cudaSuccess)
             return HUFF_ERR_CUDA;
         if (refine(w, ks, vs, n_act, s, n_act, groups) != cudaSuccess)
             return HUFF_ERR_CUDA;

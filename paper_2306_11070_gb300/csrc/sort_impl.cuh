@@ -161,11 +161,16 @@ __global__ void __launch_bounds__(kRadixThreads) k_radix_count(const uint64_t *k
     __syncthreads();
     const uint64_t base = (uint64_t)blockIdx.x * kRadixTile;
     const int lane = threadIdx.x & 31;
+    uint32_t dig[kRadixItems];
+#pragma unroll
+    for (int j = 0; j < kRadixItems; ++j) {  // every load in flight before the first use
+        const uint64_t e = base + (uint64_t)j * kRadixThreads + threadIdx.x;
+        dig[j] = e < count ? (uint32_t)(keys[e] >> shift) & 255u : 256u;
+    }
 #pragma unroll
     for (int j = 0; j < kRadixItems; ++j) {
-        const uint64_t e = base + (uint64_t)j * kRadixThreads + threadIdx.x;
-        const bool ok = e < count;
-        const uint32_t d = ok ? (uint32_t)(keys[e] >> shift) & 255u : 256u;
+        const uint32_t d = dig[j];
+        const bool ok = d < 256u;
         const uint32_t mask = __match_any_sync(0xffffffffu, d);
         // one shared add per distinct digit of the warp step
         if (ok && lane == __ffs(mask) - 1)
@@ -195,11 +200,16 @@ __global__ void __launch_bounds__(kRadixThreads) k_radix_scatter(
     uint64_t key[kRadixItems];
     uint32_t val[kRadixItems], rank[kRadixItems];
 #pragma unroll
-    for (int j = 0; j < kRadixItems; ++j) {
+    for (int j = 0; j < kRadixItems; ++j) {  // every load in flight before the first use
         const uint64_t e = base + (uint64_t)j * 32 + lane;
         const bool ok = e < count;
         key[j] = ok ? kin[e] : 0ull;
         val[j] = ok ? vin[e] : 0u;
+    }
+#pragma unroll
+    for (int j = 0; j < kRadixItems; ++j) {
+        const uint64_t e = base + (uint64_t)j * 32 + lane;
+        const bool ok = e < count;
         const uint32_t d = ok ? (uint32_t)(key[j] >> shift) & 255u : 256u;
         const uint32_t mask = __match_any_sync(0xffffffffu, d);
         rank[j] = ok ? wcnt[w][d & 255u] + __popc(mask & lanemask_lt()) : 0u;
