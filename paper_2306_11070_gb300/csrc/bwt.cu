@@ -98,54 +98,184 @@ __global__ void k_bwt_round_keys(const uint32_t *sa, const uint32_t *rk, const u
     }
 }
 
-// sorted slots back into SA; a group starts where the key changes
-__global__ void k_bwt_heads(const uint64_t *key, const uint32_t *val, const uint32_t *act,
-                            uint32_t count, uint32_t *sa, uint32_t *head)
+// ---- refining the groups of a sorted active list ---------------------------
+// Element k of the sorted list starts a group when its key differs from
+// k-1's (head), and its group has two members or more unless it is a head
+// whose successor is a head too (flag).  One scan over the list gives, per
+// element, the number of heads up to it (its group's number + 1), the number
+// of flagged elements before it (its place in the next active list) and the
+// largest head slot up to it (its group's first slot: slots increase along
+// the list, so the last head wins), the three carried together.
+constexpr int kRfThreads = 512;
+constexpr int kRfItems = 8;
+constexpr uint32_t kRfTile = kRfThreads * kRfItems;
+
+struct AddOp {
+    __device__ __forceinline__ uint32_t operator()(uint32_t a, uint32_t b) const { return a + b; }
+};
+struct MaxOp {
+    __device__ __forceinline__ uint32_t operator()(uint32_t a, uint32_t b) const { return a > b ? a : b; }
+};
+
+// block-wide exclusive scan under op (kRfThreads threads), *total the
+// reduction of all
+template <class Op>
+__device__ __forceinline__ uint32_t rf_block_scan(uint32_t v, uint32_t *ws, uint32_t &total, Op op,
+                                                  uint32_t id)
 {
-    for (uint32_t k = blockIdx.x * kEw + threadIdx.x; k < count; k += gridDim.x * kEw) {
-        sa[act[k]] = val[k];
-        head[k] = (k == 0 || key[k] != key[k - 1]) ? 1u : 0u;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    uint32_t x = v;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, x, d);
+        if (lane >= d)
+            x = op(x, y);
     }
-}
-
-// gi = inclusive count of heads: group of k is gi[k] - 1
-__global__ void k_bwt_group_starts(const uint32_t *head, const uint32_t *gi, uint32_t count,
-                                   uint32_t *gstart)
-{
-    for (uint32_t k = blockIdx.x * kEw + threadIdx.x; k < count; k += gridDim.x * kEw) {
-        if (head[k])
-            gstart[gi[k] - 1] = k;
-        if (k + 1 == count)
-            gstart[gi[k]] = count;
-    }
-}
-
-__device__ __forceinline__ uint32_t group_size(const uint32_t *gstart, uint32_t g)
-{
-    return gstart[g + 1] - gstart[g];
-}
-
-// new ranks; flag = the element's group still has two members or more
-__global__ void k_bwt_rank(const uint32_t *val, const uint32_t *gi, const uint32_t *gstart,
-                           const uint32_t *act, uint32_t count, uint32_t *rk, uint32_t *flag)
-{
-    for (uint32_t k = blockIdx.x * kEw + threadIdx.x; k < count; k += gridDim.x * kEw) {
-        const uint32_t g = gi[k] - 1;
-        rk[val[k]] = act[gstart[g]];
-        flag[k] = group_size(gstart, g) > 1 ? 1u : 0u;
-    }
-}
-
-// keep the unresolved elements, in slot order, with their group numbers
-__global__ void k_bwt_compact(const uint32_t *gi, const uint32_t *gstart, const uint32_t *fpos,
-                              const uint32_t *act, uint32_t count, uint32_t *act2, uint32_t *grp2)
-{
-    for (uint32_t k = blockIdx.x * kEw + threadIdx.x; k < count; k += gridDim.x * kEw) {
-        const uint32_t g = gi[k] - 1;
-        if (group_size(gstart, g) > 1) {
-            act2[fpos[k]] = act[k];
-            grp2[fpos[k]] = g;
+    if (lane == 31)
+        ws[w] = x;
+    __syncthreads();
+    if (w == 0) {
+        uint32_t t = lane < kRfThreads / 32 ? ws[lane] : id;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, t, d);
+            if (lane >= d)
+                t = op(t, y);
         }
+        if (lane < kRfThreads / 32)
+            ws[lane] = t;
+    }
+    __syncthreads();
+    total = ws[kRfThreads / 32 - 1];
+    const uint32_t before = w > 0 ? ws[w - 1] : id;
+    uint32_t xe = __shfl_up_sync(0xffffffffu, x, 1);
+    if (lane == 0)
+        xe = id;
+    __syncthreads();
+    return op(before, xe);
+}
+
+struct RfItems {
+    uint32_t head[kRfItems], flag[kRfItems], slot[kRfItems];
+};
+
+// the values of this thread's kRfItems consecutive elements
+__device__ __forceinline__ RfItems rf_items(const uint64_t *key, const uint32_t *act,
+                                            uint32_t count, uint64_t base)
+{
+    uint64_t kk[kRfItems + 2];
+#pragma unroll
+    for (int j = 0; j < kRfItems + 2; ++j) {
+        const uint64_t k = base + j;  // element k - 1
+        kk[j] = (k >= 1 && k - 1 < count) ? key[k - 1] : 0ull;
+    }
+    RfItems r;
+#pragma unroll
+    for (int j = 0; j < kRfItems; ++j) {
+        const uint64_t k = base + j;
+        const bool ok = k < count;
+        const bool hd = ok && (k == 0 || kk[j + 1] != kk[j]);
+        const bool nh = k + 1 >= count || kk[j + 2] != kk[j + 1];
+        r.head[j] = hd ? 1u : 0u;
+        r.flag[j] = (ok && !(hd && nh)) ? 1u : 0u;
+        r.slot[j] = hd ? act[k] : 0u;
+    }
+    return r;
+}
+
+__global__ void __launch_bounds__(kRfThreads) k_refine_tiles(const uint64_t *key, const uint32_t *act,
+                                                             uint32_t count, uint32_t *ph,
+                                                             uint32_t *pf, uint32_t *pm)
+{
+    __shared__ uint32_t ws[kRfThreads / 32];
+    const uint64_t base = (uint64_t)blockIdx.x * kRfTile + (uint64_t)threadIdx.x * kRfItems;
+    const RfItems r = rf_items(key, act, count, base);
+    uint32_t h = 0, f = 0, m = 0;
+#pragma unroll
+    for (int j = 0; j < kRfItems; ++j) {
+        h += r.head[j];
+        f += r.flag[j];
+        m = r.slot[j] > m ? r.slot[j] : m;
+    }
+    uint32_t th, tf, tm;
+    rf_block_scan(h, ws, th, AddOp(), 0u);
+    rf_block_scan(f, ws, tf, AddOp(), 0u);
+    rf_block_scan(m, ws, tm, MaxOp(), 0u);
+    if (threadIdx.x == 0) {
+        ph[blockIdx.x] = th;
+        pf[blockIdx.x] = tf;
+        pm[blockIdx.x] = tm;
+    }
+}
+
+// one CTA: exclusive scans of the tile aggregates in place; the totals of
+// heads (groups) and flags (next active count) to tot[0], tot[1]
+__global__ void __launch_bounds__(kRfThreads) k_refine_parts(uint32_t *ph, uint32_t *pf, uint32_t *pm,
+                                                             uint32_t tiles, uint32_t *tot)
+{
+    __shared__ uint32_t ws[kRfThreads / 32];
+    uint32_t ch = 0, cf = 0, cm = 0;
+    for (uint32_t b = 0; b < tiles; b += kRfThreads) {
+        const uint32_t i = b + threadIdx.x;
+        const bool ok = i < tiles;
+        uint32_t th, tf, tm;
+        const uint32_t xh = rf_block_scan(ok ? ph[i] : 0u, ws, th, AddOp(), 0u);
+        const uint32_t xf = rf_block_scan(ok ? pf[i] : 0u, ws, tf, AddOp(), 0u);
+        const uint32_t xm = rf_block_scan(ok ? pm[i] : 0u, ws, tm, MaxOp(), 0u);
+        if (ok) {
+            ph[i] = ch + xh;
+            pf[i] = cf + xf;
+            pm[i] = xm > cm ? xm : cm;
+        }
+        ch += th;
+        cf += tf;
+        cm = tm > cm ? tm : cm;
+    }
+    if (threadIdx.x == 0) {
+        tot[0] = ch;
+        tot[1] = cf;
+    }
+}
+
+// sorted slots back into SA, new ranks scattered to the positions, and the
+// elements of groups still unresolved appended to the next active list with
+// their group numbers
+__global__ void __launch_bounds__(kRfThreads) k_refine_apply(
+    const uint64_t *key, const uint32_t *val, const uint32_t *act, uint32_t count,
+    const uint32_t *ph, const uint32_t *pf, const uint32_t *pm, uint32_t *sa, uint32_t *rk,
+    uint32_t *act2, uint32_t *grp2)
+{
+    __shared__ uint32_t ws[kRfThreads / 32];
+    const uint64_t base = (uint64_t)blockIdx.x * kRfTile + (uint64_t)threadIdx.x * kRfItems;
+    const RfItems r = rf_items(key, act, count, base);
+    uint32_t h = 0, f = 0, m = 0;
+#pragma unroll
+    for (int j = 0; j < kRfItems; ++j) {
+        h += r.head[j];
+        f += r.flag[j];
+        m = r.slot[j] > m ? r.slot[j] : m;
+    }
+    uint32_t th, tf, tm;
+    uint32_t gh = ph[blockIdx.x] + rf_block_scan(h, ws, th, AddOp(), 0u);
+    uint32_t gf = pf[blockIdx.x] + rf_block_scan(f, ws, tf, AddOp(), 0u);
+    const uint32_t xm = rf_block_scan(m, ws, tm, MaxOp(), 0u);
+    const uint32_t pmb = pm[blockIdx.x];
+    uint32_t gm = xm > pmb ? xm : pmb;
+#pragma unroll
+    for (int j = 0; j < kRfItems; ++j) {
+        const uint64_t k = base + j;
+        if (k >= count)
+            break;
+        gh += r.head[j];
+        gm = r.slot[j] > gm ? r.slot[j] : gm;
+        const uint32_t a = act[k], v = val[k];
+        sa[a] = v;
+        rk[v] = gm;
+        if (r.flag[j]) {
+            act2[gf] = a;
+            grp2[gf] = gh - 1;
+        }
+        gf += r.flag[j];
     }
 }
 
@@ -163,10 +293,10 @@ __global__ void k_bwt_output(const uint8_t *x, const uint32_t *sa, uint32_t n, u
 }
 
 struct FwdWs {
-    uint32_t *sa, *rk, *act, *act2, *grp, *grp2, *head, *gi, *gstart, *scal;
+    uint32_t *sa, *rk, *act, *act2, *grp, *grp2, *part, *scal;
     uint64_t *k0, *k1;
     uint32_t *v0, *v1;
-    void *radix, *part;
+    void *radix;
     uint64_t bytes;
 };
 
@@ -188,16 +318,13 @@ FwdWs fwd_layout(uint8_t *base, uint64_t n)
     w.act2 = carve<uint32_t>(base, off, 4 * n);
     w.grp = carve<uint32_t>(base, off, 4 * n);
     w.grp2 = carve<uint32_t>(base, off, 4 * n);
-    w.head = carve<uint32_t>(base, off, 4 * n);
-    w.gi = carve<uint32_t>(base, off, 4 * n);
-    w.gstart = carve<uint32_t>(base, off, 4 * (n + 1));
+    w.part = carve<uint32_t>(base, off, 3 * 4 * (uint64_t)div_up(n, kRfTile) + 16);
     w.scal = carve<uint32_t>(base, off, 16);
     w.k0 = carve<uint64_t>(base, off, 8 * n);
     w.k1 = carve<uint64_t>(base, off, 8 * n);
     w.v0 = carve<uint32_t>(base, off, 4 * n);
     w.v1 = carve<uint32_t>(base, off, 4 * n);
     w.radix = carve<uint8_t>(base, off, radix_scratch_bytes(n));
-    w.part = carve<uint8_t>(base, off, scan_parts_bytes(n));
     w.bytes = off;
     return w;
 }
@@ -218,18 +345,14 @@ cudaError_t sort_keys(FwdWs &w, uint32_t count, uint32_t bits, cudaStream_t s, u
 cudaError_t refine(FwdWs &w, const uint64_t *ks, const uint32_t *vs, uint32_t count,
                    cudaStream_t s, uint32_t &n_act, uint32_t &groups)
 {
-    const unsigned g = ew_grid(count);
-    k_bwt_heads<<<g, kEw, 0, s>>>(ks, vs, w.act, count, w.sa, w.head);
-    cudaError_t e = scan_u32(w.head, w.gi, count, true, static_cast<uint32_t *>(w.part), w.scal, s);
-    if (e != cudaSuccess)
-        return e;
-    k_bwt_group_starts<<<g, kEw, 0, s>>>(w.head, w.gi, count, w.gstart);
-    k_bwt_rank<<<g, kEw, 0, s>>>(vs, w.gi, w.gstart, w.act, count, w.rk, w.head);
-    e = scan_u32(w.head, w.head, count, false, static_cast<uint32_t *>(w.part), w.scal + 1, s);
-    if (e != cudaSuccess)
-        return e;
-    k_bwt_compact<<<g, kEw, 0, s>>>(w.gi, w.gstart, w.head, w.act, count, w.act2, w.grp2);
+    const uint32_t tiles = div_up(count, kRfTile);
+    uint32_t *ph = w.part, *pf = w.part + tiles, *pm = w.part + 2 * tiles;
+    k_refine_tiles<<<tiles, kRfThreads, 0, s>>>(ks, w.act, count, ph, pf, pm);
+    k_refine_parts<<<1, kRfThreads, 0, s>>>(ph, pf, pm, tiles, w.scal);
+    k_refine_apply<<<tiles, kRfThreads, 0, s>>>(ks, vs, w.act, count, ph, pf, pm, w.sa, w.rk,
+                                                 w.act2, w.grp2);
     uint32_t h[2];
+    cudaError_t e;
     if ((e = cudaGetLastError()) != cudaSuccess ||
         (e = cudaMemcpyAsync(h, w.scal, sizeof(h), cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
         (e = cudaStreamSynchronize(s)) != cudaSuccess)
