@@ -24,8 +24,6 @@
 // re-walks its stretch writing the bytes in place.  A periodic block's walk
 // returns to the primary row after one period c; the rest of the block
 // repeats it.
-#include <vector>
-
 #include "sort_impl.cuh"
 
 namespace huff {
