@@ -3,6 +3,7 @@
 // touches the data on the host.
 #include <cstdint>
 
+#include "api_trace.h"
 #include "huff_internal.cuh"
 
 namespace huff {
@@ -91,6 +92,7 @@ uint64_t huff_workspace_size(uint64_t n, uint32_t chunk_symbols)
 
 huff_status_t huff_histogram(const uint8_t *d_in, uint64_t n, uint64_t *d_hist, huff_stream_t stream)
 {
+    HUFF_API_RANGE("huff_histogram");
     if (!d_hist || (n && !d_in) || (d_in && !aligned16(d_in)))
         return HUFF_ERR_INVALID_ARG;
     return cuda_status(launch_histogram(d_in, n, reinterpret_cast<unsigned long long *>(d_hist),
@@ -102,6 +104,7 @@ uint64_t huff_unit_hist_size(uint64_t n) { return unit_hist_bytes(n); }
 huff_status_t huff_histogram_units(const uint8_t *d_in, uint64_t n, uint64_t *d_hist,
                                    uint16_t *d_unit_hist, huff_stream_t stream)
 {
+    HUFF_API_RANGE("huff_histogram_units");
     if (!d_hist || !d_unit_hist || (n && !d_in) || (d_in && !aligned16(d_in)) ||
         !aligned16(d_unit_hist))
         return HUFF_ERR_INVALID_ARG;
@@ -112,6 +115,7 @@ huff_status_t huff_histogram_units(const uint8_t *d_in, uint64_t n, uint64_t *d_
 huff_status_t huff_build_codebook(const uint64_t *d_hist, huff_codebook_t *d_cb, int32_t *d_status,
                                   huff_stream_t stream)
 {
+    HUFF_API_RANGE("huff_build_codebook");
     if (!d_hist || !d_cb || !d_status)
         return HUFF_ERR_INVALID_ARG;
     return cuda_status(launch_build_codebook(reinterpret_cast<const unsigned long long *>(d_hist),
@@ -123,6 +127,7 @@ huff_status_t huff_build_codebook_limited(const uint64_t *d_hist, uint32_t max_l
                                           huff_codebook_t *d_cb, int32_t *d_status,
                                           huff_stream_t stream)
 {
+    HUFF_API_RANGE("huff_build_codebook_limited");
     if (!d_hist || !d_cb || !d_status || max_len < 1 || max_len > kMaxCodeLen)
         return HUFF_ERR_INVALID_ARG;
     return cuda_status(launch_build_codebook(reinterpret_cast<const unsigned long long *>(d_hist),
@@ -135,6 +140,7 @@ huff_status_t huff_encode(const uint8_t *d_in, uint64_t n, const huff_codebook_t
                           uint64_t *d_out_bytes, void *d_ws, uint64_t ws_bytes, int32_t *d_status,
                           huff_stream_t stream)
 {
+    HUFF_API_RANGE("huff_encode");
     if (!chunk_symbols_valid(chunk_symbols) || !d_cb || !d_out || !d_out_bytes || !d_ws ||
         !d_status || (n && !d_in) || (d_in && !aligned16(d_in)) || !aligned16(d_out) ||
         !aligned16(d_ws) || ws_bytes < encode_workspace_bytes(n) ||
@@ -151,6 +157,7 @@ huff_status_t huff_encode_units(const uint8_t *d_in, uint64_t n, const huff_code
                                 void *d_ws, uint64_t ws_bytes, int32_t *d_status,
                                 huff_stream_t stream)
 {
+    HUFF_API_RANGE("huff_encode_units");
     if (!chunk_symbols_valid(chunk_symbols) || !d_cb || !d_out || !d_out_bytes || !d_ws ||
         !d_status || !d_unit_hist || !aligned16(d_unit_hist) || (n && !d_in) ||
         (d_in && !aligned16(d_in)) || !aligned16(d_out) || !aligned16(d_ws) ||
@@ -164,6 +171,7 @@ huff_status_t huff_encode_units(const uint8_t *d_in, uint64_t n, const huff_code
 huff_status_t huff_decode(const uint8_t *d_stream, uint64_t stream_bytes, uint8_t *d_out,
                           uint64_t out_cap, uint64_t *d_n, int32_t *d_status, huff_stream_t stream)
 {
+    HUFF_API_RANGE("huff_decode");
     if (!d_stream || !d_n || !d_status || !aligned16(d_stream) || (d_out && !aligned16(d_out)) ||
         (!d_out && out_cap))
         return HUFF_ERR_INVALID_ARG;
@@ -176,6 +184,7 @@ huff_status_t huff_compress(const uint8_t *d_in, uint64_t n, uint32_t chunk_symb
                             uint64_t out_cap, uint64_t *d_out_bytes, void *d_ws, uint64_t ws_bytes,
                             int32_t *d_status, huff_stream_t stream)
 {
+    HUFF_API_RANGE("huff_compress");
     if (!chunk_symbols_valid(chunk_symbols) || !d_ws || !aligned16(d_ws) || !d_status ||
         !d_out || !d_out_bytes || (n && !d_in) || (d_in && !aligned16(d_in)) ||
         !aligned16(d_out) || ws_bytes < huff_workspace_size(n, chunk_symbols) ||

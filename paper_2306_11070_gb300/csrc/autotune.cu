@@ -15,6 +15,7 @@
 #include <tuple>
 #include <vector>
 
+#include "api_trace.h"
 #include "huff_internal.cuh"
 
 namespace {
@@ -106,6 +107,7 @@ extern "C" huff_status_t huff_batch_autotune(const huff_batch_desc_t *descs, uin
                                              uint32_t flags, huff_batch_params_t *best,
                                              huff_stream_t stream)
 {
+    HUFF_API_RANGE("huff_batch_autotune");
     if (!descs || count == 0 || !best ||
         (op != HUFF_BATCH_COMPRESS && op != HUFF_BATCH_DECOMPRESS))
         return HUFF_ERR_INVALID_ARG;

@@ -27,6 +27,7 @@
 #include <new>
 #include <vector>
 
+#include "api_trace.h"
 #include "batch_internal.cuh"
 #include "codebook_impl.cuh"
 #include "decode_impl.cuh"
@@ -571,6 +572,7 @@ void huff_batch_default_params(huff_batch_params_t *params)
 huff_status_t huff_batch_plan(const huff_batch_desc_t *descs, uint32_t count, huff_op_t op,
                               const huff_batch_params_t *params, huff_batch_plan_t **out_plan)
 {
+    HUFF_API_RANGE("huff_batch_plan");
     if (!out_plan)
         return HUFF_ERR_INVALID_ARG;
     *out_plan = nullptr;
@@ -642,6 +644,7 @@ huff_status_t huff_batch_plan(const huff_batch_desc_t *descs, uint32_t count, hu
 
 huff_status_t huff_batch_run(huff_batch_plan_t *plan, huff_stream_t stream)
 {
+    HUFF_API_RANGE("huff_batch_run");
     if (!plan)
         return HUFF_ERR_INVALID_ARG;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);

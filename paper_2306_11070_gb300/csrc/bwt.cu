@@ -24,6 +24,7 @@
 // re-walks its stretch writing the bytes in place.  A periodic block's walk
 // returns to the primary row after one period c; the rest of the block
 // repeats it.
+#include "api_trace.h"
 #include "sort_impl.cuh"
 
 namespace huff {
@@ -597,6 +598,7 @@ huff_status_t huff_bwt_forward(const uint8_t *d_in, uint64_t n, uint32_t block, 
                                uint32_t *d_primary, void *d_ws, uint64_t ws_bytes,
                                int32_t *d_status, huff_stream_t stream)
 {
+    HUFF_API_RANGE("huff_bwt_forward");
     if (!bwt_args_ok(n, block) || !d_status || (n && (!d_in || !d_last || !d_primary || !d_ws)) ||
         (n && ws_bytes < huff_bwt_workspace_size(n, block)) || (d_ws && !aligned16(d_ws)))
         return HUFF_ERR_INVALID_ARG;
@@ -634,6 +636,7 @@ huff_status_t huff_bwt_inverse(const uint8_t *d_last, uint64_t n, uint32_t block
                                const uint32_t *d_primary, uint8_t *d_out, void *d_ws,
                                uint64_t ws_bytes, int32_t *d_status, huff_stream_t stream)
 {
+    HUFF_API_RANGE("huff_bwt_inverse");
     if (!bwt_args_ok(n, block) || !d_status || (n && (!d_last || !d_primary || !d_out || !d_ws)) ||
         (n && ws_bytes < huff_bwt_workspace_size(n, block)) || (d_ws && !aligned16(d_ws)))
         return HUFF_ERR_INVALID_ARG;
@@ -711,6 +714,7 @@ huff_status_t huff_m3_compress(const uint8_t *d_in, uint64_t n, uint32_t block,
                                uint64_t out_cap, uint64_t *d_out_bytes, void *d_ws,
                                uint64_t ws_bytes, int32_t *d_status, huff_stream_t stream)
 {
+    HUFF_API_RANGE("huff_m3_compress");
     const uint64_t need = huff_m3_workspace_size(n, block, segment_bytes, chunk_symbols);
     const uint64_t count = block ? (n + block - 1) / block : 0;
     const uint32_t head = m3_head_bytes(count);
@@ -749,6 +753,7 @@ huff_status_t huff_m3_decompress(const uint8_t *d_in, uint64_t in_bytes, uint8_t
                                  uint64_t out_cap, uint64_t *d_n, void *d_ws, uint64_t ws_bytes,
                                  int32_t *d_status, huff_stream_t stream)
 {
+    HUFF_API_RANGE("huff_m3_decompress");
     if (!d_in || !d_n || !d_status || !aligned16(d_in) || (d_ws && !aligned16(d_ws)))
         return HUFF_ERR_INVALID_ARG;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);

@@ -18,6 +18,7 @@
 // on it.
 #include <mutex>
 
+#include "api_trace.h"
 #include "huff_internal.cuh"
 
 namespace {
@@ -62,6 +63,7 @@ extern "C" huff_status_t huff_encode_noalloc(const uint8_t *d_in, uint64_t n,
                                              uint64_t *d_out_bytes, int32_t *d_status,
                                              huff_stream_t stream)
 {
+    HUFF_API_RANGE("huff_encode_noalloc");
     if (!huff::chunk_symbols_valid(chunk_symbols) || !d_cb || !d_out || !d_out_bytes ||
         !d_status || (n && !d_in) || (d_in && !aligned16(d_in)) || !aligned16(d_out))
         return HUFF_ERR_INVALID_ARG;

@@ -13,6 +13,7 @@
 #include <cstring>
 #include <vector>
 
+#include "api_trace.h"
 #include "huff_internal.cuh"
 
 namespace huff {
@@ -196,6 +197,7 @@ huff_status_t huff_segmented_compress(const uint8_t *d_in, uint64_t n, uint64_t 
                                       uint64_t *d_out_bytes, void *d_ws, uint64_t ws_bytes,
                                       int32_t *d_status, huff_stream_t stream)
 {
+    HUFF_API_RANGE("huff_segmented_compress");
     SegLayout L;
     if (!seg_layout(n, segment_bytes, chunk_symbols, L) || !d_out || !d_out_bytes || !d_status ||
         (n && !d_in) || !d_ws || ws_bytes < L.ws_bytes || out_cap < L.header ||
@@ -252,6 +254,7 @@ huff_status_t huff_segmented_decompress(const uint8_t *d_in, uint64_t in_bytes, 
                                         uint64_t out_cap, uint64_t *d_n, int32_t *d_status,
                                         huff_stream_t stream)
 {
+    HUFF_API_RANGE("huff_segmented_decompress");
     if (!d_in || !d_n || !d_status || !aligned16(d_in) || (out_cap && !d_out))
         return HUFF_ERR_INVALID_ARG;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);

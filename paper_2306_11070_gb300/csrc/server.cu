@@ -25,6 +25,7 @@
 #include <unordered_map>
 #include <vector>
 
+#include "api_trace.h"
 #include "batch_internal.cuh"
 
 namespace {
@@ -364,6 +365,7 @@ void huff_server_default_config(huff_server_cfg_t *cfg)
 
 huff_status_t huff_server_create(const huff_server_cfg_t *cfg, huff_server_t **out)
 {
+    HUFF_API_RANGE("huff_server_create");
     if (!out)
         return HUFF_ERR_INVALID_ARG;
     *out = nullptr;
@@ -417,6 +419,7 @@ huff_status_t huff_server_create(const huff_server_cfg_t *cfg, huff_server_t **o
 
 huff_status_t huff_server_submit(huff_server_t *S, const huff_request_t *req, uint64_t *ticket)
 {
+    HUFF_API_RANGE("huff_server_submit");
     if (!S || !req || !ticket || (req->op != HUFF_BATCH_COMPRESS && req->op != HUFF_BATCH_DECOMPRESS) ||
         (req->in_bytes && !req->h_in) || !req->h_out)
         return HUFF_ERR_INVALID_ARG;
@@ -477,6 +480,7 @@ huff_status_t huff_server_poll(huff_server_t *S, uint64_t ticket, huff_result_t 
 huff_status_t huff_server_wait(huff_server_t *S, uint64_t ticket, uint32_t timeout_ms,
                                huff_result_t *res)
 {
+    HUFF_API_RANGE("huff_server_wait");
     if (!S || !res)
         return HUFF_ERR_INVALID_ARG;
     std::unique_lock<std::mutex> lk(S->mu);
