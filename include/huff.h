@@ -382,8 +382,14 @@ huff_status_t huff_m3_decompress(const uint8_t *d_in, uint64_t in_bytes, uint8_t
  * `base` (NULL = defaults) supplies everything not tuned.  Tuning RUNS the
  * batch several times on `stream` (the outputs are overwritten with valid
  * results each time) and synchronizes it; with HUFF_TUNE_ROUND_TRIP it also
- * allocates, and frees again, scratch for the decoded bytes.  Errors: those
- * of huff_batch_plan / huff_batch_run, HUFF_ERR_CUDA. */
+ * allocates, and frees again, scratch for the decoded bytes.  With the
+ * environment variable HUFF_TUNE_CACHE naming a file, the cache persists
+ * there as JSON lines (device name/SM count, op, shape buckets, chunk size,
+ * round trip, and the chosen chunk_symbols, ctas_per_sm, decode_lanes): the
+ * file is read on the first call and a line is appended per newly tuned
+ * shape; lines that do not parse or hold values the tuner cannot choose are
+ * ignored.  Errors: those of huff_batch_plan / huff_batch_run,
+ * HUFF_ERR_CUDA. */
 #define HUFF_TUNE_FORCE 1u      /* ignore the cache and tune again */
 #define HUFF_TUNE_ROUND_TRIP 2u /* compress: score by compress + decompress */
 huff_status_t huff_batch_autotune(const huff_batch_desc_t *descs, uint32_t count, huff_op_t op,

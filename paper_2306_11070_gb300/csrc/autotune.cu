@@ -8,10 +8,17 @@
 // independent decoders at the cost of a larger offset table).  The tuner
 // plans the caller's own batch with each candidate, times a few runs with
 // CUDA events on the caller's stream and keeps the fastest; the result is
-// cached per (device, operation, batch shape).
+// cached per (device, operation, batch shape).  With HUFF_TUNE_CACHE set to
+// a file path the cache also persists there, one JSON object per line
+// (device name and SM count, operation, shape, chosen parameters): read on
+// the first call, a line appended for every newly tuned shape.
 #include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
 #include <map>
 #include <mutex>
+#include <string>
 #include <tuple>
 #include <vector>
 
@@ -21,7 +28,7 @@
 namespace {
 
 struct ShapeKey {
-    int device;
+    std::string device;  // name and SM count
     int op;
     uint32_t count_log2, total_log2, mean_log2, cs, round_trip;
     bool operator<(const ShapeKey &o) const
@@ -34,6 +41,85 @@ struct ShapeKey {
 
 std::mutex g_mu;
 std::map<ShapeKey, huff_batch_params_t> g_cache;
+bool g_file_read = false;
+
+const char *cache_path()
+{
+    const char *p = std::getenv("HUFF_TUNE_CACHE");
+    return p && *p ? p : nullptr;
+}
+
+// entries of the cache file (g_mu held); lines that do not parse are skipped
+void read_cache_file()
+{
+    g_file_read = true;
+    const char *path = cache_path();
+    if (!path)
+        return;
+    FILE *f = std::fopen(path, "r");
+    if (!f)
+        return;
+    char line[512];
+    while (std::fgets(line, sizeof line, f)) {
+        char dev[200];
+        ShapeKey k;
+        huff_batch_params_t p;
+        huff_batch_default_params(&p);
+        unsigned op, c, t, m, cs, rt, chunk, ctas, lanes;
+        if (std::sscanf(line,
+                        "{\"device\": \"%199[^\"]\", \"op\": %u, \"count_log2\": %u, "
+                        "\"total_log2\": %u, \"mean_log2\": %u, \"cs\": %u, \"round_trip\": %u, "
+                        "\"chunk_symbols\": %u, \"ctas_per_sm\": %u, \"decode_lanes\": %u}",
+                        dev, &op, &c, &t, &m, &cs, &rt, &chunk, &ctas, &lanes) != 10)
+            continue;
+        const bool lanes_ok = lanes >= 1 && lanes <= 256 && (lanes & (lanes - 1)) == 0;
+        if (!huff::chunk_symbols_valid(chunk) || !lanes_ok || ctas > 64 || rt > 1 ||
+            (op != HUFF_BATCH_COMPRESS && op != HUFF_BATCH_DECOMPRESS))
+            continue;  // not a set the tuner could have chosen
+        k.device = dev;
+        k.op = (int)op;
+        k.count_log2 = c;
+        k.total_log2 = t;
+        k.mean_log2 = m;
+        k.cs = cs;
+        k.round_trip = rt;
+        p.chunk_symbols = chunk;
+        p.ctas_per_sm = ctas;
+        p.decode_lanes = lanes;
+        g_cache[k] = p;
+    }
+    std::fclose(f);
+}
+
+// append one entry (g_mu held)
+void append_cache_file(const ShapeKey &k, const huff_batch_params_t &p)
+{
+    const char *path = cache_path();
+    if (!path)
+        return;
+    FILE *f = std::fopen(path, "a");
+    if (!f)
+        return;
+    std::fprintf(f,
+                 "{\"device\": \"%s\", \"op\": %d, \"count_log2\": %u, \"total_log2\": %u, "
+                 "\"mean_log2\": %u, \"cs\": %u, \"round_trip\": %u, \"chunk_symbols\": %u, "
+                 "\"ctas_per_sm\": %u, \"decode_lanes\": %u}\n",
+                 k.device.c_str(), k.op, k.count_log2, k.total_log2, k.mean_log2, k.cs,
+                 k.round_trip, p.chunk_symbols, p.ctas_per_sm, p.decode_lanes);
+    std::fclose(f);
+}
+
+std::string device_id(int device)
+{
+    cudaDeviceProp prop;
+    if (cudaGetDeviceProperties(&prop, device) != cudaSuccess)
+        return std::to_string(device);
+    std::string name(prop.name);
+    for (char &ch : name)
+        if (ch == '"' || ch == '\\' || ch == '\n')
+            ch = ' ';
+    return name + "/" + std::to_string(prop.multiProcessorCount);
+}
 
 uint32_t log2_bucket(double v) { return v < 1.0 ? 0u : (uint32_t)std::floor(std::log2(v)); }
 
@@ -125,15 +211,22 @@ extern "C" huff_status_t huff_batch_autotune(const huff_batch_desc_t *descs, uin
     int device = 0;
     if (cudaGetDevice(&device) != cudaSuccess)
         return HUFF_ERR_CUDA;
-    const ShapeKey key{device, (int)op, log2_bucket(count), log2_bucket(total),
+    const ShapeKey key{device_id(device), (int)op, log2_bucket(count), log2_bucket(total),
                        log2_bucket(total / count), b0.chunk_symbols, round_trip ? 1u : 0u};
-    if (!(flags & HUFF_TUNE_FORCE)) {
+    {
         std::lock_guard<std::mutex> lk(g_mu);
-        auto it = g_cache.find(key);
-        if (it != g_cache.end()) {
-            *best = it->second;
-            best->use_graph = b0.use_graph;
-            return HUFF_OK;
+        if (!g_file_read)
+            read_cache_file();
+        if (!(flags & HUFF_TUNE_FORCE)) {
+            auto it = g_cache.find(key);
+            if (it != g_cache.end()) {
+                // tuned fields from the cache, the rest from base
+                *best = b0;
+                best->chunk_symbols = it->second.chunk_symbols;
+                best->ctas_per_sm = it->second.ctas_per_sm;
+                best->decode_lanes = it->second.decode_lanes;
+                return HUFF_OK;
+            }
         }
     }
 
@@ -240,6 +333,7 @@ extern "C" huff_status_t huff_batch_autotune(const huff_batch_desc_t *descs, uin
     {
         std::lock_guard<std::mutex> lk(g_mu);
         g_cache[key] = chosen;
+        append_cache_file(key, chosen);
     }
     *best = chosen;
     return HUFF_OK;

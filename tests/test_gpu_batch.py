@@ -218,3 +218,58 @@ def test_autotune_decompress_and_round_trip_compress():
         assert np.array_equal(dec[i][:x.size].cpu().numpy(), x), i
     tuned.close()
     plan2.close()
+
+
+_TUNE_CHILD = r"""
+import json, sys
+sys.path.insert(0, "tests")
+import numpy as np, torch, synth
+import paper_2306_11070_gb300 as hg
+xs = [synth.text(int(n), 900 + i) for i, n in
+      enumerate(synth.log_uniform_sizes(64, seed=5, lo=4096, hi=1 << 18))]
+ins = [torch.from_numpy(x).cuda() for x in xs]
+outs = [torch.empty(hg.huff_max_stream_size(x.size), dtype=torch.uint8, device="cuda")
+        for x in xs]
+p = hg.BatchPlan(ins, outs, hg.HUFF_BATCH_COMPRESS)
+p.run()
+torch.cuda.synchronize()
+nb = p.out_bytes.cpu().numpy()
+streams = [outs[i][:nb[i]].clone() for i in range(len(xs))]
+dec = [torch.empty(max(x.size, 16), dtype=torch.uint8, device="cuda") for x in xs]
+d = hg.BatchPlan(streams, dec, hg.HUFF_BATCH_DECOMPRESS)
+b = d.autotune()
+print(json.dumps({"decode_lanes": b.decode_lanes, "ctas_per_sm": b.ctas_per_sm}))
+"""
+
+
+def test_autotune_cache_file_round_trip(tmp_path):
+    # a first process tunes and appends a JSON line; a second one, given a
+    # cache file whose entry was edited to other valid parameters, returns
+    # those without tuning: the file is written and read back
+    import json
+    import os
+    import subprocess
+    import sys
+    cache = tmp_path / "tune.jsonl"
+    env = dict(os.environ, HUFF_TUNE_CACHE=str(cache))
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    r1 = subprocess.run([sys.executable, "-c", _TUNE_CHILD], cwd=root, env=env,
+                        capture_output=True, text=True, timeout=600)
+    assert r1.returncode == 0, r1.stderr[-2000:]
+    first = json.loads(r1.stdout.strip().splitlines()[-1])
+    lines = cache.read_text().splitlines()
+    assert len(lines) == 1
+    entry = json.loads(lines[0])  # a valid JSON object
+    assert entry["op"] == hg.HUFF_BATCH_DECOMPRESS
+    assert (entry["decode_lanes"], entry["ctas_per_sm"]) == (first["decode_lanes"],
+                                                             first["ctas_per_sm"])
+    other = 32 if entry["decode_lanes"] != 32 else 64
+    entry["decode_lanes"] = other
+    entry["ctas_per_sm"] = 1
+    cache.write_text(json.dumps(entry) + "\n")
+    r2 = subprocess.run([sys.executable, "-c", _TUNE_CHILD], cwd=root, env=env,
+                        capture_output=True, text=True, timeout=600)
+    assert r2.returncode == 0, r2.stderr[-2000:]
+    second = json.loads(r2.stdout.strip().splitlines()[-1])
+    assert (second["decode_lanes"], second["ctas_per_sm"]) == (other, 1)
+    assert len(cache.read_text().splitlines()) == 1  # served from the file
