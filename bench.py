@@ -38,6 +38,32 @@ REF_SAMPLE = 16 << 20       # bytes per reference-arm step
 CPU_SAMPLE = 256 << 20      # bytes of the CPU-baseline sample
 
 
+# The paper's own compression latencies (Tables I and II: its ~45 MB text
+# corpus on CPU clusters, 4 cores per node, compression only), quoted beside
+# the GPU figures as context; they are not a target (other hardware, other
+# data, undefined I/O inclusion).
+PAPER_CORPUS_MB = 45.0
+PAPER_TIMINGS = [
+    ("Method 1 (sequential)", "Beta", 1, 7.4105),
+    ("Method 1 (sequential)", "Iota", 1, 5.5988),
+    ("Method 2 (MPI+OpenMP)", "Beta", 4, 4.754),
+    ("Method 2 (UPC)", "Iota", 4, 4.671),
+    ("Method 3 (MPI only)", "Beta", 4, 1.219),
+    ("Method 3 (MPI only)", "Iota", 2, 0.732),
+]
+
+
+def paper_context(compress_gbs):
+    rows = [{"method": m, "cluster": c, "nodes": k, "seconds": t,
+             "mb_per_s": round(PAPER_CORPUS_MB / t, 2)} for m, c, k, t in PAPER_TIMINGS]
+    return {"source": "the paper's Tables I-II: compression latency of a ~45 MB text corpus "
+                      "on CPU clusters (4 cores per node); context only, not a target",
+            "rows": rows,
+            "ours_compress_gbs": compress_gbs,
+            "note": "ours: histogram + codebook + encode of the 1 GiB synthetic text on one "
+                    "GB300, inputs resident on the device"}
+
+
 def load_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -669,6 +695,7 @@ def run_ours(args):
         "served": served,
         "method3": method3,
         "cpu_baseline": base,
+        "paper_context": paper_context(n / ((per_k[0] + per_k[1] + per_k[2]) * 1e-3) / 1e9),
     }
     print(json.dumps(line), flush=True)
     if dist is not None:
