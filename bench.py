@@ -385,6 +385,83 @@ def measure_method3(hg, synth, torch, oracle=None, n=256 << 20, block=1 << 20,
     return out
 
 
+def measure_next_rows(hg, synth, torch, oracle=None):
+    """Two next rows of the path on their own workloads: length-limited
+    codebooks (12-bit limit) on the 1 GiB geometric stress input, whose
+    Huffman codes run to ~29 bits, against the unlimited codebook; and
+    per-segment codebooks (Method 2 taken literally) on 256 MiB of text in
+    1 MiB segments, with the oracle's container timed on a 16 MiB sample."""
+    def t_ms(fn, reps=5, warm=2):
+        for _ in range(warm):
+            fn()
+        torch.cuda.synchronize()
+        ts = []
+        for _ in range(reps):
+            s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            s.record()
+            fn()
+            e.record()
+            torch.cuda.synchronize()
+            ts.append(s.elapsed_time(e))
+        return float(statistics.median(ts))
+
+    res = {}
+    x = torch.from_numpy(synth.make("geometric_1g")).cuda()
+    n = x.numel()
+    dev = x.device
+    h = hg.huff_histogram(x)
+    ws = torch.empty(hg.huff_workspace_size(n), dtype=torch.uint8, device=dev)
+    buf = torch.empty(hg.huff_max_stream_size(n), dtype=torch.uint8, device=dev)
+    ob = torch.zeros(1, dtype=torch.int64, device=dev)
+    dn = torch.zeros(1, dtype=torch.int64, device=dev)
+    dec = torch.empty(n, dtype=torch.uint8, device=dev)
+    rows = {}
+    for name, limit in (("huffman", None), ("limited_12", 12)):
+        cb, st = (hg.huff_build_codebook(h) if limit is None
+                  else hg.huff_build_codebook_limited(h, limit))
+
+        def enc(cb=cb, st=st):
+            hg.huff_encode(x, cb, d_out=buf, d_out_bytes=ob, d_ws=ws, d_status=st)
+
+        te = t_ms(enc)
+        enc()
+        torch.cuda.synchronize()
+        nb = int(ob.item())
+        td = t_ms(lambda st=st: hg.huff_decode(buf, nb, d_out=dec, out_cap=n, d_n=dn,
+                                                d_status=st))
+        max_len = int.from_bytes(bytes(cb[1284:1288].cpu().numpy()), "little")
+        rows[name] = {"max_len": max_len, "encode_ms": te, "decode_ms": td,
+                      "stream_ratio": nb / n,
+                      "round_trip_ok": int(st.item()) == 0 and bool(torch.equal(dec, x))}
+    res["length_limited"] = {"workload": "geometric_1g (p = 0.5 over 256 bytes, 1 GiB, seed 41)",
+                             **rows}
+    del x, ws, buf, dec
+    torch.cuda.empty_cache()
+    n2, seg = 256 << 20, 1 << 20
+    x2 = torch.from_numpy(synth.text(n2, 1)).cuda()
+    tc = t_ms(lambda: hg.huff_segmented_compress(x2, seg), reps=3, warm=1)
+    c, st = hg.huff_segmented_compress(x2, seg)
+    td = t_ms(lambda: hg.huff_segmented_decompress(c), reps=3, warm=1)
+    back, m, st2 = hg.huff_segmented_decompress(c)
+    torch.cuda.synchronize()
+    seg_row = {"workload": "synthetic text 256 MiB (seed 1), 1 MiB segments, own codebook each",
+               "compress_ms": tc, "compress_gbs": n2 / tc / 1e6,
+               "decompress_ms": td, "decompress_gbs": n2 / td / 1e6,
+               "ratio": c.numel() / n2,
+               "round_trip_ok": int(st.item()) == 0 and int(st2.item()) == 0 and m == n2
+               and bool(torch.equal(back, x2))}
+    if oracle is not None:
+        sample = x2[:16 << 20].cpu().numpy()
+        t0 = time.perf_counter()
+        oracle.segmented_compress(sample, seg)
+        dt = time.perf_counter() - t0
+        seg_row["cpu_baseline"] = {"kind": "oracle", "cores": 1,
+                                   "sample": "the first 16 MiB, compress only",
+                                   "compress_gbs": sample.size / dt / 1e9}
+    res["segmented"] = seg_row
+    return res
+
+
 def measure_served(hg, synth, oracle, torch, loads=(10.0, 20.0, 50.0, 100.0, 150.0, 200.0),
                    seconds=1.0, max_requests=2000):
     """Config 5: open-loop Poisson arrivals of 50/50 compress/decompress
@@ -632,7 +709,7 @@ def run_ours(args):
     # the host-only oracle runs after every GPU timing of the step, so that
     # nothing it leaves behind on the host shares the timed region
     base = cpu_baseline(x) if (rank == 0 and world == 1 and not args.no_cpu) else None
-    batched = served = method3 = None
+    batched = served = method3 = next_rows = None
     if rank == 0 and not args.no_batched:
         batched = measure_batched(hg, synth, torch)
     if rank == 0 and not args.no_served:
@@ -643,6 +720,7 @@ def run_ours(args):
         if world == 1 and not args.no_cpu:
             import oracle as m3_oracle
         method3 = measure_method3(hg, synth, torch, m3_oracle)
+        next_rows = measure_next_rows(hg, synth, torch, m3_oracle)
 
     if rank != 0:
         if dist is not None:
@@ -694,6 +772,7 @@ def run_ours(args):
         "batched": batched,
         "served": served,
         "method3": method3,
+        "next_rows": next_rows,
         "cpu_baseline": base,
         "paper_context": paper_context(n / ((per_k[0] + per_k[1] + per_k[2]) * 1e-3) / 1e9),
     }
