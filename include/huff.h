@@ -240,7 +240,10 @@ typedef struct huff_batch_desc {
 typedef struct huff_batch_params {
     uint32_t chunk_symbols; /* compress: chunk size of every stream           */
     uint32_t ctas_per_sm;   /* persistent CTAs per SM, 0 = as many as fit     */
-    uint32_t decode_lanes;  /* decompress: lanes to spread a buffer over      */
+    uint32_t decode_lanes;  /* decompress: lanes to spread a buffer over
+                               (1..65536): its chunks are split into the
+                               smallest power of two S <= 32 of sub-segments
+                               with chunks x S >= decode_lanes            */
     uint32_t use_graph;     /* capture the launch in a CUDA graph (1) or not  */
     uint32_t barrier_extra; /* test hook, 0 in use: nonzero makes the launch's
                                grid barriers wait for that many CTAs more than
@@ -287,7 +290,9 @@ huff_status_t huff_batch_info(const huff_batch_plan_t *plan, huff_batch_params_t
  *   and offsets) at start[i], a multiple of 16; start[0] = the header size
  *   rounded up to 16; zero bytes between streams.
  * Both calls run the batched engine (one fused launch) and SYNCHRONIZE the
- * stream: they plan the batch on the host and free the plan afterwards. */
+ * stream: they plan the batch on the host and free the plan afterwards.
+ * Decompression spreads each segment over enough lanes that the whole
+ * container fills about one wave of decoders (256 lanes per SM). */
 uint64_t huff_segmented_max_size(uint64_t n, uint64_t segment_bytes, uint32_t chunk_symbols);
 /* Device scratch of huff_segmented_compress: the streams in worst-case
  * slots, then per-segment sizes and statuses. */

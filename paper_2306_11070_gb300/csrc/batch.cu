@@ -508,7 +508,7 @@ huff_status_t batch_check(const huff_batch_desc_t *descs, uint32_t count, huff_o
         return HUFF_ERR_INVALID_ARG;
     if (op == HUFF_BATCH_COMPRESS && !chunk_symbols_valid(prm.chunk_symbols))
         return HUFF_ERR_INVALID_ARG;
-    if (prm.decode_lanes == 0 || prm.decode_lanes > 1024 || prm.barrier_extra > 65536)
+    if (prm.decode_lanes == 0 || prm.decode_lanes > 65536 || prm.barrier_extra > 65536)
         return HUFF_ERR_INVALID_ARG;
     for (uint32_t i = 0; i < count; ++i) {
         const huff_batch_desc_t &d = descs[i];

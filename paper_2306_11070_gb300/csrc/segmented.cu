@@ -309,6 +309,15 @@ huff_status_t huff_segmented_decompress(const uint8_t *d_in, uint64_t in_bytes, 
     huff_batch_params_t prm;
     huff_batch_default_params(&prm);
     prm.use_graph = 0;
+    // spread each segment over enough lanes that the whole container fills
+    // about one wave of decoders (256 lanes per SM, the single-stream rule)
+    {
+        const uint64_t want = ((uint64_t)device_sm_count() * 256 + count - 1) / count;
+        uint32_t lanes = 32;
+        while (lanes < want && lanes < 65536)
+            lanes <<= 1;
+        prm.decode_lanes = lanes;
+    }
     huff_batch_plan_t *plan = nullptr;
     huff_status_t st = huff_batch_plan(descs.data(), (uint32_t)count, HUFF_BATCH_DECOMPRESS, &prm,
                                        &plan);
