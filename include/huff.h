@@ -420,7 +420,10 @@ typedef struct huff_server_cfg {
     uint32_t max_rounds;     /* rounds in flight at once (default 3, max 16)    */
     uint32_t max_batch;      /* requests per round (default 256)                */
     uint32_t chunk_symbols;  /* chunk size of the streams written (16384)      */
-    uint32_t decode_lanes;   /* lanes to spread a decompress request over (128) */
+    uint32_t decode_lanes;   /* lanes to spread a decompress request over, at
+                                least (128; 1..65536): a round of few
+                                requests spreads each over more, so that
+                                the round fills about one wave of decoders */
 } huff_server_cfg_t;
 
 typedef struct huff_request {

@@ -222,8 +222,15 @@ bool start_round(huff_server_t *S, Round &r, huff_op_t op)
                              take[i]->in_bytes, cudaMemcpyHostToDevice, r.s) == cudaSuccess;
     ok = ok && huff::batch_upload(L, blk, r.h_stage, r.s) == cudaSuccess;
     if (ok) {
-        const huff::BatchArgs args =
-            huff::batch_args(L, blk, S->cfg.chunk_symbols, S->cfg.decode_lanes);
+        // a decompress round of few requests spreads each over more lanes,
+        // so that the round alone fills about one wave of decoders
+        uint32_t lanes = S->cfg.decode_lanes;
+        if (op == HUFF_BATCH_DECOMPRESS) {
+            const uint64_t want = ((uint64_t)huff::device_sm_count() * 256 + count - 1) / count;
+            while (lanes < want && lanes < 65536)
+                lanes <<= 1;
+        }
+        const huff::BatchArgs args = huff::batch_args(L, blk, S->cfg.chunk_symbols, lanes);
         ok = huff::batch_launch(op, args, S->grid, r.s) == cudaSuccess;
     }
     ok = ok && cudaMemcpyAsync(r.h_stage, d_meta, 16ull * count, cudaMemcpyDeviceToHost, r.s) ==
@@ -375,7 +382,7 @@ huff_status_t huff_server_create(const huff_server_cfg_t *cfg, huff_server_t **o
         c = *cfg;
     if (c.device_budget < (1ull << 20) || c.max_rounds == 0 || c.max_rounds > 16 ||
         c.max_batch == 0 || !huff::chunk_symbols_valid(c.chunk_symbols) || c.decode_lanes == 0 ||
-        c.decode_lanes > 1024)
+        c.decode_lanes > 65536)
         return HUFF_ERR_INVALID_ARG;
     huff_server_t *S = new (std::nothrow) huff_server_t();
     if (!S)
