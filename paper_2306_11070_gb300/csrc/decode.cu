@@ -80,7 +80,7 @@ __global__ void __launch_bounds__(kDecBlock) k_decode(DecodeArgs a)
             const uint64_t chunks = n / cs + (n % cs != 0);
             const uint32_t S = pick_split(chunks, a.min_chains);
             const uint64_t tasks = (chunks + (32 / S) - 1) / (32 / S);
-            if ((uint64_t)blockIdx.x * (kDecBlock / 32) >= tasks)
+            if ((uint64_t)blockIdx.x >= tasks)
                 return;
         }
     }
@@ -94,9 +94,10 @@ __global__ void __launch_bounds__(kDecBlock) k_decode(DecodeArgs a)
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     uint32_t *in_col = in_ring + wib * kInRing * 32 + lane;
     uint32_t *out_col = out_ring + wib * kOutRing * 32 + lane;
+    // tasks are dealt to the CTAs in turn (task t to CTA t mod grid), so
+    // when there are fewer tasks than warps every SM still gets its share
     const uint64_t nwarps = (uint64_t)gridDim.x * (kDecBlock / 32);
-    for (uint64_t task = ((uint64_t)blockIdx.x * kDecBlock + threadIdx.x) >> 5; task < tasks;
-         task += nwarps) {
+    for (uint64_t task = (uint64_t)wib * gridDim.x + blockIdx.x; task < tasks; task += nwarps) {
         if (decode_task(si, S, task, in_col, out_col)) {
             if (lane == 0)
                 set_status(a.status, HUFF_ERR_CORRUPT_STREAM);
