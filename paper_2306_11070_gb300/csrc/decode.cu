@@ -30,7 +30,7 @@
 //     every code and the chunk's bit limit.
 // Counting (1) and decoding (4) run in windows of lookups.  A window far
 // from every lane's segment end (32 lookups) runs with no checks and no
-// branch (warp-uniform); the others (16 lookups) check each code.  Per
+// branch (warp-uniform); the others (12 lookups) check each code.  Per
 // lookup the unchecked window does one 4-byte shared-memory load of the table
 // entry, two funnel shifts to drop the bits (entry >> 24 is the shift
 // amount), and appends the entry's symbol bytes to a register word that is
