@@ -32,6 +32,7 @@ sys.path.insert(0, ROOT)
 
 METRIC = "Huffman enc/dec GB/s & % HBM roofline; batched vs plain; served p50/p99 ms"
 WORKLOAD = "text_1g"
+E2E_PASSES = 3  # end-to-end passes of e2e_steps steps; the median is reported
 E2E_SETS = 2  # buffer sets the end-to-end pipeline rotates through (3 or 4: slower, 78-102 GB/s)
 WORKLOAD_DESC = ("synthetic Zipf-word text (50,000-word vocabulary, Zipf(1.0), 5% punctuation, "
                  "newline at 80 chars), 1 GiB, seed 1, 16384-symbol chunks")
@@ -684,25 +685,32 @@ def run_ours(args):
                            d_status=b["st"], stream=s_comp)
             b["ev_d"].record(s_comp)
 
-    barrier()
-    t0 = time.perf_counter()
-    ahead = E2E_SETS - 1  # steps enqueued ahead of the one being copied out
-    for j in range(min(ahead, e2e_steps)):
-        enqueue_in_and_compute(j)
-    for k in range(e2e_steps):
-        if k + ahead < e2e_steps:
-            enqueue_in_and_compute(k + ahead)
-        b = sets[k % E2E_SETS]
-        b["ev_c"].synchronize()  # the caller learns the stream size
-        size = int(b["ob_h"].item())
-        with torch.cuda.stream(s_out):
-            s_out.wait_event(b["ev_c"])
-            b["h_stream"][:size].copy_(b["out"][:size], non_blocking=True)
-            s_out.wait_event(b["ev_d"])
-            b["h_out"].copy_(b["dec"], non_blocking=True)
-            b["ev_done"].record(s_out)
-    torch.cuda.synchronize()
-    e2e_sec = max_over_ranks((time.perf_counter() - t0) / e2e_steps, dist, dev)
+    def e2e_pass():
+        barrier()
+        t0 = time.perf_counter()
+        ahead = E2E_SETS - 1  # steps enqueued ahead of the one being copied out
+        for j in range(min(ahead, e2e_steps)):
+            enqueue_in_and_compute(j)
+        for k in range(e2e_steps):
+            if k + ahead < e2e_steps:
+                enqueue_in_and_compute(k + ahead)
+            b = sets[k % E2E_SETS]
+            b["ev_c"].synchronize()  # the caller learns the stream size
+            size = int(b["ob_h"].item())
+            with torch.cuda.stream(s_out):
+                s_out.wait_event(b["ev_c"])
+                b["h_stream"][:size].copy_(b["out"][:size], non_blocking=True)
+                s_out.wait_event(b["ev_d"])
+                b["h_out"].copy_(b["dec"], non_blocking=True)
+                b["ev_done"].record(s_out)
+        torch.cuda.synchronize()
+        return max_over_ranks((time.perf_counter() - t0) / e2e_steps, dist, dev)
+
+    # the host link is shared with the machine's other GPUs and tenants, so
+    # one pass can land on a busy moment: E2E_PASSES passes, the median kept
+    # and every pass reported
+    e2e_passes = [e2e_pass() for _ in range(E2E_PASSES)]
+    e2e_sec = statistics.median(e2e_passes)
     ok = all(int(b["st"].item()) == 0 for b in sets) and \
         torch.equal(sets[(e2e_steps - 1) % E2E_SETS]["h_out"], h_x)
     del sets
@@ -760,10 +768,12 @@ def run_ours(args):
                    "parallelism": f"replicas x{world}"},
         "clocks": clk,
         "e2e": {"value": job_gbs(world, n, e2e_sec), "unit": "GB/s", "h2d_bytes_per_step": n,
+                "passes_gbs": [job_gbs(world, n, t) for t in e2e_passes],
                 "d2h_bytes_per_step": nbytes + n + 8,
                 "how": f"huff_compress + huff_decode per step from pinned host memory, {E2E_SETS} "
                        "buffer sets, copies in and out on their own streams beside the "
-                       "compute stream; host reads each stream size before copying it"},
+                       "compute stream; host reads each stream size before copying it; "
+                       f"median of {E2E_PASSES} passes of {e2e_steps} steps"},
         "gpu_launches": launches_per_step * args.steps,
         "roofline": {"kernel": names[dom], "bound": "hbm", "achieved": achieved, "peak": peak,
                      "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
