@@ -82,8 +82,10 @@ __global__ void __launch_bounds__(kEncBlock, 1) k_encode(EncodeArgs a)
 
 uint64_t encode_workspace_bytes(uint64_t n)
 {
+    // unit bit counts (u32), unit offsets (u64, + total), the scan's tile sums
     const uint64_t units = (n + kUnitSymbols - 1) / kUnitSymbols;
-    return ((4 * units + 255) & ~255ull) + 8 * (units + 1);
+    return ((4 * units + 255) & ~255ull) + ((8 * (units + 1) + 255) & ~255ull) +
+           8 * unit_scan_tiles(units);
 }
 
 cudaError_t launch_encode(const uint8_t *d_in, uint64_t n, const huff_codebook_t *d_cb, uint32_t cs,
@@ -110,7 +112,10 @@ cudaError_t launch_encode(const uint8_t *d_in, uint64_t n, const huff_codebook_t
     uint32_t *unit_bits = reinterpret_cast<uint32_t *>(ws);
     unsigned long long *unit_off =
         reinterpret_cast<unsigned long long *>(ws + ((4 * units + 255) & ~255ull));
-    err = launch_unit_offsets(d_in, n, d_unit_hist, d_cb, unit_bits, unit_off, d_status, s);
+    unsigned long long *tile_sum = reinterpret_cast<unsigned long long *>(
+        ws + ((4 * units + 255) & ~255ull) + ((8 * (units + 1) + 255) & ~255ull));
+    err = launch_unit_offsets(d_in, n, d_unit_hist, d_cb, unit_bits, unit_off, tile_sum, d_status,
+                              s);
     if (err != cudaSuccess)
         return err;
     EncodeArgs a;

@@ -199,9 +199,13 @@ cudaError_t launch_histogram(const uint8_t *d_in, uint64_t n, unsigned long long
 // at most `limit` bits (package-merge where the Huffman code exceeds it)
 cudaError_t launch_build_codebook(const unsigned long long *d_hist, huff_codebook_t *d_cb,
                                   int32_t *d_status, cudaStream_t s, uint32_t limit = 0);
+// d_tile_sum: unit_scan_tiles(units) u64 of scratch
 cudaError_t launch_unit_offsets(const uint8_t *d_in, uint64_t n, const uint16_t *d_unit_hist,
                                 const huff_codebook_t *d_cb, uint32_t *d_unit_bits,
-                                unsigned long long *d_unit_off, int32_t *d_status, cudaStream_t s);
+                                unsigned long long *d_unit_off, unsigned long long *d_tile_sum,
+                                int32_t *d_status, cudaStream_t s);
+// tiles of the unit offset scan (2048 units each)
+__host__ __device__ constexpr uint64_t unit_scan_tiles(uint64_t units) { return (units + 2047) / 2048; }
 cudaError_t launch_encode(const uint8_t *d_in, uint64_t n, const huff_codebook_t *d_cb,
                           uint32_t cs, uint8_t *d_out, uint64_t out_cap,
                           unsigned long long *d_out_bytes, void *d_ws,

@@ -25,8 +25,11 @@ namespace {
 
 constexpr uint64_t kMaxSymbols = HUFF_NOALLOC_MAX_SYMBOLS;
 constexpr uint64_t kMaxUnits = (kMaxSymbols + huff::kUnitSymbols - 1) / huff::kUnitSymbols;
-// unit bit counts (u32, padded to 256 bytes) then unit offsets (u64, + total)
-constexpr uint64_t kScratchBytes = ((4 * kMaxUnits + 255) & ~255ull) + 8 * (kMaxUnits + 1);
+// unit bit counts (u32, padded to 256 bytes), unit offsets (u64, + total,
+// padded), the unit scan's tile sums: the encoder's workspace layout
+constexpr uint64_t kScratchBytes = ((4 * kMaxUnits + 255) & ~255ull) +
+                                   ((8 * (kMaxUnits + 1) + 255) & ~255ull) +
+                                   8 * huff::unit_scan_tiles(kMaxUnits);
 
 static __device__ __align__(256) unsigned char g_encode_scratch[kScratchBytes];
 

@@ -11,8 +11,8 @@
 //  - k_unit_bits_input: without those histograms, the same count straight
 //    from the input (one HBM read of the input, per-lane replicated length
 //    table in shared memory);
-//  - k_scan_units: one CTA turns the counts into exclusive prefixes
-//    (u64 per unit, plus the total at index `units`).
+//  - k_scan_tile_sums + k_scan_apply: the counts become exclusive
+//    prefixes (u64 per unit, plus the total at index `units`).
 #include "huff_internal.cuh"
 
 namespace huff {
@@ -20,8 +20,6 @@ namespace {
 
 constexpr int kDotBlock = 256;
 constexpr int kCountBlock = 256;
-constexpr int kScanBlock = 512;
-constexpr int kScanPer = 32;  // counts per thread and tile
 
 __global__ void __launch_bounds__(kDotBlock)
     k_unit_bits_hist(const uint16_t *__restrict__ unit_hist, uint64_t units,
@@ -104,97 +102,136 @@ __global__ void __launch_bounds__(kCountBlock)
     }
 }
 
-// One CTA scans the unit counts in tiles of kScanBlock * kScanPer units:
-// each thread loads its kScanPer consecutive counts with 16-byte loads that
-// are all in flight at once, so a tile costs one memory round trip (1 GiB of
-// input is 4 tiles), then a block scan of the thread totals and a carry
-// across tiles.
-__global__ void __launch_bounds__(kScanBlock)
-    k_scan_units(const uint32_t *__restrict__ unit_bits, uint64_t units,
-                 unsigned long long *__restrict__ unit_off, const int32_t *status)
+// The exclusive scan of the unit counts in two launches over tiles of
+// kScanTile units (one CTA per tile, each thread kScanPer consecutive counts
+// loaded with 16-byte loads that are all in flight at once):
+//  - k_scan_tile_sums: every tile's total;
+//  - k_scan_apply: every tile adds up the totals of the tiles before it (a
+//    few dozen at 1 GiB), scans its own counts and writes the u64 offsets;
+//    the last tile also writes the grand total at index `units`.
+constexpr int kScanThreads = 256;
+constexpr int kScanPer = 8;
+constexpr uint32_t kScanTile = kScanThreads * kScanPer;  // 2048 units
+
+__device__ __forceinline__ void load_counts(const uint32_t *unit_bits, uint64_t units, uint64_t i,
+                                            uint32_t (&v)[kScanPer])
 {
-    __shared__ unsigned long long s_warp[kScanBlock / 32];
-    __shared__ unsigned long long s_total;
-    if (chain_failed(status))
-        return;
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    unsigned long long carry = 0;
-    for (uint64_t t0 = 0; t0 < units; t0 += (uint64_t)kScanBlock * kScanPer) {
-        const uint64_t i = t0 + (uint64_t)kScanPer * tid;
-        uint32_t v[kScanPer];
-        if (i + kScanPer <= units) {  // i is a multiple of 32: 16-byte aligned
-            const uint4 *q = reinterpret_cast<const uint4 *>(unit_bits + i);
-#pragma unroll
-            for (int j = 0; j < kScanPer / 4; ++j) {
-                const uint4 x = q[j];
-                v[4 * j] = x.x;
-                v[4 * j + 1] = x.y;
-                v[4 * j + 2] = x.z;
-                v[4 * j + 3] = x.w;
-            }
-        } else {
-#pragma unroll
-            for (int j = 0; j < kScanPer; ++j)
-                v[j] = i + j < units ? unit_bits[i + j] : 0u;
-        }
-        unsigned long long own = 0;
+    if (i + kScanPer <= units) {  // i is a multiple of 8: 16-byte aligned
+        const uint4 *q = reinterpret_cast<const uint4 *>(unit_bits + i);
+        const uint4 x0 = q[0], x1 = q[1];
+        v[0] = x0.x, v[1] = x0.y, v[2] = x0.z, v[3] = x0.w;
+        v[4] = x1.x, v[5] = x1.y, v[6] = x1.z, v[7] = x1.w;
+    } else {
 #pragma unroll
         for (int j = 0; j < kScanPer; ++j)
-            own += v[j];
-        unsigned long long x = own;
-#pragma unroll
-        for (int d = 1; d < 32; d <<= 1) {
-            const unsigned long long y = __shfl_up_sync(0xffffffffu, x, d);
-            if (lane >= d)
-                x += y;
-        }
-        if (lane == 31)
-            s_warp[warp] = x;
-        __syncthreads();
-        if (warp == 0) {
-            const unsigned long long w = lane < kScanBlock / 32 ? s_warp[lane] : 0ull;
-            unsigned long long z = w;
-#pragma unroll
-            for (int d = 1; d < 32; d <<= 1) {
-                const unsigned long long y = __shfl_up_sync(0xffffffffu, z, d);
-                if (lane >= d)
-                    z += y;
-            }
-            if (lane < kScanBlock / 32)
-                s_warp[lane] = z - w;
-            if (lane == 31)
-                s_total = z;  // the tile total
-        }
-        __syncthreads();
-        unsigned long long run = carry + s_warp[warp] + x - own;
-        if (i + kScanPer <= units) {
-#pragma unroll
-            for (int j = 0; j < kScanPer; j += 2) {
-                const unsigned long long a = run;
-                run += v[j];
-                reinterpret_cast<ulonglong2 *>(unit_off + i)[j / 2] = make_ulonglong2(a, run);
-                run += v[j + 1];
-            }
-        } else {
-#pragma unroll
-            for (int j = 0; j < kScanPer; ++j) {
-                if (i + j < units)
-                    unit_off[i + j] = run;
-                run += v[j];
-            }
-        }
-        carry += s_total;
-        __syncthreads();
+            v[j] = i + j < units ? unit_bits[i + j] : 0u;
     }
-    if (tid == 0)
-        unit_off[units] = carry;
+}
+
+// block-wide exclusive scan of one u64 per thread; *total the sum
+__device__ __forceinline__ unsigned long long block_scan_u64(unsigned long long own,
+                                                             unsigned long long *s_warp,
+                                                             unsigned long long &total)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    unsigned long long x = own;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const unsigned long long y = __shfl_up_sync(0xffffffffu, x, d);
+        if (lane >= d)
+            x += y;
+    }
+    if (lane == 31)
+        s_warp[warp] = x;
+    __syncthreads();
+    unsigned long long before = 0, all = 0;
+#pragma unroll
+    for (int w = 0; w < kScanThreads / 32; ++w) {
+        const unsigned long long t = s_warp[w];
+        before += w < warp ? t : 0ull;
+        all += t;
+    }
+    total = all;
+    return before + x - own;
+}
+
+__global__ void __launch_bounds__(kScanThreads)
+    k_scan_tile_sums(const uint32_t *__restrict__ unit_bits, uint64_t units,
+                     unsigned long long *__restrict__ tile_sum, const int32_t *status)
+{
+    __shared__ unsigned long long s_warp[kScanThreads / 32];
+    if (chain_failed(status))
+        return;
+    uint32_t v[kScanPer];
+    load_counts(unit_bits, units, (uint64_t)blockIdx.x * kScanTile + (uint64_t)kScanPer * threadIdx.x,
+                v);
+    unsigned long long own = 0;
+#pragma unroll
+    for (int j = 0; j < kScanPer; ++j)
+        own += v[j];
+    unsigned long long total;
+    block_scan_u64(own, s_warp, total);
+    if (threadIdx.x == 0)
+        tile_sum[blockIdx.x] = total;
+}
+
+__global__ void __launch_bounds__(kScanThreads)
+    k_scan_apply(const uint32_t *__restrict__ unit_bits, uint64_t units,
+                 const unsigned long long *__restrict__ tile_sum,
+                 unsigned long long *__restrict__ unit_off, const int32_t *status)
+{
+    __shared__ unsigned long long s_warp[kScanThreads / 32];
+    __shared__ unsigned long long s_base;
+    if (chain_failed(status))
+        return;
+    // the totals of the tiles before this one
+    unsigned long long b = 0;
+    for (uint32_t t = threadIdx.x; t < blockIdx.x; t += kScanThreads)
+        b += tile_sum[t];
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1)
+        b += __shfl_xor_sync(0xffffffffu, b, d);
+    if (threadIdx.x == 0)
+        s_base = 0;
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0 && b)
+        atomicAdd(&s_base, b);
+    const uint64_t i = (uint64_t)blockIdx.x * kScanTile + (uint64_t)kScanPer * threadIdx.x;
+    uint32_t v[kScanPer];
+    load_counts(unit_bits, units, i, v);
+    unsigned long long own = 0;
+#pragma unroll
+    for (int j = 0; j < kScanPer; ++j)
+        own += v[j];
+    unsigned long long total;
+    const unsigned long long x = block_scan_u64(own, s_warp, total);  // has a barrier
+    unsigned long long run = s_base + x;
+    if (i + kScanPer <= units) {
+#pragma unroll
+        for (int j = 0; j < kScanPer; j += 2) {
+            const unsigned long long a = run;
+            run += v[j];
+            reinterpret_cast<ulonglong2 *>(unit_off + i)[j / 2] = make_ulonglong2(a, run);
+            run += v[j + 1];
+        }
+    } else {
+#pragma unroll
+        for (int j = 0; j < kScanPer; ++j) {
+            if (i + j < units)
+                unit_off[i + j] = run;
+            run += v[j];
+        }
+    }
+    if (blockIdx.x == gridDim.x - 1 && threadIdx.x == 0)
+        unit_off[units] = s_base + total;
 }
 
 }  // namespace
 
 cudaError_t launch_unit_offsets(const uint8_t *d_in, uint64_t n, const uint16_t *d_unit_hist,
                                 const huff_codebook_t *d_cb, uint32_t *d_unit_bits,
-                                unsigned long long *d_unit_off, int32_t *d_status, cudaStream_t s)
+                                unsigned long long *d_unit_off, unsigned long long *d_tile_sum,
+                                int32_t *d_status, cudaStream_t s)
 {
     const uint64_t units = (n + kUnitSymbols - 1) / kUnitSymbols;
     if (units == 0)
@@ -223,7 +260,11 @@ cudaError_t launch_unit_offsets(const uint8_t *d_in, uint64_t n, const uint16_t 
     cudaError_t err = cudaGetLastError();
     if (err != cudaSuccess)
         return err;
-    k_scan_units<<<1, kScanBlock, 0, s>>>(d_unit_bits, units, d_unit_off, d_status);
+    static_assert(kScanTile == 2048, "unit_scan_tiles assumes 2048-unit tiles");
+    const uint32_t tiles = (uint32_t)unit_scan_tiles(units);
+    k_scan_tile_sums<<<tiles, kScanThreads, 0, s>>>(d_unit_bits, units, d_tile_sum, d_status);
+    k_scan_apply<<<tiles, kScanThreads, 0, s>>>(d_unit_bits, units, d_tile_sum, d_unit_off,
+                                                d_status);
     return cudaGetLastError();
 }
 
