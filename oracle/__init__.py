@@ -75,6 +75,10 @@ def _configure(lib):
     lib.oracle_bwt.argtypes = [u8p, u64, u32, u8p, u32p]
     lib.oracle_ibwt.restype = ctypes.c_int
     lib.oracle_ibwt.argtypes = [u8p, u64, u32, u32p, u8p]
+    lib.oracle_mtf.restype = ctypes.c_int
+    lib.oracle_mtf.argtypes = [u8p, u64, u32, u8p]
+    lib.oracle_imtf.restype = ctypes.c_int
+    lib.oracle_imtf.argtypes = [u8p, u64, u32, u8p]
     return lib
 
 
@@ -310,12 +314,34 @@ def ibwt(L, block: int, primary):
     return out
 
 
+def mtf(x, block: int):
+    """Move-to-front coding of every `block`-byte block (list 0..255 at each
+    block start)."""
+    a = _bytes(x)
+    out = np.zeros(a.size, dtype=np.uint8)
+    st = _load().oracle_mtf(_p(a, ctypes.c_uint8), a.size, block, _p(out, ctypes.c_uint8))
+    if st != OK:
+        raise ValueError(f"oracle_mtf status {st}")
+    return out
+
+
+def imtf(idx, block: int):
+    """Inverse of :func:`mtf`."""
+    a = _bytes(idx)
+    out = np.zeros(a.size, dtype=np.uint8)
+    st = _load().oracle_imtf(_p(a, ctypes.c_uint8), a.size, block, _p(out, ctypes.c_uint8))
+    if st != OK:
+        raise ValueError(f"oracle_imtf status {st}")
+    return out
+
+
 # ---------------------------------------------------------------- Method 3 container
-def m3_compress(x, block: int, segment_bytes: int, cs: int = DEFAULT_CHUNK):
+def m3_compress(x, block: int, segment_bytes: int, cs: int = DEFAULT_CHUNK, mtf_stage: bool = False):
     """(status, container bytes): Method 3 (Section III-A) -- the
-    block-sorting transform of every `block`-byte block, then Method 2's
-    segmented coder (one codebook per segment) over the transformed bytes.
-    Layout (include/huff.h): n (u64), block (u32), count (u32), one u32
+    block-sorting transform of every `block`-byte block, optionally
+    move-to-front coding of every block, then Method 2's segmented coder (one
+    codebook per segment) over the result.  Layout (include/huff.h): n (u64),
+    block (u32), count (u32), stages (u32: bit 0 = move-to-front), one u32
     primary index per block, zero bytes up to a multiple of 16, then the
     segmented container."""
     a = _bytes(x)
@@ -324,39 +350,46 @@ def m3_compress(x, block: int, segment_bytes: int, cs: int = DEFAULT_CHUNK):
     if block < 1 or block >= 1 << 32:
         return ERR_INVALID_ARG, empty
     L, prim = bwt(a, block)
+    if mtf_stage:
+        L = mtf(L, block)
     st, seg = segmented_compress(L, segment_bytes, cs)
     if st != OK:
         return st, empty
     count = prim.size
-    head = _al16(16 + 4 * count)
+    head = _al16(20 + 4 * count)
     out = np.zeros(head + seg.size, dtype=np.uint8)
     out[0:8] = np.frombuffer(np.array([n], dtype="<u8").tobytes(), np.uint8)
-    out[8:16] = np.frombuffer(np.array([block, count], dtype="<u4").tobytes(), np.uint8)
-    out[16:16 + 4 * count] = np.frombuffer(prim.astype("<u4").tobytes(), np.uint8)
+    out[8:20] = np.frombuffer(np.array([block, count, 1 if mtf_stage else 0], dtype="<u4")
+                              .tobytes(), np.uint8)
+    out[20:20 + 4 * count] = np.frombuffer(prim.astype("<u4").tobytes(), np.uint8)
     out[head:] = seg
     return OK, out
 
 
 def m3_decompress(c, cap: int | None = None):
-    """(status, bytes, n): validate the header, decode the segmented
-    container, check it holds n bytes and every primary index lies inside
-    its block, then invert the transform."""
+    """(status, bytes, n): validate the header (stages other than bit 0 are
+    corrupt), decode the segmented container, check it holds n bytes and
+    every primary index lies inside its block, undo move-to-front if it was
+    applied, then invert the transform."""
     c = _bytes(c)
     empty = np.zeros(0, dtype=np.uint8)
-    if c.size < 16:
+    if c.size < 20:
         return ERR_CORRUPT, empty, 0
     n = int(np.frombuffer(c[0:8].tobytes(), "<u8")[0])
-    block, count = (int(v) for v in np.frombuffer(c[8:16].tobytes(), "<u4"))
-    if block < 1 or count != (n + block - 1) // block or 16 + 4 * count > c.size:
+    block, count, stages = (int(v) for v in np.frombuffer(c[8:20].tobytes(), "<u4"))
+    if block < 1 or count != (n + block - 1) // block or stages > 1 or \
+            20 + 4 * count > c.size:
         return ERR_CORRUPT, empty, 0
     if cap is not None and n > cap:
         return ERR_CAPACITY, empty, n
-    prim = np.frombuffer(c[16:16 + 4 * count].tobytes(), "<u4").astype(np.uint32)
+    prim = np.frombuffer(c[20:20 + 4 * count].tobytes(), "<u4").astype(np.uint32)
     for i in range(count):
         if int(prim[i]) >= min(block, n - i * block):
             return ERR_CORRUPT, empty, n
-    head = _al16(16 + 4 * count)
+    head = _al16(20 + 4 * count)
     st, L, m = segmented_decompress(c[head:], cap=n)
     if st != OK or m != n:
         return ERR_CORRUPT, empty, n
+    if stages & 1:
+        L = imtf(L, block)
     return OK, ibwt(L, block, prim), n

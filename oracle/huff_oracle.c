@@ -24,6 +24,8 @@
  *   6. Method 3 first applies the block-sorting (Burrows-Wheeler) transform
  *      to every block, and its inverse after decoding.
  *                                                 oracle_bwt / oracle_ibwt
+ *      Optionally followed by move-to-front coding per block.
+ *                                               oracle_mtf / oracle_imtf
  *
  * Readings of points the paper leaves open:
  *   R1 tie-break: nodes are ordered by (weight, id); leaf id = byte value,
@@ -657,5 +659,54 @@ int oracle_ibwt(const uint8_t *L, uint64_t n, uint32_t block, const uint32_t *pr
         }
     }
     free(lf);
+    return ORACLE_OK;
+}
+
+/* Move-to-front coding of each block (the stage that usually follows the
+ * block-sorting transform: Burrows and Wheeler, 1994, Section 4): a list of
+ * the 256 byte values, in increasing order at the start of every block; each
+ * byte is coded as its current position in the list and then moved to the
+ * front.  Runs of equal bytes become runs of zeros. */
+int oracle_mtf(const uint8_t *x, uint64_t n, uint32_t block, uint8_t *out)
+{
+    if (n == 0)
+        return ORACLE_OK;
+    if (block == 0)
+        return ORACLE_ERR_INVALID_ARG;
+    uint8_t list[256];
+    for (uint64_t i = 0; i < n; ++i) {
+        if (i % block == 0)
+            for (int v = 0; v < 256; ++v)
+                list[v] = (uint8_t)v;
+        const uint8_t c = x[i];
+        int j = 0;
+        while (list[j] != c)
+            ++j;
+        out[i] = (uint8_t)j;
+        for (; j > 0; --j)
+            list[j] = list[j - 1];
+        list[0] = c;
+    }
+    return ORACLE_OK;
+}
+
+int oracle_imtf(const uint8_t *idx, uint64_t n, uint32_t block, uint8_t *out)
+{
+    if (n == 0)
+        return ORACLE_OK;
+    if (block == 0)
+        return ORACLE_ERR_INVALID_ARG;
+    uint8_t list[256];
+    for (uint64_t i = 0; i < n; ++i) {
+        if (i % block == 0)
+            for (int v = 0; v < 256; ++v)
+                list[v] = (uint8_t)v;
+        int j = idx[i];
+        const uint8_t c = list[j];
+        out[i] = c;
+        for (; j > 0; --j)
+            list[j] = list[j - 1];
+        list[0] = c;
+    }
     return ORACLE_OK;
 }

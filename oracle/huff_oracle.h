@@ -37,4 +37,7 @@ int oracle_decode(const uint8_t *s, uint64_t bytes, uint8_t *out, uint64_t cap,
 int oracle_bwt(const uint8_t *x, uint64_t n, uint32_t block, uint8_t *L, uint32_t *primary);
 int oracle_ibwt(const uint8_t *L, uint64_t n, uint32_t block, const uint32_t *primary,
                 uint8_t *out);
+/* Method 3's optional second stage: move-to-front coding per block */
+int oracle_mtf(const uint8_t *x, uint64_t n, uint32_t block, uint8_t *out);
+int oracle_imtf(const uint8_t *idx, uint64_t n, uint32_t block, uint8_t *out);
 #endif

@@ -114,19 +114,67 @@ def test_empty_and_bad_arguments():
         oracle.ibwt(u8(b"abc"), 3, np.array([3], dtype=np.uint32))
 
 
-@pytest.mark.parametrize("n,block,seg", [(0, 16, 16), (1, 1, 16), (5000, 1000, 2048),
-                                         (70000, 65536, 16384)])
-def test_m3_container_round_trip(n, block, seg):
+def brute_mtf(x: bytes, block: int):
+    """Move-to-front with a Python list, the definition written out."""
+    out = []
+    for s in range(0, len(x), block):
+        lst = list(range(256))
+        for c in x[s:s + block]:
+            j = lst.index(c)
+            out.append(j)
+            lst.insert(0, lst.pop(j))
+    return bytes(out)
+
+
+def test_mtf_hand_example():
+    # Worked by hand, list 0..255 at the start: b (98) sits at 98; then a
+    # (97) is at 98 (b moved in front of it); n (110) at 110 (b and a in
+    # front, 0..96 and 99..109 before it); then a, n, a at 1 each; a, a at 0
+    x = np.frombuffer(b"bananaaa", np.uint8)
+    assert list(oracle.mtf(x, 8)) == [98, 98, 110, 1, 1, 1, 0, 0]
+    assert bytes(oracle.imtf(oracle.mtf(x, 8), 8)) == b"bananaaa"
+
+
+def test_mtf_bruteforce_and_round_trip():
+    rng = np.random.default_rng(3)
+    for n in (1, 2, 7, 300, 1000):
+        for alpha in (2, 5, 256):
+            x = bytes(rng.integers(0, alpha, n, dtype=np.uint8))
+            for block in (1, 3, 64, n):
+                m = oracle.mtf(np.frombuffer(x, np.uint8), block)
+                assert bytes(m) == brute_mtf(x, block), (n, alpha, block)
+                assert bytes(oracle.imtf(m, block)) == x
+
+
+def test_mtf_after_transform_is_mostly_small():
+    # runs of equal bytes become zeros: far more of them after the transform
+    # than when the text itself is coded
+    x = synth.text(1 << 16, 12)
+    L, _ = oracle.bwt(x, 1 << 16)
+    m = oracle.mtf(L, 1 << 16)
+    raw = oracle.mtf(x, 1 << 16)
+    assert np.count_nonzero(m == 0) > 3 * np.count_nonzero(raw == 0)
+    assert np.count_nonzero(m < 4) > 0.5 * m.size
+
+
+@pytest.mark.parametrize("n,block,seg,use_mtf", [(0, 16, 16, False), (1, 1, 16, True),
+                                                 (5000, 1000, 2048, False),
+                                                 (5000, 1000, 2048, True),
+                                                 (70000, 65536, 16384, True)])
+def test_m3_container_round_trip(n, block, seg, use_mtf):
     x = synth.text(n, 9)
-    st, c = oracle.m3_compress(x, block, seg)
+    st, c = oracle.m3_compress(x, block, seg, mtf_stage=use_mtf)
     assert st == oracle.OK
     count = (n + block - 1) // block
     assert int(np.frombuffer(c[0:8].tobytes(), "<u8")[0]) == n
-    assert [int(v) for v in np.frombuffer(c[8:16].tobytes(), "<u4")] == [block, count]
-    head = (16 + 4 * count + 15) & ~15
-    assert not c[16 + 4 * count:head].any()
+    assert [int(v) for v in np.frombuffer(c[8:20].tobytes(), "<u4")] == [block, count,
+                                                                         int(use_mtf)]
+    head = (20 + 4 * count + 15) & ~15
+    assert not c[20 + 4 * count:head].any()
     L, prim = oracle.bwt(x, block)
-    assert np.array_equal(np.frombuffer(c[16:16 + 4 * count].tobytes(), "<u4"), prim)
+    assert np.array_equal(np.frombuffer(c[20:20 + 4 * count].tobytes(), "<u4"), prim)
+    if use_mtf:
+        L = oracle.mtf(L, block)
     st2, seg_c = oracle.segmented_compress(L, seg)
     assert np.array_equal(c[head:], seg_c)
     st, y, m = oracle.m3_decompress(c)
@@ -137,10 +185,13 @@ def test_m3_corrupt_containers():
     x = synth.text(3000, 2)
     st, c = oracle.m3_compress(x, 1000, 1024)
     bad = c.copy()
-    bad[16:20] = np.frombuffer(np.array([1000], dtype="<u4").tobytes(), np.uint8)  # primary = block
+    bad[20:24] = np.frombuffer(np.array([1000], dtype="<u4").tobytes(), np.uint8)  # primary = block
     assert oracle.m3_decompress(bad)[0] == oracle.ERR_CORRUPT
     bad = c.copy()
     bad[12] ^= 1  # block count
     assert oracle.m3_decompress(bad)[0] == oracle.ERR_CORRUPT
-    assert oracle.m3_decompress(c[:15])[0] == oracle.ERR_CORRUPT
+    bad = c.copy()
+    bad[16] = 2  # unknown stage
+    assert oracle.m3_decompress(bad)[0] == oracle.ERR_CORRUPT
+    assert oracle.m3_decompress(c[:19])[0] == oracle.ERR_CORRUPT
     assert oracle.m3_decompress(c, cap=2999)[0] == oracle.ERR_CAPACITY

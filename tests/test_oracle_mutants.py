@@ -51,6 +51,11 @@ MUTANTS = [
      "for (uint32_t t = 0; t < m / 2 + 1; ++t) {\n        uint8_t u"),
     ("ibwt_writes_forwards", "out[c * block + (m - 1 - t)] = l[p];", "out[c * block + t] = l[p];"),
     ("ibwt_starts_next_row", "uint32_t p = primary[c];", "uint32_t p = (primary[c] + 1) % m;"),
+    ("mtf_index_plus_one", "out[i] = (uint8_t)j;", "out[i] = (uint8_t)(j + (j > 0 && j < 255));"),
+    ("mtf_list_kept_across_blocks",
+     "        if (i % block == 0)\n            for (int v = 0; v < 256; ++v)\n                list[v] = (uint8_t)v;\n        const uint8_t c = x[i];",
+     "        if (i == 0)\n            for (int v = 0; v < 256; ++v)\n                list[v] = (uint8_t)v;\n        const uint8_t c = x[i];"),
+    ("imtf_moves_to_second", "        out[i] = c;\n        for (; j > 0; --j)", "        out[i] = c;\n        for (; j > 1; --j)"),
 ]
 # Not listed: skipping the Huffman shortcut of the length-limited lengths
 # when the limit equals the Huffman maximum gave the same lengths on every
@@ -98,6 +103,8 @@ def _pins():
         bwt_pins.test_empty_and_bad_arguments,
         lambda: bwt_pins.test_inverse_round_trip("text", 256),
         bwt_pins.test_bruteforce_tiny_inputs,
+        bwt_pins.test_mtf_hand_example,
+        bwt_pins.test_mtf_bruteforce_and_round_trip,
     ]
     out += [lambda c=c: pins.test_round_trip(c) for c in pins._inputs()]
     out.append(pins.test_bruteforce_minimum_weighted_length)
