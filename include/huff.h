@@ -344,11 +344,25 @@ huff_status_t huff_bwt_forward(const uint8_t *d_in, uint64_t n, uint32_t block, 
 huff_status_t huff_bwt_inverse(const uint8_t *d_last, uint64_t n, uint32_t block,
                                const uint32_t *d_primary, uint8_t *d_out, void *d_ws,
                                uint64_t ws_bytes, int32_t *d_status, huff_stream_t stream);
+/* Move-to-front coding per block (Method 3's optional second stage; Burrows
+ * and Wheeler 1994, Section 4): every block of `block` bytes starts from the
+ * list 0..255; each byte is coded as its position in the list and moved to
+ * the front; the inverse decodes.  Asynchronous on the stream; d_in / d_out
+ * n bytes (they may be the same buffer); workspace huff_mtf_workspace_size
+ * bytes, 16-byte aligned (about n / 8 + n).  Host errors only:
+ * HUFF_ERR_INVALID_ARG, HUFF_ERR_CUDA. */
+uint64_t huff_mtf_workspace_size(uint64_t n, uint32_t block);
+huff_status_t huff_mtf_forward(const uint8_t *d_in, uint64_t n, uint32_t block, uint8_t *d_out,
+                               void *d_ws, uint64_t ws_bytes, huff_stream_t stream);
+huff_status_t huff_mtf_inverse(const uint8_t *d_in, uint64_t n, uint32_t block, uint8_t *d_out,
+                               void *d_ws, uint64_t ws_bytes, huff_stream_t stream);
 /* Method 3 container (all integers LE):
  *   [0, 8) n; [8, 12) block; [12, 16) count = ceil(n / block);
- *   [16, 16 + 4 count) primary index of every block; zero bytes up to a
- *   multiple of 16; then the segmented container (above) of the
- *   transformed bytes, with its own segment size and chunk size.
+ *   [16, 20) stages: bit 0 set = move-to-front after the transform (other
+ *   bits zero); [20, 20 + 4 count) primary index of every block; zero bytes
+ *   up to a multiple of 16; then the segmented container (above) of the
+ *   transformed (and move-to-front coded) bytes, with its own segment size
+ *   and chunk size.
  * huff_m3_compress: *d_out_bytes receives the container size; workspace
  * huff_m3_workspace_size (16-byte aligned, d_out too).  huff_m3_decompress
  * reads the header on the host, decodes the segments into the workspace
@@ -361,10 +375,12 @@ uint64_t huff_m3_max_size(uint64_t n, uint32_t block, uint64_t segment_bytes,
                           uint32_t chunk_symbols);
 uint64_t huff_m3_workspace_size(uint64_t n, uint32_t block, uint64_t segment_bytes,
                                 uint32_t chunk_symbols);
+#define HUFF_M3_MTF 1u /* stages: move-to-front after the transform */
 huff_status_t huff_m3_compress(const uint8_t *d_in, uint64_t n, uint32_t block,
-                               uint64_t segment_bytes, uint32_t chunk_symbols, uint8_t *d_out,
-                               uint64_t out_cap, uint64_t *d_out_bytes, void *d_ws,
-                               uint64_t ws_bytes, int32_t *d_status, huff_stream_t stream);
+                               uint64_t segment_bytes, uint32_t chunk_symbols, uint32_t stages,
+                               uint8_t *d_out, uint64_t out_cap, uint64_t *d_out_bytes,
+                               void *d_ws, uint64_t ws_bytes, int32_t *d_status,
+                               huff_stream_t stream);
 uint64_t huff_m3_decompress_workspace_size(uint64_t n, uint32_t block);
 huff_status_t huff_m3_decompress(const uint8_t *d_in, uint64_t in_bytes, uint8_t *d_out,
                                  uint64_t out_cap, uint64_t *d_n, void *d_ws, uint64_t ws_bytes,

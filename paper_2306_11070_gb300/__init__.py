@@ -165,7 +165,13 @@ def lib() -> ctypes.CDLL:
         L.huff_m3_workspace_size.restype = u64
         L.huff_m3_workspace_size.argtypes = [u64, u32, u64, u32]
         L.huff_m3_compress.restype = i32
-        L.huff_m3_compress.argtypes = [vp, u64, u32, u64, u32, vp, u64, vp, vp, u64, vp, vp]
+        L.huff_m3_compress.argtypes = [vp, u64, u32, u64, u32, u32, vp, u64, vp, vp, u64, vp, vp]
+        L.huff_mtf_workspace_size.restype = u64
+        L.huff_mtf_workspace_size.argtypes = [u64, u32]
+        L.huff_mtf_forward.restype = i32
+        L.huff_mtf_forward.argtypes = [vp, u64, u32, vp, vp, u64, vp]
+        L.huff_mtf_inverse.restype = i32
+        L.huff_mtf_inverse.argtypes = [vp, u64, u32, vp, vp, u64, vp]
         L.huff_m3_decompress_workspace_size.restype = u64
         L.huff_m3_decompress_workspace_size.argtypes = [u64, u32]
         L.huff_m3_decompress.restype = i32
@@ -557,10 +563,39 @@ def huff_bwt_inverse(d_last: torch.Tensor, block: int, d_primary: torch.Tensor, 
     return d_out[:n], st
 
 
+def _mtf_call(fn, name, d_in, block, d_out, ws, stream):
+    x = _u8(d_in)
+    n = x.numel()
+    dev = x.device
+    if d_out is None:
+        d_out = torch.empty(max(n, 1), dtype=torch.uint8, device=dev)
+    wsb = lib().huff_mtf_workspace_size(n, block)
+    if wsb == 0:
+        raise HuffError(HUFF_ERR_INVALID_ARG, name)
+    if ws is None or ws.numel() < wsb:
+        ws = torch.empty(wsb, dtype=torch.uint8, device=dev)
+    _check(fn(_ptr(x) if n else None, n, block, _ptr(d_out), _ptr(ws), wsb, _stream(stream)), name)
+    return d_out[:n]
+
+
+def huff_mtf_forward(d_in: torch.Tensor, block: int, d_out=None, ws=None, stream=None):
+    """Move-to-front coding of every `block`-byte block (asynchronous)."""
+    return _mtf_call(lib().huff_mtf_forward, "huff_mtf_forward", d_in, block, d_out, ws, stream)
+
+
+def huff_mtf_inverse(d_in: torch.Tensor, block: int, d_out=None, ws=None, stream=None):
+    """Inverse of huff_mtf_forward (asynchronous)."""
+    return _mtf_call(lib().huff_mtf_inverse, "huff_mtf_inverse", d_in, block, d_out, ws, stream)
+
+
+HUFF_M3_MTF = 1
+
+
 def huff_m3_compress(d_in: torch.Tensor, block: int, segment_bytes: int,
-                     chunk_symbols: int = DEFAULT_CHUNK_SYMBOLS, stream=None):
+                     chunk_symbols: int = DEFAULT_CHUNK_SYMBOLS, stages: int = 0, stream=None):
     """(container uint8 tensor, status int32[1]): Method 3 -- the transform of
-    every block, then one codebook per segment."""
+    every block (then move-to-front with stages=HUFF_M3_MTF), then one
+    codebook per segment."""
     x = _u8(d_in)
     n = x.numel()
     L = lib()
@@ -574,8 +609,8 @@ def huff_m3_compress(d_in: torch.Tensor, block: int, segment_bytes: int,
     ob = torch.zeros(1, dtype=torch.int64, device=dev)
     st = new_status(dev)
     _check(L.huff_m3_compress(_ptr(x) if n else None, n, block, segment_bytes, chunk_symbols,
-                              _ptr(out), cap, _ptr(ob), _ptr(ws), wsb, _ptr(st), _stream(stream)),
-           "huff_m3_compress")
+                              stages, _ptr(out), cap, _ptr(ob), _ptr(ws), wsb, _ptr(st),
+                              _stream(stream)), "huff_m3_compress")
     size = int(ob.item())
     return (out[:size] if int(st.item()) == 0 else out[:0]), st
 

@@ -556,7 +556,8 @@ bool bwt_args_ok(uint64_t n, uint32_t block)
 
 inline bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
 
-__global__ void k_m3_header(uint8_t *out, uint64_t n, uint32_t block, uint32_t count, uint32_t head)
+__global__ void k_m3_header(uint8_t *out, uint64_t n, uint32_t block, uint32_t count,
+                            uint32_t stages, uint32_t head)
 {
     for (uint32_t i = threadIdx.x; i < head; i += blockDim.x) {
         if (i < 8)
@@ -565,7 +566,9 @@ __global__ void k_m3_header(uint8_t *out, uint64_t n, uint32_t block, uint32_t c
             out[i] = (uint8_t)(block >> (8 * (i - 8)));
         else if (i < 16)
             out[i] = (uint8_t)(count >> (8 * (i - 12)));
-        else if (i >= 16 + 4 * count)
+        else if (i < 20)
+            out[i] = (uint8_t)(stages >> (8 * (i - 16)));
+        else if (i >= 20 + 4 * count)
             out[i] = 0;
     }
 }
@@ -576,7 +579,9 @@ __global__ void k_add_u64(unsigned long long *p, uint64_t v, const int32_t *stat
         *p += v;
 }
 
-uint32_t m3_head_bytes(uint64_t count) { return (uint32_t)((16 + 4 * count + 15) & ~15ull); }
+uint32_t m3_head_bytes(uint64_t count) { return (uint32_t)((20 + 4 * count + 15) & ~15ull); }
+
+uint64_t max3(uint64_t a, uint64_t b, uint64_t c) { return a > b ? (a > c ? a : c) : (b > c ? b : c); }
 
 }  // namespace
 }  // namespace huff
@@ -705,32 +710,37 @@ uint64_t huff_m3_workspace_size(uint64_t n, uint32_t block, uint64_t segment_byt
     const uint64_t seg = huff_segmented_workspace_size(n, segment_bytes, chunk_symbols);
     if (!seg)
         return 0;
-    const uint64_t b = huff_bwt_workspace_size(n, block);
-    return ((n + 255) & ~255ull) + (b > seg ? b : seg);
+    return ((n + 255) & ~255ull) +
+           max3(huff_bwt_workspace_size(n, block), seg, huff_mtf_workspace_size(n, block));
 }
 
 huff_status_t huff_m3_compress(const uint8_t *d_in, uint64_t n, uint32_t block,
-                               uint64_t segment_bytes, uint32_t chunk_symbols, uint8_t *d_out,
-                               uint64_t out_cap, uint64_t *d_out_bytes, void *d_ws,
-                               uint64_t ws_bytes, int32_t *d_status, huff_stream_t stream)
+                               uint64_t segment_bytes, uint32_t chunk_symbols, uint32_t stages,
+                               uint8_t *d_out, uint64_t out_cap, uint64_t *d_out_bytes,
+                               void *d_ws, uint64_t ws_bytes, int32_t *d_status,
+                               huff_stream_t stream)
 {
     HUFF_API_RANGE("huff_m3_compress");
     const uint64_t need = huff_m3_workspace_size(n, block, segment_bytes, chunk_symbols);
     const uint64_t count = block ? (n + block - 1) / block : 0;
     const uint32_t head = m3_head_bytes(count);
     if (!need || !d_out || !d_out_bytes || !d_status || !d_ws || ws_bytes < need ||
-        out_cap < head || (n && !d_in) || !aligned16(d_out) || !aligned16(d_ws))
+        out_cap < head || (n && !d_in) || !aligned16(d_out) || !aligned16(d_ws) ||
+        (stages & ~HUFF_M3_MTF))
         return HUFF_ERR_INVALID_ARG;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     uint8_t *ws = static_cast<uint8_t *>(d_ws);
     uint8_t *last = ws;
     uint8_t *rest = ws + ((n + 255) & ~255ull);
+    const uint64_t rest_bytes = ws_bytes - (uint64_t)(rest - ws);
     huff_status_t st = huff_bwt_forward(d_in, n, block, last,
-                                        reinterpret_cast<uint32_t *>(d_out + 16), rest,
-                                        ws_bytes - (uint64_t)(rest - ws), d_status, stream);
+                                        reinterpret_cast<uint32_t *>(d_out + 20), rest, rest_bytes,
+                                        d_status, stream);
+    if (st == HUFF_OK && (stages & HUFF_M3_MTF))
+        st = huff_mtf_forward(last, n, block, last, rest, rest_bytes, stream);
     if (st != HUFF_OK)
         return st;
-    k_m3_header<<<1, 256, 0, s>>>(d_out, n, block, (uint32_t)count, head);
+    k_m3_header<<<1, 256, 0, s>>>(d_out, n, block, (uint32_t)count, stages, head);
     if (cudaGetLastError() != cudaSuccess)
         return HUFF_ERR_CUDA;
     st = huff_segmented_compress(last, n, segment_bytes, chunk_symbols, d_out + head,
@@ -746,7 +756,8 @@ uint64_t huff_m3_decompress_workspace_size(uint64_t n, uint32_t block)
 {
     if (!bwt_args_ok(n, block))
         return 0;
-    return ((n + 255) & ~255ull) + huff_bwt_workspace_size(n, block);
+    const uint64_t b = huff_bwt_workspace_size(n, block), m = huff_mtf_workspace_size(n, block);
+    return ((n + 255) & ~255ull) + (b > m ? b : m);
 }
 
 huff_status_t huff_m3_decompress(const uint8_t *d_in, uint64_t in_bytes, uint8_t *d_out,
@@ -759,12 +770,12 @@ huff_status_t huff_m3_decompress(const uint8_t *d_in, uint64_t in_bytes, uint8_t
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     if (cudaMemsetAsync(d_status, 0, sizeof(int32_t), s) != cudaSuccess)
         return HUFF_ERR_CUDA;
-    uint8_t h[16];
+    uint8_t h[20];
     uint64_t n = 0;
-    uint32_t block = 0, count = 0;
-    bool ok = in_bytes >= 16;
+    uint32_t block = 0, count = 0, stages = 0;
+    bool ok = in_bytes >= 20;
     if (ok) {
-        if (cudaMemcpyAsync(h, d_in, 16, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        if (cudaMemcpyAsync(h, d_in, 20, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
             cudaStreamSynchronize(s) != cudaSuccess)
             return HUFF_ERR_CUDA;
         for (int i = 7; i >= 0; --i)
@@ -773,8 +784,11 @@ huff_status_t huff_m3_decompress(const uint8_t *d_in, uint64_t in_bytes, uint8_t
             block = (block << 8) | h[i];
         for (int i = 15; i >= 12; --i)
             count = (count << 8) | h[i];
+        for (int i = 19; i >= 16; --i)
+            stages = (stages << 8) | h[i];
         ok = block >= 1 && n <= HUFF_BWT_MAX_N && count == (n + block - 1) / block &&
-             16 + 4ull * count <= in_bytes && m3_head_bytes(count) <= in_bytes;
+             (stages & ~HUFF_M3_MTF) == 0 && 20 + 4ull * count <= in_bytes &&
+             m3_head_bytes(count) <= in_bytes;
     }
     if (!ok) {
         static const int32_t corrupt = HUFF_ERR_CORRUPT_STREAM;
@@ -816,8 +830,14 @@ huff_status_t huff_m3_decompress(const uint8_t *d_in, uint64_t in_bytes, uint8_t
             return HUFF_ERR_CUDA;
         return HUFF_OK;
     }
-    return huff_bwt_inverse(last, n, block, reinterpret_cast<const uint32_t *>(d_in + 16), d_out,
-                            rest, ws_bytes - (uint64_t)(rest - ws), d_status, stream);
+    const uint64_t rest_bytes = ws_bytes - (uint64_t)(rest - ws);
+    if (stages & HUFF_M3_MTF) {
+        st = huff_mtf_inverse(last, n, block, last, rest, rest_bytes, stream);
+        if (st != HUFF_OK)
+            return st;
+    }
+    return huff_bwt_inverse(last, n, block, reinterpret_cast<const uint32_t *>(d_in + 20), d_out,
+                            rest, rest_bytes, d_status, stream);
 }
 
 }  // extern "C"

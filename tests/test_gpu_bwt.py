@@ -1,6 +1,6 @@
 """GPU parity of Method 3 (Section III-A): the block-sorting transform of
-every block, its inverse and the Method 3 container, byte for byte against
-the oracle, through the C ABI."""
+every block, its inverse, the move-to-front stage and the Method 3
+container, byte for byte against the oracle, through the C ABI."""
 import numpy as np
 import pytest
 import torch
@@ -91,14 +91,50 @@ def test_empty_input():
     assert last.numel() == 0 and prim.numel() == 0 and int(st.item()) == 0
 
 
-@pytest.mark.parametrize("kind,n,block,seg", [("text", 0, 16, 16), ("text", 70001, 65536, 16384),
-                                              ("zipf", 300000, 100000, 65536),
-                                              ("single", 20000, 4096, 4096)])
-def test_m3_container_matches_oracle(kind, n, block, seg):
-    x = _gen(kind, n, 29) if n else np.zeros(0, dtype=np.uint8)
-    c, st = hg.huff_m3_compress(_dev(x), block, seg)
+MTF_CASES = [("text", 1, 1), ("text", 5000, 1000), ("text", 4096, 4096), ("text", 4097, 4096),
+             ("text", 100003, 65536), ("text", 200000, 12345), ("uniform", 70000, 9000),
+             ("geometric", 65536, 8192), ("single", 9000, 777), ("periodic", 10007, 1024)]
+
+
+@pytest.mark.parametrize("kind,n,block", MTF_CASES, ids=[f"{k}-{n}-{b}" for k, n, b in MTF_CASES])
+def test_mtf_matches_oracle(kind, n, block):
+    # on the transform's output (the stage's real input) and on raw bytes
+    x = _gen(kind, n, 31)
+    L, _ = oracle.bwt(x, block) if n <= 300000 else (x, None)
+    for src in (L, x):
+        ref = oracle.mtf(src, block)
+        got = hg.huff_mtf_forward(_dev(src), block)
+        torch.cuda.synchronize()
+        assert np.array_equal(got.cpu().numpy(), ref)
+        back = hg.huff_mtf_inverse(_dev(ref), block)
+        torch.cuda.synchronize()
+        assert np.array_equal(back.cpu().numpy(), src)
+
+
+def test_mtf_large_blocks_in_place():
+    n, block = (8 << 20) + 333, 1 << 20
+    x = synth.text(n, 37)
+    ref = oracle.mtf(x, block)
+    d = _dev(x)
+    hg.huff_mtf_forward(d, block, d_out=d)  # in place
     torch.cuda.synchronize()
-    ost, ref = oracle.m3_compress(x, block, seg)
+    assert np.array_equal(d.cpu().numpy(), ref)
+    hg.huff_mtf_inverse(d, block, d_out=d)
+    torch.cuda.synchronize()
+    assert np.array_equal(d.cpu().numpy(), x)
+
+
+@pytest.mark.parametrize("kind,n,block,seg,stages", [("text", 0, 16, 16, 0),
+                                                     ("text", 70001, 65536, 16384, 0),
+                                                     ("text", 70001, 65536, 16384, 1),
+                                                     ("zipf", 300000, 100000, 65536, 1),
+                                                     ("single", 20000, 4096, 4096, 0),
+                                                     ("single", 20000, 4096, 4096, 1)])
+def test_m3_container_matches_oracle(kind, n, block, seg, stages):
+    x = _gen(kind, n, 29) if n else np.zeros(0, dtype=np.uint8)
+    c, st = hg.huff_m3_compress(_dev(x), block, seg, stages=stages)
+    torch.cuda.synchronize()
+    ost, ref = oracle.m3_compress(x, block, seg, mtf_stage=bool(stages))
     assert int(st.item()) == 0 and ost == 0
     assert np.array_equal(c.cpu().numpy(), ref)
     back, m, st = hg.huff_m3_decompress(c)
@@ -109,12 +145,14 @@ def test_m3_container_matches_oracle(kind, n, block, seg):
 def test_m3_rejects_bad_containers():
     x = synth.text(50000, 8)
     st, c = oracle.m3_compress(x, 20000, 16384)
-    for mutate in ("primary", "count", "short"):
+    for mutate in ("primary", "count", "stages", "short"):
         t = c.copy()
         if mutate == "primary":
-            t[16:20] = np.frombuffer((20000).to_bytes(4, "little"), np.uint8)
+            t[20:24] = np.frombuffer((20000).to_bytes(4, "little"), np.uint8)
         elif mutate == "count":
             t[12] ^= 1
+        elif mutate == "stages":
+            t[16] = 2
         else:
             t = t[:-16]
         dc = torch.zeros(max(t.size, 16), dtype=torch.uint8, device="cuda")
