@@ -360,6 +360,21 @@ def measure_method3(hg, synth, torch, oracle=None, n=256 << 20, block=1 << 20,
     y, m, st2 = hg.huff_m3_decompress(c)
     td = t_ms(lambda: hg.huff_m3_decompress(c), reps=2)
     ok = ok and int(st.item()) == 0 and int(st2.item()) == 0 and m == n and bool(torch.equal(y, x))
+    # with move-to-front after the transform (64 KiB segments suit its output)
+    mws = torch.empty(hg.lib().huff_mtf_workspace_size(n, block), dtype=torch.uint8,
+                      device="cuda")
+    mtf_out = torch.empty(n, dtype=torch.uint8, device="cuda")
+    tmf = t_ms(lambda: hg.huff_mtf_forward(last, block, d_out=mtf_out, ws=mws))
+    tmi = t_ms(lambda: hg.huff_mtf_inverse(mtf_out, block, d_out=back, ws=mws))
+    ok = ok and bool(torch.equal(back, last))
+    del mws, mtf_out
+    seg_mtf = 65536
+    cm, stm = hg.huff_m3_compress(x, block, seg_mtf, stages=hg.HUFF_M3_MTF)
+    tcm = t_ms(lambda: hg.huff_m3_compress(x, block, seg_mtf, stages=hg.HUFF_M3_MTF), reps=2)
+    ym, mm, stm2 = hg.huff_m3_decompress(cm)
+    tdm = t_ms(lambda: hg.huff_m3_decompress(cm), reps=2)
+    ok = ok and int(stm.item()) == 0 and int(stm2.item()) == 0 and mm == n and \
+        bool(torch.equal(ym, x))
     seg_c, _ = hg.huff_segmented_compress(x, segment)
     one = hg.compress(x)
     out = {"workload": f"synthetic text {n >> 20} MiB (seed 1), {block >> 20} MiB blocks, "
@@ -369,6 +384,9 @@ def measure_method3(hg, synth, torch, oracle=None, n=256 << 20, block=1 << 20,
            "inverse_ms": ti, "inverse_gbs": n / ti / 1e6,
            "m3_compress_ms": tc, "m3_compress_gbs": n / tc / 1e6,
            "m3_decompress_ms": td, "m3_decompress_gbs": n / td / 1e6,
+           "mtf_forward_gbs": n / tmf / 1e6, "mtf_inverse_gbs": n / tmi / 1e6,
+           "m3_mtf_compress_ms": tcm, "m3_mtf_decompress_ms": tdm,
+           "ratio_m3_mtf_64k_segments": cm.numel() / n,
            "ratio_m3": c.numel() / n, "ratio_segmented_same_segments": seg_c.numel() / n,
            "ratio_one_codebook": one.numel() / n,
            "bound": "hbm (stable radix passes and random rank scatters); see "
