@@ -398,10 +398,16 @@ def measure_method3(hg, synth, torch, oracle=None, n=256 << 20, block=1 << 20,
         t1 = time.perf_counter()
         oracle.ibwt(L, block, P)
         t2 = time.perf_counter()
+        M = oracle.mtf(L, block)
+        t3 = time.perf_counter()
+        oracle.imtf(M, block)
+        t4 = time.perf_counter()
         out["cpu_baseline"] = {"kind": "oracle", "cores": 1,
                                "sample": f"the first 4 blocks ({4 * block >> 20} MiB)",
                                "forward_gbs": xs.size / (t1 - t0) / 1e9,
-                               "inverse_gbs": xs.size / (t2 - t1) / 1e9}
+                               "inverse_gbs": xs.size / (t2 - t1) / 1e9,
+                               "mtf_forward_gbs": xs.size / (t3 - t2) / 1e9,
+                               "mtf_inverse_gbs": xs.size / (t4 - t3) / 1e9}
     return out
 
 
