@@ -161,3 +161,33 @@ def test_m3_rejects_bad_containers():
         torch.cuda.synchronize()
         assert int(st.item()) != 0, mutate
         assert oracle.m3_decompress(t)[0] != oracle.OK, mutate
+
+
+def test_full_size_sampled_against_oracle():
+    # 64 MiB of text in 1 MiB blocks, the bench's block size: three blocks
+    # checked against the oracle one by one (the oracle would take minutes
+    # for all), the rest by the round trip through the GPU inverse
+    n, block = 64 << 20, 1 << 20
+    x = synth.text(n, 1)
+    d = _dev(x)
+    last, prim, st = hg.huff_bwt_forward(d, block)
+    torch.cuda.synchronize()
+    assert int(st.item()) == 0
+    L = last.cpu().numpy()
+    P = prim.cpu().numpy().astype(np.uint32)
+    for b in (0, 31, 63):
+        s = b * block
+        ref_l, ref_p = oracle.bwt(x[s:s + block], block)
+        assert np.array_equal(L[s:s + block], ref_l), b
+        assert int(P[b]) == int(ref_p[0]), b
+        ref_m = oracle.mtf(ref_l, block)
+        got_m = hg.huff_mtf_forward(last[s:s + block].clone(), block)
+        torch.cuda.synchronize()
+        assert np.array_equal(got_m.cpu().numpy(), ref_m), b
+    back, st = hg.huff_bwt_inverse(last, block, prim)
+    torch.cuda.synchronize()
+    assert int(st.item()) == 0 and torch.equal(back, d)
+    c, st = hg.huff_m3_compress(d, block, 65536, stages=hg.HUFF_M3_MTF)
+    y, m, st2 = hg.huff_m3_decompress(c)
+    torch.cuda.synchronize()
+    assert int(st.item()) == 0 and int(st2.item()) == 0 and m == n and torch.equal(y, d)
