@@ -416,3 +416,23 @@ def test_limited_stream_round_trip(gen):
     assert np.array_equal(out[:nb].cpu().numpy(), ref)
     back, n, st = gpu_decode(out[:nb])
     assert st == 0 and np.array_equal(back[:n].cpu().numpy(), x)
+
+
+def test_limited_full_size_geometric():
+    # the length-limited row on 64 MiB of the geometric stress input (its
+    # Huffman codes run to ~29 bits): the whole 12-bit stream equals the
+    # oracle's and decodes back
+    x = synth.geometric(64 << 20, 41)
+    d = dev(x)
+    h = hg.huff_histogram(d)
+    cb, st = hg.huff_build_codebook_limited(h, 12)
+    out, ob, st = hg.huff_encode(d, cb, d_status=st)
+    torch.cuda.synchronize()
+    nb = int(ob.item())
+    ost, oln = oracle.code_lengths_limited(oracle.histogram(x), 12)
+    assert max(int(v) for v in oln) == 12
+    ost, ref, need = oracle.encode(x, oln)
+    assert int(st.item()) == 0 and ost == 0 and nb == need
+    assert np.array_equal(out[:nb].cpu().numpy(), ref)
+    back, n, st = gpu_decode(out[:nb])
+    assert st == 0 and n == x.size and torch.equal(back[:n], d)

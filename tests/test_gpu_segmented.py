@@ -71,3 +71,27 @@ def test_segmented_bad_arguments():
     for seg in (0, 8, 24):
         with pytest.raises(hg.HuffError):
             hg.huff_segmented_compress(x, seg)
+
+
+def test_segmented_full_size_sampled():
+    # 256 MiB of text in 1 MiB segments (the bench's workload): three
+    # segments' streams against the oracle's, every start-table entry
+    # consistent, and the whole container back through the GPU
+    n, seg = 256 << 20, 1 << 20
+    x = synth.text(n, 1)
+    d = _dev(x)
+    c, st = hg.huff_segmented_compress(d, seg)
+    torch.cuda.synchronize()
+    assert int(st.item()) == 0
+    ch = c.cpu().numpy()
+    count = n // seg
+    start = np.frombuffer(ch[24:24 + 8 * (count + 1)].tobytes(), "<u8")
+    assert int(start[-1]) == ch.size
+    for i in (0, 100, count - 1):
+        ost, ref = oracle.compress(x[i * seg:(i + 1) * seg])
+        s0 = int(start[i])
+        assert np.array_equal(ch[s0:s0 + ref.size], ref), i
+        assert not ch[s0 + ref.size:int(start[i + 1])].any()
+    back, m, st = hg.huff_segmented_decompress(c)
+    torch.cuda.synchronize()
+    assert int(st.item()) == 0 and m == n and torch.equal(back, d)
