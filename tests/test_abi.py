@@ -75,3 +75,30 @@ def test_product_never_touches_the_oracle():
             text = open(f).read()
             assert "import oracle" not in text and "huff_oracle" not in text, f
             assert "from oracle" not in text, f
+
+
+def test_next_row_sizes_and_argument_checks(lib):
+    # host-only paths of the next rows: sizes, and argument errors returned
+    # before any device work
+    import ctypes
+    assert lib.huff_bwt_workspace_size(1 << 20, 0) == 0          # block 0
+    assert lib.huff_bwt_workspace_size(1 << 31, 1 << 20) == 0    # above the limit
+    a, b = lib.huff_bwt_workspace_size(1 << 20, 1 << 16), lib.huff_bwt_workspace_size(1 << 22, 1 << 16)
+    assert 0 < a < b
+    assert lib.huff_mtf_workspace_size(1 << 20, 0) == 0
+    assert lib.huff_mtf_workspace_size(1 << 20, 4096) > (1 << 20)
+    assert lib.huff_m3_max_size(1000, 0, 16, 16384) == 0
+    assert lib.huff_m3_max_size(1000, 100, 15, 16384) == 0          # segment not a multiple of 16
+    count = 10
+    head = (20 + 4 * count + 15) & ~15
+    assert lib.huff_m3_max_size(1000, 100, 1024, 16384) == \
+        head + lib.huff_segmented_max_size(1000, 1024, 16384)
+    st = ctypes.c_int32(0)
+    none = ctypes.c_void_p(0)
+    # null pointers / zero block: invalid before the device is touched
+    assert lib.huff_bwt_forward(none, 16, 0, none, none, none, 0, ctypes.byref(st), none) == \
+        hg.HUFF_ERR_INVALID_ARG
+    assert lib.huff_mtf_forward(none, 16, 4, none, none, 0, none) == hg.HUFF_ERR_INVALID_ARG
+    assert lib.huff_mtf_inverse(none, 16, 0, none, none, 0, none) == hg.HUFF_ERR_INVALID_ARG
+    assert lib.huff_m3_compress(none, 16, 4, 16, 16384, 2, none, 0, none, none, 0, none,
+                                none) == hg.HUFF_ERR_INVALID_ARG
