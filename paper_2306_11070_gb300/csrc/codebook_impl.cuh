@@ -135,20 +135,37 @@ __device__ __forceinline__ void build_codebook(const unsigned long long *__restr
     if (m >= 2) {
         // 2. two-queue merge
         if (t == 0) {
+            // the fronts of both queues are kept in registers: a leaf's weight
+            // is loaded once, and a merged node's weight usually never is
             int li = 0, ii = m, ni = m;
+            unsigned long long lw = sh.nw[0], iw = 0;
             for (int step = 0; step < m - 1; ++step) {
                 int a, b;
-                if (li < m && (ii >= ni || sh.nw[li] <= sh.nw[ii]))
+                unsigned long long wa, wb;
+                if (li < m && (ii >= ni || lw <= iw)) {
                     a = li++;
-                else
+                    wa = lw;
+                    lw = li < m ? sh.nw[li] : 0ull;
+                } else {
                     a = ii++;
-                if (li < m && (ii >= ni || sh.nw[li] <= sh.nw[ii]))
+                    wa = iw;
+                    iw = ii < ni ? sh.nw[ii] : 0ull;
+                }
+                if (li < m && (ii >= ni || lw <= iw)) {
                     b = li++;
-                else
+                    wb = lw;
+                    lw = li < m ? sh.nw[li] : 0ull;
+                } else {
                     b = ii++;
-                sh.nw[ni] = sh.nw[a] + sh.nw[b];
+                    wb = iw;
+                    iw = ii < ni ? sh.nw[ii] : 0ull;
+                }
+                const unsigned long long w2 = wa + wb;
+                sh.nw[ni] = w2;
                 sh.par[a] = (int16_t)ni;
                 sh.par[b] = (int16_t)ni;
+                if (ii == ni)
+                    iw = w2;  // the merged queue was empty: the new node is its front
                 ++ni;
             }
             sh.par[2 * m - 2] = (int16_t)(2 * m - 2);  // the root points at itself
