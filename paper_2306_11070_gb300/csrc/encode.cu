@@ -36,7 +36,8 @@ using namespace enc;
 // One CTA of 24 warps per SM: one copy of the 32 KiB code table per SM and
 // the rest of shared memory left to L1 (measured on 1 GiB text: 0.89 ms
 // with three 8-warp CTAs per SM, 0.86 ms with two 12-warp CTAs, 0.80 ms
-// with one 24-warp CTA; 28 warps spill more and take 0.82 ms).
+// with one 24-warp CTA; 28 warps spill more and take 0.82 ms, 20 warps
+// without spills 0.84 ms).
 constexpr int kEncBlock = 768;
 constexpr int kEncWarps = kEncBlock / 32;
 constexpr int kEncSmemBytes = (kTblWords + kEncWarps * kWarpObuf) * 4;
