@@ -3,7 +3,7 @@
 // from the list 0..255; a byte is coded as its position in the list and then
 // moved to the front.
 //
-// Blocks are cut into 4 KiB segments, one thread each, and the list a
+// Blocks are cut into 1 KiB segments, one thread each, and the list a
 // segment starts from is found without running the blocks serially:
 //  - forward: the list at the end of a segment is the segment's distinct
 //    bytes, latest occurrence first, followed by the rest of the list it
@@ -25,7 +25,7 @@
 namespace huff {
 namespace {
 
-constexpr uint32_t kSeg = 4096;    // bytes per segment
+constexpr uint32_t kSeg = 1024;    // bytes per segment
 constexpr int kMtfThreads = 128;   // threads (segments) per CTA of the coding kernels
 constexpr int kListWarps = 4;      // warps (blocks) per CTA of the chaining kernels
 
