@@ -8,19 +8,57 @@
 
 namespace huff {
 
+int current_device()
+{
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices)
+        return -1;
+    return dev;
+}
+
 int device_sm_count()
 {
-    static int cached[16] = {0};
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 16)
-        dev = 0;
-    if (cached[dev] == 0) {
-        int v = 0;
+    static std::atomic<int> cached[kMaxDevices];
+    const int dev = current_device();
+    if (dev < 0)
+        return 0;
+    int v = cached[dev].load(std::memory_order_relaxed);
+    if (v == 0) {
         if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v < 1)
-            v = 1;
-        cached[dev] = v;
+            return 0;
+        cached[dev].store(v, std::memory_order_relaxed);
     }
-    return cached[dev];
+    return v;
+}
+
+cudaError_t kernel_setup(KernelSetup &ks, const void *func, int block, size_t dyn_smem,
+                         int *per_sm)
+{
+    const int dev = current_device();
+    if (dev < 0)
+        return cudaErrorInvalidDevice;
+    int v = ks.per_sm[dev].load(std::memory_order_acquire);
+    if (v == 0) {
+        std::lock_guard<std::mutex> lock(ks.mu);
+        v = ks.per_sm[dev].load(std::memory_order_relaxed);
+        if (v == 0) {
+            cudaError_t err;
+            if (dyn_smem > 48 * 1024) {
+                err = cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)dyn_smem);
+                if (err != cudaSuccess)
+                    return err;
+            }
+            err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, func, block, dyn_smem);
+            if (err != cudaSuccess)
+                return err;
+            if (v < 1)
+                v = 1;
+            ks.per_sm[dev].store(v, std::memory_order_release);
+        }
+    }
+    *per_sm = v;
+    return cudaSuccess;
 }
 
 namespace {

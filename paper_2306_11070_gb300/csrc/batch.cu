@@ -277,11 +277,21 @@ __global__ void __launch_bounds__(kBatchBlock, 3) k_batch_compress(BatchArgs a)
 }
 
 // ------------------------------------------------------------------ decompress
+// One copy of the lookup table per CTA (tables are rebuilt per buffer, and
+// most buffers of a batch are small); dynamic shared memory as in decode.cu:
+// the tables, then from the next 4 KiB boundary a 4 KiB output block and a
+// 4 KiB input block per warp.
+constexpr int kBatchCopies = 1;
+constexpr size_t kDecompTables = (sizeof(dec::DecodeShared<kBatchCopies>) + 15) & ~size_t(15);
+constexpr size_t kDecompressSmem = kDecompTables + 4096 + (size_t)kBatchWarps * 2 * 4096;
+
 __global__ void __launch_bounds__(kBatchBlock, 2) k_batch_decompress(BatchArgs a)
 {
-    __shared__ dec::DecodeShared sh;
-    __shared__ uint32_t in_ring[kBatchWarps * dec::kInRing * 32];
-    __shared__ uint32_t out_ring[kBatchWarps * dec::kOutRing * 32];
+    extern __shared__ __align__(16) unsigned char dsm[];
+    dec::DecodeShared<kBatchCopies> &sh = *reinterpret_cast<dec::DecodeShared<kBatchCopies> *>(dsm);
+    const uint32_t rings = (smem_u32(dsm) + (uint32_t)kDecompTables + 4095u) & ~4095u;
+    uint16_t *scratch = reinterpret_cast<uint16_t *>(dsm + (rings - smem_u32(dsm)) +
+                                                     kBatchWarps * 4096);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
 
     // phase 1: statuses and work sizes from the headers
@@ -334,8 +344,8 @@ __global__ void __launch_bounds__(kBatchBlock, 2) k_batch_decompress(BatchArgs a
     }
 
     // phase 3: decode items
-    uint32_t *in_col = in_ring + warp * dec::kInRing * 32 + lane;
-    uint32_t *out_col = out_ring + warp * dec::kOutRing * 32 + lane;
+    const uint32_t out_s = rings + warp * 4096 + lane * 4;
+    const uint32_t in_s = rings + (kBatchWarps + warp) * 4096 + lane * 16;
     const uint64_t total_items = a.dec_items[a.count];
     uint32_t have = 0xffffffffu;
     bool ready = false;
@@ -351,7 +361,7 @@ __global__ void __launch_bounds__(kBatchBlock, 2) k_batch_decompress(BatchArgs a
             __syncthreads();
             ready = dec::prepare<kBatchBlock>(B.in, B.in_bytes, B.out, B.out_cap, B.out_bytes,
                                               B.status, it == a.dec_items[b] && tid == 0, sh,
-                                              reinterpret_cast<uint16_t *>(in_ring), si);
+                                              scratch, si);
             if (ready)
                 S = dec::pick_split(si.chunks, a.min_lanes);
             have = b;
@@ -360,7 +370,7 @@ __global__ void __launch_bounds__(kBatchBlock, 2) k_batch_decompress(BatchArgs a
             continue;
         const uint64_t tasks = (si.chunks + (32 / S) - 1) / (32 / S);
         const uint64_t task = (uint64_t)(it - a.dec_items[b]) * kTasksPerItem + warp;
-        if (task < tasks && dec::decode_task(si, S, task, in_col, out_col)) {
+        if (task < tasks && dec::decode_task(si, S, task, in_s, out_s)) {
             if (lane == 0)
                 set_status(B.status, HUFF_ERR_CORRUPT_STREAM);
         }
@@ -455,29 +465,20 @@ cudaError_t batch_upload(const BatchLayout &L, void *d_block, uint8_t *host, cud
     return cudaMemcpyAsync(d_block, host, L.upload_bytes, cudaMemcpyHostToDevice, s);
 }
 
-// Resident CTAs per SM of the batch kernel for `op`.
+KernelSetup g_compress_setup, g_decompress_setup;
+
+// Resident CTAs per SM of the batch kernel for `op` on the current device
+// (0 on error).
 int batch_occupancy(huff_op_t op)
 {
-    static int occ[2] = {0, 0};
-    const int i = op == HUFF_BATCH_COMPRESS ? 0 : 1;
-    if (occ[i] == 0) {
-        int per_sm = 0;
-        cudaError_t err;
-        if (i == 0) {
-            err = cudaFuncSetAttribute(k_batch_compress,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, kCompressSmem);
-            if (err == cudaSuccess)
-                err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch_compress,
-                                                                    kBatchBlock, kCompressSmem);
-        } else {
-            err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch_decompress,
-                                                                kBatchBlock, 0);
-        }
-        if (err != cudaSuccess || per_sm < 1)
-            return 0;
-        occ[i] = per_sm;
-    }
-    return occ[i];
+    int per_sm = 0;
+    const cudaError_t err =
+        op == HUFF_BATCH_COMPRESS
+            ? kernel_setup(g_compress_setup, (const void *)k_batch_compress, kBatchBlock,
+                           kCompressSmem, &per_sm)
+            : kernel_setup(g_decompress_setup, (const void *)k_batch_decompress, kBatchBlock,
+                           kDecompressSmem, &per_sm);
+    return err == cudaSuccess ? per_sm : 0;
 }
 
 // Clear the control words and launch the cooperative batch kernel.
@@ -489,7 +490,7 @@ cudaError_t batch_launch(huff_op_t op, const BatchArgs &args, unsigned grid, cud
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(grid);
     cfg.blockDim = dim3(kBatchBlock);
-    cfg.dynamicSmemBytes = op == HUFF_BATCH_COMPRESS ? kCompressSmem : 0;
+    cfg.dynamicSmemBytes = op == HUFF_BATCH_COMPRESS ? kCompressSmem : kDecompressSmem;
     cfg.stream = s;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeCooperative;

@@ -4,10 +4,11 @@
 //
 // Every CTA validates the header and builds the canonical decode tables in
 // shared memory from the 256 stored lengths:
-//  - a 2^12-entry lookup table; an entry holds the bytes of up to three codes
-//    that fit in the 12-bit window, their total length and their number, so
-//    text decodes ~2.3 symbols per lookup; a byte table beside it holds the
-//    length of the first code alone;
+//  - a 2^12-entry lookup table in four interleaved copies (lane l reads copy
+//    l mod 4); an entry holds the bytes of up to two codes that fit in the
+//    12-bit window, their total length and their number, so text decodes
+//    ~2.0 symbols per lookup; a byte table beside it holds the length of the
+//    first code alone;
 //  - per length, the first canonical code and the index of its first symbol,
 //    for codes longer than 12 bits (searched by length).
 //
@@ -32,18 +33,20 @@
 // from every lane's segment end (32 lookups) runs with no checks and no
 // branch (warp-uniform); the others (12 lookups) check each code.  Per
 // lookup the unchecked window does one 4-byte shared-memory load of the table
-// entry, two funnel shifts to drop the bits (entry >> 24 is the shift
-// amount), and appends the entry's symbol bytes to a register word that is
-// stored to the lane's output ring when it is complete.  A code longer than
-// the table has an all-zero entry, which consumes and emits nothing: the
-// lane waits on it until the next window resolves it.  Between windows each
-// lane tops up a 32-word input ring in shared memory with cp.async (4-byte
-// copies, laid out [word][lane] so a warp's reads and writes never share a
-// bank) and stores every completed 16-byte group of its 128-byte output ring
-// (same layout) with one 16-byte global store.  The next input word is always preloaded,
-// so the ring's latency stays off the per-codeword dependency chain.  The
-// decoded codeword sequence is exactly the sequential one, so the stream
-// checks are those of a sequential decoder.
+// entry, two funnel shifts by the entry itself to drop the bits, and two
+// funnel shifts by entry >> 8 that push the entry's symbol bytes into a
+// 64-bit output queue; every second lookup refills the bit buffer from the
+// input ring and stores the queue's oldest word to the lane's output ring.
+// A code longer than the table has an all-zero entry, which consumes and
+// emits nothing: the lane waits on it until the next window resolves it.
+// Between windows each lane tops up its input ring in shared memory with
+// 16-byte cp.async copies that bypass L1 (eight 16-byte cells per lane) and
+// stores every completed 16-byte group of its 128-byte output ring (laid out
+// [word][lane], so a warp's accesses never share a bank) with one 16-byte
+// global store.  The next input word is always preloaded, so the ring's
+// latency stays off the per-codeword dependency chain.  The decoded codeword
+// sequence is exactly the sequential one, so the stream checks are those of
+// a sequential decoder.
 #include "decode_impl.cuh"
 
 namespace huff {
@@ -51,7 +54,14 @@ namespace {
 
 using namespace dec;
 
-constexpr int kDecBlock = 256;
+// One 16-warp CTA per SM with four interleaved copies of the lookup table.
+constexpr int kDecBlock = 512;
+constexpr int kDecWarps = kDecBlock / 32;
+constexpr int kDecCopies = 4;
+// dynamic shared memory: the tables, then (from the next 4 KiB boundary) one
+// 4 KiB output block and one 4 KiB input block per warp
+constexpr size_t kDecTables = (sizeof(DecodeShared<kDecCopies>) + 15) & ~size_t(15);
+constexpr size_t kDecSmem = kDecTables + 4096 + (size_t)kDecWarps * 2 * 4096;
 
 struct DecodeArgs {
     const uint8_t *stream;
@@ -63,11 +73,14 @@ struct DecodeArgs {
     uint32_t min_chains;
 };
 
-__global__ void __launch_bounds__(kDecBlock) k_decode(DecodeArgs a)
+__global__ void __launch_bounds__(kDecBlock, 1) k_decode(DecodeArgs a)
 {
-    __shared__ DecodeShared sh;
-    __shared__ uint32_t in_ring[(kDecBlock / 32) * kInRing * 32];
-    __shared__ uint32_t out_ring[(kDecBlock / 32) * kOutRing * 32];
+    extern __shared__ __align__(16) unsigned char dsm[];
+    DecodeShared<kDecCopies> &sh = *reinterpret_cast<DecodeShared<kDecCopies> *>(dsm);
+    const uint32_t tbl_end = smem_u32(dsm) + (uint32_t)kDecTables;
+    const uint32_t rings = (tbl_end + 4095u) & ~4095u;  // warps' output blocks, then input blocks
+    uint16_t *scratch = reinterpret_cast<uint16_t *>(dsm + (rings - smem_u32(dsm)) +
+                                                     kDecWarps * 4096);  // free while tables build
 
     if (chain_failed(a.status))
         return;
@@ -86,19 +99,18 @@ __global__ void __launch_bounds__(kDecBlock) k_decode(DecodeArgs a)
     }
     StreamInfo si;
     if (!prepare<kDecBlock>(a.stream, a.bytes, a.out, a.cap, a.d_n, a.status,
-                            blockIdx.x == 0 && threadIdx.x == 0, sh,
-                            reinterpret_cast<uint16_t *>(in_ring), si))
+                            blockIdx.x == 0 && threadIdx.x == 0, sh, scratch, si))
         return;
     const uint32_t S = pick_split(si.chunks, a.min_chains);
     const uint64_t tasks = (si.chunks + (32 / S) - 1) / (32 / S);
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-    uint32_t *in_col = in_ring + wib * kInRing * 32 + lane;
-    uint32_t *out_col = out_ring + wib * kOutRing * 32 + lane;
+    const uint32_t out_s = rings + wib * 4096 + lane * 4;
+    const uint32_t in_s = rings + (kDecWarps + wib) * 4096 + lane * 16;
     // tasks are dealt to the CTAs in turn (task t to CTA t mod grid), so
     // when there are fewer tasks than warps every SM still gets its share
-    const uint64_t nwarps = (uint64_t)gridDim.x * (kDecBlock / 32);
+    const uint64_t nwarps = (uint64_t)gridDim.x * kDecWarps;
     for (uint64_t task = (uint64_t)wib * gridDim.x + blockIdx.x; task < tasks; task += nwarps) {
-        if (decode_task(si, S, task, in_col, out_col)) {
+        if (decode_task(si, S, task, in_s, out_s)) {
             if (lane == 0)
                 set_status(a.status, HUFF_ERR_CORRUPT_STREAM);
             return;
@@ -106,24 +118,24 @@ __global__ void __launch_bounds__(kDecBlock) k_decode(DecodeArgs a)
     }
 }
 
+KernelSetup g_decode_setup;
+
 }  // namespace
 
 cudaError_t launch_decode(const uint8_t *d_stream, uint64_t bytes, uint8_t *d_out, uint64_t out_cap,
                           unsigned long long *d_n, int32_t *d_status, cudaStream_t s)
 {
-    static int per_sm = 0;
-    cudaError_t err;
-    if (per_sm == 0) {
-        err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_decode, kDecBlock, 0);
-        if (err != cudaSuccess)
-            return err;
-        if (per_sm < 1)
-            per_sm = 1;
-    }
+    int per_sm = 0;
+    cudaError_t err = kernel_setup(g_decode_setup, (const void *)k_decode, kDecBlock, kDecSmem,
+                                   &per_sm);
+    if (err != cudaSuccess)
+        return err;
     const int sms = device_sm_count();
+    if (sms < 1)
+        return cudaErrorInvalidDevice;
     // the chunk count is only known on the device; bound it by the table size
     const uint64_t max_chunks = bytes > kHeaderBytes ? (bytes - kHeaderBytes) / 8 : 0;
-    uint64_t grid = (max_chunks + (kDecBlock / 32) - 1) / (kDecBlock / 32);
+    uint64_t grid = (max_chunks + kDecWarps - 1) / kDecWarps;
     const uint64_t cap = (uint64_t)sms * per_sm;
     if (grid > cap)
         grid = cap;
@@ -137,7 +149,7 @@ cudaError_t launch_decode(const uint8_t *d_stream, uint64_t bytes, uint8_t *d_ou
     a.d_n = d_n;
     a.status = d_status;
     a.min_chains = (uint32_t)sms * 256u;
-    k_decode<<<(unsigned)grid, kDecBlock, 0, s>>>(a);
+    k_decode<<<(unsigned)grid, kDecBlock, kDecSmem, s>>>(a);
     return cudaGetLastError();
 }
 

@@ -10,34 +10,42 @@ namespace dec {
 constexpr int kLutBits = 12;
 constexpr int kLutSize = 1 << kLutBits;
 constexpr int kInRing = 32;   // input ring: words per lane
-constexpr int kOutRing = 32;  // output ring: 128 bytes per lane
-constexpr int kWindow = 32;   // table lookups per unchecked window
+constexpr int kOutRing = 32;  // output ring: 128 bytes per lane (one 4 KiB-aligned block per warp)
+constexpr int kWindow = 32;   // table lookups per unchecked window (an even number)
 constexpr int kCheckedWindow = 12;  // lookups per checked window
-constexpr int kMaxPerLookup = 3;
+constexpr int kMaxPerLookup = 2;
 constexpr uint32_t kFull = 0xffffffffu;
 
 // Lookup table entry for a 12-bit window (first stream bit = MSB), 32 bits:
-//   bits  0..23  the bytes of up to three whole codes in the window, first
-//                code in the low byte, zero above the last one;
-//   bits 24..29  L, the total length of those codes (1..12);
-//   bits 30..31  ns, their number (1..3);
+//   bits 24..31  s0, the byte of the first code in the window;
+//   bits 16..23  s1, the byte of the second code when it also fits, else 0;
+//   bits  8..15  8 * ns, ns = 1 or 2 codes;
+//   bits  0..7   L, the total length of those codes (1..12);
 // and 0 when the window starts with a code longer than 12 bits (or with no
-// code at all).  So entry >> 24 = L + 64 * ns: its low five bits are L, as a
-// wrap-mode funnel shift wants them, and the rest is a multiple of 64.  The
-// length of the first code alone is in a second, byte-wide table.
+// code at all).  The entry itself is the shift that drops the codes from
+// the bit buffer (the wrap-mode funnel shifts read only its low five bits,
+// and above bit 5 it is a multiple of 64), so the only work between two
+// lookups of a lane is that shift, the next window's index and address.
+// entry >> 8 is the output queue's operand: its low five bits are the shift
+// 8 * ns and the entry's top 8 * ns bits are the symbols.  The length of
+// the first code alone is in a second, byte-wide table.  The table is
+// stored in C interleaved copies ([entry][copy]); lane l reads copy l mod C.
 struct Tables {
-    const uint32_t *lut;
+    const uint32_t *lut;  // copy 0 of entry i at lut[i * copies]
+    uint32_t copies;
     const uint8_t *len0;
     const uint32_t *count;
     const uint32_t *first;
     const uint32_t *start;
     const uint8_t *sorted;
     uint32_t max_len;
+    __device__ __forceinline__ uint32_t entry(uint32_t idx) const { return lut[idx * copies]; }
 };
 
-// Shared-memory state of one stream's decode tables.
+// Shared-memory state of one stream's decode tables (C copies of the table).
+template <int C>
 struct DecodeShared {
-    uint32_t lut[kLutSize];
+    uint32_t lut[kLutSize * C];
     uint8_t len0[kLutSize];
     uint8_t len_s[256];
     uint8_t sorted[256];
@@ -62,16 +70,30 @@ struct StreamInfo {
     Tables T;
 };
 
-// table entry of the 12-bit window at the top of bh.  Volatile like the ring
-// accesses, so that the order written below (each lookup's table load
-// before the previous lookup's ring store) reaches the compiled code:
-// a load cannot be moved above a shared store it might alias.
-__device__ __forceinline__ uint32_t lut_ld(uint32_t lut_s, uint32_t bh)
+// Shared-memory rings of one warp: input [word][lane] and output [row][lane]
+// columns, the output block 4 KiB aligned (its wrap is one AND-OR).
+struct WarpRings {
+    uint32_t in_col;   // shared address of this lane's input column
+    uint32_t out_col;  // shared address of this lane's output column
+};
+
+// Table entry of the 12-bit window at the top of bh, from this lane's copy
+// (lut_l = copy base of this lane, stride = 4 * copies from the constant
+// bank).  Volatile like the ring accesses, so that the order written below
+// (each lookup's table load before the previous lookup's ring store) reaches
+// the compiled code: a load cannot be moved above a shared store it might
+// alias.
+__device__ __forceinline__ uint32_t lut_ld(uint32_t lut_l, uint32_t stride, uint32_t bh)
 {
     uint32_t v;
-    asm volatile("ld.shared.u32 %0, [%1];" : "=r"(v) : "r"(imad(bh >> (32 - kLutBits), kc[kFour], lut_s)));
+    asm volatile("ld.shared.u32 %0, [%1];"
+                 : "=r"(v)
+                 : "r"(imad(bh >> (32 - kLutBits), stride, lut_l)));
     return v;
 }
+// entry fields
+__device__ __forceinline__ uint32_t ent_len(uint32_t e) { return e & 31u; }
+__device__ __forceinline__ uint32_t ent_count(uint32_t e) { return (e >> 11) & 3u; }
 __device__ __forceinline__ uint32_t len0_at(const uint8_t *len0, uint32_t bh)
 {
     return len0[bh >> (32 - kLutBits)];
@@ -155,10 +177,14 @@ struct Reader {
     }
 };
 
-__device__ __forceinline__ void cp_async4(uint32_t dst, const uint32_t *src, bool valid)
+// 16-byte copy global -> shared, not kept in L1 (each lane streams its own
+// chunk, so nothing is read twice through L1; measured on 1 GiB text the
+// L1-allocating form took the decoder from 0.85 to 1.11 ms); bytes beyond
+// `src_bytes` (0..16) are zero
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void *src, uint32_t src_bytes)
 {
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(dst), "l"(src),
-                 "r"(valid ? 4 : 0)
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src),
+                 "r"(src_bytes)
                  : "memory");
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
@@ -168,9 +194,13 @@ __device__ __forceinline__ void cp_async_wait()
     asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
 }
 
-// Bit stream of one lane fed through its column of the warp's input ring
-// (word slot w of lane l at ring[w * 32 + l]).  Word indices are relative to
-// w0, the payload word that holds the chunk's first bit.
+// Bit stream of one lane fed through its part of the warp's input ring.
+// The ring holds, per lane, eight 16-byte cells of the payload as it lies in
+// global memory (16-byte aligned groups of four words): cell c of lane l at
+// byte c * 512 + l * 16 of the warp's 4 KiB-aligned block, so one 16-byte
+// cp.async fills a cell and the 32 lanes' cells of a row are one 512-byte
+// line of shared memory.  Words are numbered from w0, the payload word that
+// holds the chunk's first bit; `ph` is the position of w0 in its group.
 //
 // The bit buffer bh:bl holds `have` valid bits, left-aligned.  `have` is
 // kept in the low six bits of H (0 <= have <= 63); the bits above are junk:
@@ -185,70 +215,81 @@ __device__ __forceinline__ void cp_async_wait()
 // checked window reads at most 12 codes of <= 32 bits, an unchecked one at
 // most one such code and 32 of <= 12 bits plus one spare refill, and the
 // buffer holds < 64 bits).
-// Requests never reach the slot of a word that has not been read.  Each
+// Requests never reach the cell of a word that has not been read.  Each
 // top-up also asks L2 for the line 64 words past the requests.
 struct Bits {
-    uint32_t col;           // shared address of this lane's column
-    const uint32_t *words;  // payload
-    uint64_t nwords;
-    uint64_t w0;
+    uint32_t col;          // shared address of this lane's cell in row 0
+    const uint4 *groups;   // the payload's 16-byte groups (may start up to 3 words early)
+    uint64_t gend;         // virtual end: payload words + words before the payload in group 0
+    uint64_t g0;           // group holding w0
+    uint32_t ph;           // w0's position in its group
     uint32_t widx;    // next word to move into the bit buffer
-    uint32_t fidx;    // next word to request
+    uint32_t fgr;     // next group to request, counted from g0
+    uint32_t raddr;   // ring address of word widx
     uint32_t nxt;     // word widx, preloaded
     uint32_t bh, bl;  // bit buffer
     uint32_t H;       // have in the low six bits
 
-    __device__ __forceinline__ uint32_t slot(uint32_t w) const { return col + (w & (kInRing - 1)) * 128; }
-    // request words fidx .. fidx+3 (fidx is a multiple of 4, so they fill
-    // ring rows (fidx & 31) .. +3 without wrapping)
-    __device__ __forceinline__ void fetch4()
+    // ring address of word w (from w0)
+    __device__ __forceinline__ uint32_t slot(uint32_t w) const
     {
-        const uint32_t d = slot(fidx);
-        const uint64_t aw = w0 + fidx;
-        if (aw + 4 <= nwords) {
-            const uint32_t *src = words + aw;
-            cp_async4(d, src, true);
-            cp_async4(d + 128, src + 1, true);
-            cp_async4(d + 256, src + 2, true);
-            cp_async4(d + 384, src + 3, true);
-        } else {
-#pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                const bool ok = aw + j < nwords;
-                cp_async4(d + 128 * j, words + (ok ? aw + j : 0), ok);
-            }
-        }
-        fidx += 4;
+        const uint32_t v = w + ph;
+        return col + (((uint32_t)g0 + (v >> 2)) & 7u) * 512 + (v & 3u) * 4;
+    }
+    // the address after ring address a: the next word of the cell, or the
+    // first word of the next cell (a carry through the lane bits, set to all
+    // ones, into the cell number), within the lane's eight cells
+    __device__ __forceinline__ uint32_t next_slot(uint32_t a, uint32_t k) const
+    {
+        return (imad(k, kc[kFour], a | 0x1f0u) & 0xe0cu) | col;
+    }
+    // request group fgr (four words), zero-filled past the payload
+    __device__ __forceinline__ void fetch()
+    {
+        const uint64_t g = g0 + fgr;
+        const uint32_t d = col + ((uint32_t)g & 7u) * 512;
+        const uint64_t vw = 4 * g;  // first virtual word of the group
+        uint32_t bytes = 16;
+        if (vw + 4 > gend)
+            bytes = vw >= gend ? 0u : (uint32_t)(gend - vw) * 4;
+        cp_async16(d, bytes ? (const void *)(groups + g) : (const void *)groups, bytes);
+        ++fgr;
         cp_async_commit();
     }
     __device__ __forceinline__ void top_up()
     {
-        while (fidx - widx <= (uint32_t)kInRing - 4)
-            fetch4();
-        const uint64_t pf = w0 + fidx + 64;
-        if (pf < nwords)
-            asm volatile("prefetch.global.L2 [%0];" ::"l"(words + pf));
+        while (4 * fgr - (widx + ph) <= (uint32_t)kInRing - 4)
+            fetch();
+        const uint64_t pf = 4 * (g0 + fgr) + 64;
+        if (pf < gend)
+            asm volatile("prefetch.global.L2 [%0];" ::"l"(groups + (pf >> 2)));
     }
-    // start at bit `pbit` counted from the first bit of word w0
+    // start at bit `pbit` counted from the first bit of payload word word0;
+    // column: this lane's cell in row 0 of a 4 KiB-aligned block
     __device__ __forceinline__ void init(uint32_t column, const uint32_t *pay, uint64_t nw,
                                          uint64_t word0, uint32_t pbit)
     {
         col = column;
-        words = pay;
-        nwords = nw;
-        w0 = word0;
+        const uint32_t lead = (uint32_t)(reinterpret_cast<uintptr_t>(pay) >> 2) & 3u;
+        groups = reinterpret_cast<const uint4 *>(pay - lead);
+        gend = nw + lead;
+        const uint64_t v0 = word0 + lead;
+        g0 = v0 >> 2;
+        ph = (uint32_t)(v0 & 3);
         widx = pbit >> 5;
-        fidx = widx & ~3u;
+        fgr = (widx + ph) >> 2;
 #pragma unroll
         for (int r = 0; r < kInRing / 4; ++r)
-            fetch4();
+            fetch();
         cp_async_wait<0>();
         const uint32_t sh = pbit & 31;
-        bh = lds(slot(widx)) << sh;
+        raddr = slot(widx);
+        bh = lds(raddr) << sh;
         bl = 0;
         H = 32 - sh;
         ++widx;
-        nxt = lds(slot(widx));
+        raddr = next_slot(raddr, 1u);
+        nxt = lds(raddr);
     }
     __device__ __forceinline__ uint32_t have() const { return H & 63u; }
     // stream bits consumed so far, counted from the first bit of word w0
@@ -264,10 +305,11 @@ struct Bits {
         bl = imad(k, __funnelshift_r(0u, nxt, H), bl);  // nxt << (32 - have), 0 at have = 0
         H = imad(k, kc[k32], H);
         widx = imad(k, kc[kOne], widx);
-        lds_if(k, imad(widx & (kInRing - 1), kc[k128], col), nxt);
+        raddr = next_slot(raddr, k);
+        lds_if(k, raddr, nxt);
     }
-    // drop the L = (t & 31) bits of t = entry >> 24 (1 <= L <= 31); the rest
-    // of t is a multiple of 64 and never reaches have
+    // drop the L = (t & 31) bits of t (a table entry: 1 <= L <= 12, 0 for a
+    // long code); the rest of t is a multiple of 64 and never reaches have
     __device__ __forceinline__ void consume_t(uint32_t t)
     {
         bh = __funnelshift_l(bl, bh, t);
@@ -283,46 +325,59 @@ struct Bits {
     }
 };
 
-// Output bytes of one lane assembled in a register and stored to its column
-// of the warp's output ring one completed word at a time (row r of lane l at byte
-// r * 128 + 4 * l of the warp's ring; the ring holds kOutRing words).
-// `lo` holds the bytes of the word being filled at its low end, `sh` = 8 *
-// (bytes in lo) and R = 128 * (number of the word being filled), of which
-// the row is R mod (128 * kOutRing).  Bytes above the filled ones are zero,
-// so appending is adding.
-struct OutWord {
-    uint32_t col;  // shared address of this lane's column
-    uint32_t lo, sh, R;
+// Output bytes of one lane: a 64-bit queue in registers, oldest byte
+// highest (big-endian), fed by the table entries' funnel shifts, and the
+// lane's column of the warp's output ring (row r of lane l at byte
+// r * 128 + 4 * l of the warp's 4 KiB-aligned block; kOutRing rows).  `P`
+// counts the pending bits (a multiple of 8, < 64) in its low bits; adding a
+// whole table entry adds 8 * ns there and junk only from bit 8 up.  `addr`
+// is the ring slot of the word being filled.  store() writes that word every
+// time it is called -- the four oldest pending bytes when P >= 32, else a
+// partial word that a later store overwrites -- and moves to the next row
+// when the word was complete, so it needs no predicate and no branch.
+struct OutQ {
+    uint32_t hi, lo;  // pending bytes in the low P bits of hi:lo
+    uint32_t P;
+    uint32_t addr;  // ring slot of the word being filled
+    uint32_t base;  // 4 KiB-aligned base of the warp's output block
+    uint32_t col;   // this lane's column (row 0)
 
+    // the queue at output position q (the bytes of q's word before q are
+    // placeholders, never flushed)
     __device__ __forceinline__ void start(uint32_t column, uint32_t q)
     {
         col = column;
-        lo = 0;
-        sh = (q & 3u) * 8;
-        R = (q >> 2) * 128;
+        base = column & ~0xfffu;
+        hi = lo = 0;
+        P = (q & 3u) * 8;
+        addr = column + ((q >> 2) & (kOutRing - 1)) * 128;
     }
-    __device__ __forceinline__ uint32_t addr() const
+    // append the top 8 * ns bits of table entry e (s = e >> 8: its low five
+    // bits are 8 * ns, its higher ones land in P's junk)
+    __device__ __forceinline__ void merge(uint32_t e)
     {
-        return imad(R & ((kOutRing - 1) * 128), kc[kOne], col);
+        const uint32_t sft = e >> 8;
+        hi = __funnelshift_l(lo, hi, sft);
+        lo = __funnelshift_l(e, lo, sft);
+        P = imad(sft, kc[kOne], P);
     }
-    // append the ns bytes of y (zero above them); a completed word is stored
-    __device__ __forceinline__ void emit(uint32_t y, uint32_t ns)
+    __device__ __forceinline__ void store()
     {
-        const uint32_t hi = __funnelshift_l(y, 0u, sh);  // y >> (32 - sh), 0 at sh = 0
-        lo = imad(y, 1u << sh, lo);                      // lo | y << sh
-        sh = imad(ns, kc[kEight], sh);
-        const uint32_t full = sh >> 5;                   // the word is complete
-        sts_if(full, addr(), lo);
-        lo = imad(full, imad(lo, kc[kMinus1], hi), lo);  // full ? hi : lo
-        R = imad(full, kc[k128], R);
-        sh = imad(full, kc[kMinus32], sh);
+        const uint32_t w = __funnelshift_r(lo, hi, P);  // bits [P - 32, P) when P >= 32
+        sts(addr, __byte_perm(w, 0u, 0x0123));
+        const uint32_t f = P & 32u;
+        addr = ((imad(f, kc[kFour], addr)) & 0xfffu) | base;
+        P = imad(f, kc[kMinus1], P);
     }
-    // output position, given the position q0 and value R0 of R at some
-    // earlier point
-    __device__ __forceinline__ uint32_t pos_from(uint32_t q0, uint32_t R0) const
+    // the pending bytes (< 4) as the word being filled, for the final flush
+    __device__ __forceinline__ void store_partial()
     {
-        return ((q0 >> 2) + ((R - R0) >> 7)) * 4 + (sh >> 3);
+        const uint32_t p = P & 63u;
+        sts(addr, __byte_perm(__funnelshift_lc(0u, lo, 32u - p), 0u, 0x0123));
     }
+    // ring row of the word being filled (0..kOutRing-1) and pending bytes
+    __device__ __forceinline__ uint32_t row() const { return ((addr - col) & 0xfffu) >> 7; }
+    __device__ __forceinline__ uint32_t pending() const { return (P & 63u) >> 3; }
     __device__ __forceinline__ uint32_t byte_at(uint32_t b) const
     {
         return lds_u8(col + ((b >> 2) & (kOutRing - 1)) * 128 + (b & 3u));
@@ -347,8 +402,8 @@ __device__ __forceinline__ void count_codes(const Tables &T, const uint8_t *pay,
         while (pos < stop) {
             rd.refill();
             const uint32_t idx = (uint32_t)(rd.buf >> (64 - kLutBits));
-            const uint32_t ent = T.lut[idx];
-            uint32_t L = (ent >> 24) & 31u, ns = ent >> 30;
+            const uint32_t ent = T.entry(idx);
+            uint32_t L = ent_len(ent), ns = ent_count(ent);
             if (ent == 0) {
                 uint32_t sym;
                 if (!long_code(T, (uint32_t)(rd.buf >> 32), L, sym))
@@ -439,7 +494,7 @@ __device__ __forceinline__ void settle_segment(const Tables &T, const uint8_t *p
         rd.refill();
         const uint32_t idx = (uint32_t)(rd.buf >> (64 - kLutBits));
         uint32_t L = T.len0[idx];  // first code only: every boundary matters
-        if (T.lut[idx] == 0) {
+        if (T.entry(idx) == 0) {
             uint32_t sym;
             if (!long_code(T, (uint32_t)(rd.buf >> 32), L, sym))
                 L = 1;
@@ -456,10 +511,10 @@ __device__ __forceinline__ void settle_segment(const Tables &T, const uint8_t *p
 // and the header errors).  `scratch` is shared memory for kLutSize u16 that
 // is free while the tables are built.  Returns true when there are chunks to
 // decode.
-template <int NT>
+template <int NT, int C>
 __device__ __forceinline__ bool prepare(const uint8_t *stream_in, uint64_t bytes, uint8_t *out,
                                         uint64_t cap, unsigned long long *d_n, int32_t *status,
-                                        bool reporter, DecodeShared &sh, uint16_t *scratch,
+                                        bool reporter, DecodeShared<C> &sh, uint16_t *scratch,
                                         StreamInfo &si)
 {
     const int tid = threadIdx.x;
@@ -562,29 +617,24 @@ __device__ __forceinline__ bool prepare(const uint8_t *stream_in, uint64_t bytes
         scratch[v] = (uint16_t)ent;
     }
     __syncthreads();
-    // pass 2: append the following codes while they fit in the window
+    // pass 2: append the second code when it also fits in the window
     for (int v = tid; v < kLutSize; v += NT) {
         const uint32_t e0 = scratch[v];
         uint32_t ent = 0, first_len = 0;
         if (e0) {
             const uint32_t L0 = e0 >> 8;
-            uint32_t syms = e0 & 0xffu, tot = L0, ns = 1;
-#pragma unroll
-            for (int k = 1; k < kMaxPerLookup; ++k) {
-                if (ns == (uint32_t)k && tot < (uint32_t)kLutBits) {
-                    const uint32_t e1 = scratch[((uint32_t)v << tot) & (kLutSize - 1)];
-                    const uint32_t L1 = e1 >> 8;
-                    if (e1 && tot + L1 <= (uint32_t)kLutBits) {
-                        syms |= (e1 & 0xffu) << (8 * k);
-                        tot += L1;
-                        ++ns;
-                    }
-                }
+            ent = ((e0 & 0xffu) << 24) | (8u << 8) | L0;
+            if (L0 < (uint32_t)kLutBits) {
+                const uint32_t e1 = scratch[((uint32_t)v << L0) & (kLutSize - 1)];
+                const uint32_t L1 = e1 >> 8;
+                if (e1 && L0 + L1 <= (uint32_t)kLutBits)
+                    ent = ((e0 & 0xffu) << 24) | ((e1 & 0xffu) << 16) | (16u << 8) | (L0 + L1);
             }
-            ent = syms | (tot << 24) | (ns << 30);
             first_len = L0;
         }
-        sh.lut[v] = ent;
+#pragma unroll
+        for (int c = 0; c < C; ++c)
+            sh.lut[v * C + c] = ent;
         sh.len0[v] = (uint8_t)first_len;
     }
     __syncthreads();
@@ -604,6 +654,7 @@ __device__ __forceinline__ bool prepare(const uint8_t *stream_in, uint64_t bytes
     si.offs = offs;
     si.pay = pay;
     si.T.lut = sh.lut;
+    si.T.copies = C;
     si.T.len0 = sh.len0;
     si.T.count = sh.count;
     si.T.first = sh.first;
@@ -623,8 +674,7 @@ __device__ __forceinline__ uint32_t pick_split(uint64_t chunks, uint32_t min_cha
 }
 
 // Store the complete 16-byte groups of [fl, q) from the output ring.
-__device__ __forceinline__ void flush_groups(uint8_t *ob, const OutWord &ow, uint32_t &fl,
-                                             uint32_t q)
+__device__ __forceinline__ void flush_groups(uint8_t *ob, const OutQ &ow, uint32_t &fl, uint32_t q)
 {
     uint32_t hs = fl & ~15u;
     while (q >= hs + 16) {
@@ -642,23 +692,24 @@ __device__ __forceinline__ void flush_groups(uint8_t *ob, const OutWord &ow, uin
 }
 
 // Decode warp task `task` of stream si with S lanes per chunk (32/S chunks
-// per warp).  in_col / out_col: this lane's column of the warp's rings.
-// Returns true (warp-uniform) if the stream is corrupt.  kWhole: S == 1, one
-// lane per chunk, compiled without the count / settle / scan phases.
+// per warp).  in_col / out_col: shared addresses of this lane's columns of
+// the warp's rings (the output block 4 KiB aligned).  Returns true
+// (warp-uniform) if the stream is corrupt.  kWhole: S == 1, one lane per
+// chunk, compiled without the count / settle / scan phases.
 template <bool kWhole>
 __device__ __forceinline__ bool decode_task_s(const StreamInfo &si, uint32_t S_arg, uint64_t task,
-                                              uint32_t *in_col, uint32_t *out_col)
+                                              uint32_t in_s, uint32_t out_s)
 {
     const uint32_t S = kWhole ? 1u : S_arg;
     const Tables &T = si.T;
-    const uint32_t lut_s = smem_u32(T.lut);
+    const int lane = threadIdx.x & 31;
+    const uint32_t lut_l = smem_u32(T.lut) + ((uint32_t)lane & (T.copies - 1)) * 4;
+    const uint32_t stride = T.copies == 1 ? kc[kFour] : T.copies == 2 ? kc[kEight] : kc[k16];
     const uint8_t *len0 = T.len0;
-    const uint32_t in_s = smem_u32(in_col), out_s = smem_u32(out_col);
     const uint64_t n = si.n, chunks = si.chunks, pbits = si.pbits, pay_words = si.pay_words;
     const uint32_t cs = si.cs;
     const uint64_t *offs = si.offs;
     const uint8_t *pay = si.pay;
-    const int lane = threadIdx.x & 31;
     const uint32_t G = 32 / S;
     const uint32_t k = (uint32_t)lane & (S - 1);
     const uint32_t grp = (uint32_t)lane / S;
@@ -719,21 +770,21 @@ __device__ __forceinline__ bool decode_task_s(const StreamInfo &si, uint32_t S_a
             }
         }
         // 1b. windows of table lookups, several codes per lookup
-        uint32_t cnt = 0;
+        uint32_t cnt8 = 0;  // 8 x codes
         while (__any_sync(kFull, act)) {
-            // an unchecked window reads at most one long code plus 16 table
-            // lookups of <= 12 bits
+            // an unchecked window reads at most one long code plus kWindow
+            // table lookups of <= 12 bits
             const bool easy = stop - pos >= 32 + kLutBits * kWindow;
             if (__all_sync(kFull, easy || !act)) {
                 if (act) {
                     rs.refill();
-                    if (lut_ld(lut_s, rs.bh) == 0) {  // a long code (rare)
+                    if (lut_ld(lut_l, stride, rs.bh) == 0) {  // a long code (rare)
                         uint32_t L, sym;
                         if (!long_code(T, rs.bh, L, sym))
                             L = 1;
                         rs.consume(L);
                         rs.refill();
-                        ++cnt;
+                        cnt8 += 8;
                     }
                 }
 #pragma unroll
@@ -743,9 +794,9 @@ __device__ __forceinline__ bool decode_task_s(const StreamInfo &si, uint32_t S_a
                             rs.refill();  // two lookups use at most 24 of >= 32 bits
                         // a long code's entry is all zero: the lane stays on
                         // it for the rest of the window
-                        const uint32_t ent = lut_ld(lut_s, rs.bh);
-                        rs.consume_t(ent >> 24);
-                        cnt += ent >> 30;
+                        const uint32_t ent = lut_ld(lut_l, stride, rs.bh);
+                        rs.consume_t(ent);
+                        cnt8 += (ent >> 8) & 24u;
                     }
                 }
             } else {
@@ -760,7 +811,7 @@ __device__ __forceinline__ bool decode_task_s(const StreamInfo &si, uint32_t S_a
                                 L = 1;
                         }
                         rs.consume(L);
-                        ++cnt;
+                        cnt8 += 8;
                         act = rs.bitpos() - b0 < stop;
                     }
                 }
@@ -775,7 +826,7 @@ __device__ __forceinline__ bool decode_task_s(const StreamInfo &si, uint32_t S_a
         }
         cp_async_wait<0>();  // the ring is reused below
         if (work && k + 1 < S && g < stop) {
-            cnt1 += cnt;
+            cnt1 += cnt8 >> 3;
             e1 = rs.bitpos() - b0;
         }
     }
@@ -816,7 +867,7 @@ __device__ __forceinline__ bool decode_task_s(const StreamInfo &si, uint32_t S_a
     // 4. decode on the true path and write the bytes
     {
         Bits rs = {};
-        OutWord ow = {};
+        OutQ ow;
         bool act = todo > 0;
         uint8_t *const ob = si.out + c * cs;  // chunk output, 16-byte aligned
         const uint32_t qend = O + todo;
@@ -826,17 +877,16 @@ __device__ __forceinline__ bool decode_task_s(const StreamInfo &si, uint32_t S_a
             rs.init(in_s, pw, pay_words, cbase >> 5, b0 + entry);
         while (__any_sync(kFull, act)) {
             // far from the segment's end a window needs no per-code checks:
-            // at most 3 * 16 symbols and 16 x 32 bits.  The unchecked window
-            // runs only when every lane of the warp is in that state, so it
-            // needs no per-lane predicate either.
-            // A window reads at most one long code (resolved first) plus 16
-            // table lookups of <= 12 bits and 3 symbols each.
+            // at most 2 * kWindow symbols and kWindow x 12 bits, plus one
+            // long code.  The unchecked window runs only when every lane of
+            // the warp is in that state, so it needs no per-lane predicate
+            // either.
             const bool easy = act && qend - q >= 1 + kMaxPerLookup * kWindow &&
                               lim - pos >= 32 + kLutBits * kWindow;
-            const uint32_t q0 = q, R0 = ow.R;
+            const uint32_t q0 = q, row0 = ow.row(), p0 = ow.pending();
             if (__all_sync(kFull, easy)) {
                 rs.refill();
-                if (lut_ld(lut_s, rs.bh) == 0) {  // a long code (rare)
+                if (lut_ld(lut_l, stride, rs.bh) == 0) {  // a long code (rare)
                     uint32_t L = 0, sym = 0;
                     if (!long_code(T, rs.bh, L, sym)) {
                         bad = true;  // nothing more is flushed
@@ -844,68 +894,71 @@ __device__ __forceinline__ bool decode_task_s(const StreamInfo &si, uint32_t S_a
                     }
                     rs.consume(L);
                     rs.refill();
-                    ow.emit(sym, 1);
+                    ow.merge((sym << 24) | (8u << 8));
+                    ow.store();
                 }
                 // A long code's entry is all zero, so it consumes and emits
                 // nothing: the lane stays on it for the rest of the window
-                // and resolves it at the start of the next.  Software
+                // and resolves it at the start of the next.  Pairs of
+                // lookups: a refill (>= 32 bits) serves both, as two lookups
+                // use at most 24 bits, and one store serves both, as the
+                // queue then holds at most 3 + 2 * 2 bytes.  Software
                 // pipelined: lookup j+1's table load is issued before lookup
-                // j's output is appended.
-                // Pairs of lookups: a refill (>= 32 bits) serves both, as
-                // two lookups use at most 24 bits.  The last pair's refill
-                // and table load for a lookup beyond the window are
-                // harmless (one more word at most, within the ring bound).
-                uint32_t ent = lut_ld(lut_s, rs.bh);
+                // j's bytes are queued.  The last pair's refill and table
+                // load for a lookup beyond the window are harmless (one more
+                // word at most, within the ring bound).
+                uint32_t ent = lut_ld(lut_l, stride, rs.bh);
 #pragma unroll 4
                 for (int p = 0; p < kWindow / 2; ++p) {
-                    const uint32_t t0 = ent >> 24;
-                    rs.consume_t(t0);
-                    const uint32_t ent1 = lut_ld(lut_s, rs.bh);
-                    ow.emit(imad(t0, kc[kMinusTop8], ent), t0 >> 6);  // the symbol bytes
-                    const uint32_t t1 = ent1 >> 24;
-                    rs.consume_t(t1);
+                    rs.consume_t(ent);
+                    const uint32_t ent1 = lut_ld(lut_l, stride, rs.bh);
+                    ow.merge(ent);
+                    rs.consume_t(ent1);
                     rs.refill();
-                    ent = lut_ld(lut_s, rs.bh);
-                    ow.emit(imad(t1, kc[kMinusTop8], ent1), t1 >> 6);
+                    ent = lut_ld(lut_l, stride, rs.bh);
+                    ow.merge(ent1);
+                    ow.store();
                 }
             } else {
 #pragma unroll 1
                 for (int j = 0; j < kCheckedWindow; ++j) {
                     if (act) {
                         rs.refill();
-                        const uint32_t ent = lut_ld(lut_s, rs.bh);
-                        uint32_t L, ns8, y;
+                        const uint32_t ent = lut_ld(lut_l, stride, rs.bh);
+                        uint32_t L, ns, y;
                         if (ent == 0) {
-                            rs.refill();
                             uint32_t sym = 0;
                             L = 0;
                             if (!long_code(T, rs.bh, L, sym))
                                 bad = true;
-                            ns8 = 8;
-                            y = sym;
+                            ns = 1;
+                            y = (sym << 24) | (8u << 8);
                         } else {
-                            L = (ent >> 24) & 31u;
-                            ns8 = (ent >> 30) << 3;
-                            y = ent & 0xffffffu;
-                            if (q + (ns8 >> 3) > qend || pos + L > lim) {  // first code only
+                            L = ent_len(ent);
+                            ns = ent_count(ent);
+                            y = ent;
+                            if (q + ns > qend || pos + L > lim) {  // first code only
                                 L = len0_at(len0, rs.bh);
-                                ns8 = 8;
-                                y &= 0xffu;
+                                ns = 1;
+                                y = (ent & 0xff000000u) | (8u << 8);
                             }
                         }
                         if (pos + L > lim)
                             bad = true;
                         if (!bad) {
                             rs.consume(L);
-                            ow.emit(y, ns8 >> 3);
-                            q += ns8 >> 3;
+                            ow.merge(y);
+                            ow.store();
+                            q += ns;
                             pos += L;
                         }
                         act = !bad && q < qend;
                     }
                 }
             }
-            q = ow.pos_from(q0, R0);
+            // bytes queued in this window: whole rows stored plus the change
+            // in pending bytes (a window moves fewer than kOutRing rows)
+            q = q0 + 4 * ((ow.row() - row0) & (kOutRing - 1)) + ow.pending() - p0;
             pos = rs.bitpos() - b0;
             if (act) {
                 act = q < qend;
@@ -919,7 +972,7 @@ __device__ __forceinline__ bool decode_task_s(const StreamInfo &si, uint32_t S_a
         cp_async_wait<0>();
         if (!bad) {
             if (todo)
-                sts(ow.addr(), ow.lo);  // bytes carried over by the last emit
+                ow.store_partial();  // the bytes of the word being filled
             for (uint32_t b = fl; b < q; ++b)
                 ob[b] = (uint8_t)ow.byte_at(b);
             if (todo && final_seg && c + 1 < chunks && pos != lim)
@@ -930,10 +983,10 @@ __device__ __forceinline__ bool decode_task_s(const StreamInfo &si, uint32_t S_a
 }
 
 __device__ __forceinline__ bool decode_task(const StreamInfo &si, uint32_t S, uint64_t task,
-                                            uint32_t *in_col, uint32_t *out_col)
+                                            uint32_t in_s, uint32_t out_s)
 {
-    return S == 1 ? decode_task_s<true>(si, 1, task, in_col, out_col)
-                  : decode_task_s<false>(si, S, task, in_col, out_col);
+    return S == 1 ? decode_task_s<true>(si, 1, task, in_s, out_s)
+                  : decode_task_s<false>(si, S, task, in_s, out_s);
 }
 
 }  // namespace dec

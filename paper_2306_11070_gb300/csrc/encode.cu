@@ -94,20 +94,14 @@ cudaError_t launch_encode(const uint8_t *d_in, uint64_t n, const huff_codebook_t
                           void *d_ws, const uint16_t *d_unit_hist, int32_t *d_status,
                           cudaStream_t s)
 {
-    static int per_sm = 0;
-    cudaError_t err;
-    if (per_sm == 0) {
-        err = cudaFuncSetAttribute(k_encode, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                   kEncSmemBytes);
-        if (err != cudaSuccess)
-            return err;
-        err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_encode, kEncBlock,
-                                                            kEncSmemBytes);
-        if (err != cudaSuccess)
-            return err;
-        if (per_sm < 1)
-            per_sm = 1;
-    }
+    static KernelSetup setup;
+    int per_sm = 0;
+    cudaError_t err = kernel_setup(setup, (const void *)k_encode, kEncBlock, kEncSmemBytes, &per_sm);
+    if (err != cudaSuccess)
+        return err;
+    const int sms = device_sm_count();
+    if (sms < 1)
+        return cudaErrorInvalidDevice;
     const uint64_t units = (n + kUnitSymbols - 1) / kUnitSymbols;
     uint8_t *ws = static_cast<uint8_t *>(d_ws);
     uint32_t *unit_bits = reinterpret_cast<uint32_t *>(ws);
@@ -129,7 +123,7 @@ cudaError_t launch_encode(const uint8_t *d_in, uint64_t n, const huff_codebook_t
     a.out_cap = out_cap;
     a.out_bytes = d_out_bytes;
     a.status = d_status;
-    uint64_t grid = (uint64_t)device_sm_count() * per_sm;
+    uint64_t grid = (uint64_t)sms * per_sm;
     const uint64_t want = (units + kEncWarps - 1) / kEncWarps;
     if (grid > want)
         grid = want;

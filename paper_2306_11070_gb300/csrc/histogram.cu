@@ -67,16 +67,16 @@ cudaError_t launch_histogram(const uint8_t *d_in, uint64_t n, unsigned long long
     cudaError_t err = cudaMemsetAsync(d_hist, 0, 256 * sizeof(unsigned long long), s);
     if (err != cudaSuccess || n == 0)
         return err;
-    static int per_sm = 0;
-    if (per_sm == 0) {
-        err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_histogram, kHistBlock, 0);
-        if (err != cudaSuccess)
-            return err;
-        if (per_sm < 1)
-            per_sm = 1;
-    }
+    static KernelSetup setup;
+    int per_sm = 0;
+    err = kernel_setup(setup, (const void *)k_histogram, kHistBlock, 0, &per_sm);
+    if (err != cudaSuccess)
+        return err;
+    const int sms = device_sm_count();
+    if (sms < 1)
+        return cudaErrorInvalidDevice;
     const uint64_t units = (n + kUnitSymbols - 1) / kUnitSymbols;
-    const uint64_t cap = (uint64_t)device_sm_count() * per_sm;
+    const uint64_t cap = (uint64_t)sms * per_sm;
     const uint64_t grid = units < cap ? units : cap;
     k_histogram<<<(unsigned)grid, kHistBlock, 0, s>>>(d_in, n, d_hist, d_unit_hist);
     return cudaGetLastError();

@@ -1,7 +1,10 @@
 // Shared definitions of the CUDA side of libhuff (kernels and C ABI layer).
 #pragma once
 
+#include <atomic>
 #include <cstdint>
+#include <mutex>
+
 #include <cuda_runtime.h>
 
 #include "huff.h"
@@ -51,7 +54,7 @@ __device__ __forceinline__ void st_volatile_u64(unsigned long long *p, uint64_t 
                  : "memory");
 }
 
-// ---- shared-memory barriers and bulk (TMA) copies -------------------------
+// ---- shared-memory addresses ----------------------------------------------
 __device__ __forceinline__ uint32_t smem_u32(const void *p)
 {
     return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -64,9 +67,9 @@ __device__ __forceinline__ uint32_t smem_u32(const void *p)
 // shifts, logic ops and compares, at half a warp per cycle) to the work only
 // it can do.  The values are not visible to the compiler, so it cannot turn
 // the multiplies back into shifts and adds.
-enum { kOne, kMinus1, kFour, kEight, k32, kMinus32, k128, kMinusTop8, kNumConst };
+enum { kOne, kMinus1, kFour, kEight, k32, kMinus32, k128, kMinusTop8, k16, kNumConst };
 static __constant__ uint32_t kc[kNumConst] = {1u, 0xffffffffu, 4u, 8u, 32u, 0xffffffe0u,
-                                              128u, 0xff000000u};
+                                              128u, 0xff000000u, 16u};
 __device__ __forceinline__ uint32_t imad(uint32_t a, uint32_t b, uint32_t c) { return a * b + c; }
 
 // Shared-memory accesses by 32-bit shared address.  The rings are accessed
@@ -113,63 +116,6 @@ __device__ __forceinline__ void stg64_if(uint32_t k, uint64_t *p, uint64_t v)
                  : "memory");
 }
 
-__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count)
-{
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count)
-                 : "memory");
-}
-
-__device__ __forceinline__ void fence_mbar_init()
-{
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-}
-
-__device__ __forceinline__ void fence_proxy_async_smem()
-{
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-}
-
-// One arrival that also announces `bytes` of asynchronous transfer.
-__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t bytes)
-{
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
-                 "r"(bytes)
-                 : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity)
-{
-    uint32_t done;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(done)
-        : "r"(smem_u32(bar)), "r"(parity)
-        : "memory");
-    return done != 0;
-}
-
-// Bounded wait for the phase with the given parity; false on timeout.
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity)
-{
-    for (uint32_t spin = 0; spin < kSpinLimit; ++spin)
-        if (mbar_try_wait(bar, parity))
-            return true;
-    return false;
-}
-
-// 1-D bulk copy global -> shared through the TMA unit; completion is counted
-// on `bar`.  Both addresses 16-byte aligned, bytes a multiple of 16.
-__device__ __forceinline__ void tma_load_1d(void *dst, const void *src, uint32_t bytes, uint64_t *bar)
-{
-    asm volatile(
-        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
-            "r"(smem_u32(dst)),
-        "l"(src), "r"(bytes), "r"(smem_u32(bar))
-        : "memory");
-}
-
 // ---- stream header checks --------------------------------------------------
 __host__ __device__ __forceinline__ bool chunk_symbols_valid(uint32_t cs)
 {
@@ -181,8 +127,22 @@ __host__ __device__ __forceinline__ uint64_t ceil_div_u64(uint64_t a, uint64_t b
     return a / b + (a % b != 0);
 }
 
-// Launch helpers defined in api.cu.
-int device_sm_count();
+// Launch helpers defined in api.cu.  Devices are numbered below
+// kMaxDevices; a call made with a higher ordinal current fails with
+// cudaErrorInvalidDevice.
+constexpr int kMaxDevices = 64;
+int current_device();  // -1 if unreadable or not below kMaxDevices
+int device_sm_count();  // SMs of the current device, 0 on error
+
+// One kernel's launch set-up, done once per device under a mutex (several
+// host threads may launch at once): the dynamic shared-memory limit when the
+// kernel needs more than the 48 KiB default, then the resident CTAs per SM.
+struct KernelSetup {
+    std::mutex mu;
+    std::atomic<int> per_sm[kMaxDevices];
+};
+cudaError_t kernel_setup(KernelSetup &ks, const void *func, int block, size_t dyn_smem,
+                         int *per_sm);
 
 }  // namespace huff
 

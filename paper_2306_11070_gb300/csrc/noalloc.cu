@@ -33,9 +33,8 @@ constexpr uint64_t kScratchBytes = ((4 * kMaxUnits + 255) & ~255ull) +
 
 static __device__ __align__(256) unsigned char g_encode_scratch[kScratchBytes];
 
-constexpr int kMaxDevices = 64;
 std::mutex g_setup_mutex;
-void *g_scratch_ptr[kMaxDevices] = {};
+void *g_scratch_ptr[huff::kMaxDevices] = {};
 
 // Device address of the scratch array for the current device (set up once).
 huff_status_t scratch_address(void **out)
@@ -43,7 +42,7 @@ huff_status_t scratch_address(void **out)
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess)
         return HUFF_ERR_CUDA;
-    if (dev < 0 || dev >= kMaxDevices)
+    if (dev < 0 || dev >= huff::kMaxDevices)
         return HUFF_ERR_UNSUPPORTED;
     std::lock_guard<std::mutex> lock(g_setup_mutex);
     if (!g_scratch_ptr[dev]) {

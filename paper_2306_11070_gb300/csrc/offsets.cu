@@ -237,6 +237,8 @@ cudaError_t launch_unit_offsets(const uint8_t *d_in, uint64_t n, const uint16_t 
     if (units == 0)
         return cudaMemsetAsync(d_unit_off, 0, sizeof(unsigned long long), s);
     const int sms = device_sm_count();
+    if (sms < 1)
+        return cudaErrorInvalidDevice;
     if (d_unit_hist) {
         uint64_t grid = (units + (kDotBlock / 32) - 1) / (kDotBlock / 32);
         if (grid > (uint64_t)sms * 8)
@@ -244,15 +246,12 @@ cudaError_t launch_unit_offsets(const uint8_t *d_in, uint64_t n, const uint16_t 
         k_unit_bits_hist<<<(unsigned)grid, kDotBlock, 0, s>>>(d_unit_hist, units, d_cb, d_unit_bits,
                                                               d_status);
     } else {
-        static int per_sm = 0;
-        if (per_sm == 0) {
-            cudaError_t err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_unit_bits_input,
-                                                                            kCountBlock, 0);
-            if (err != cudaSuccess)
-                return err;
-            if (per_sm < 1)
-                per_sm = 1;
-        }
+        static KernelSetup setup;
+        int per_sm = 0;
+        const cudaError_t err =
+            kernel_setup(setup, (const void *)k_unit_bits_input, kCountBlock, 0, &per_sm);
+        if (err != cudaSuccess)
+            return err;
         uint64_t grid = units < (uint64_t)sms * per_sm ? units : (uint64_t)sms * per_sm;
         k_unit_bits_input<<<(unsigned)grid, kCountBlock, 0, s>>>(d_in, n, d_cb, d_unit_bits,
                                                                  d_status);
