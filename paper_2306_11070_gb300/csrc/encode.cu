@@ -2,26 +2,29 @@
 // over Method 2's segments, which become chunks of `cs` symbols with stored
 // bit offsets.
 //
-// Design (one pass over the input, HBM-bound: n bytes read + payload
-// written):
+// Design (one pass over the input, n bytes read + payload written):
 //  - The bit offset of every 16 KiB unit is known before this kernel starts
 //    (offsets.cu: unit histograms or unit counts, then a scan), so no warp
-//    ever waits on another.  Each warp encodes whole units by itself in 32
-//    steps of 512 symbols; the loop has no CTA barrier at all.
-//  - A step: every lane loads its 16 bytes (one coalesced 16-byte load,
-//    issued one step ahead), looks up the 16 table entries and keeps them in
-//    registers, a warp scan of the code-length sums gives every lane its bit
-//    position, the lanes pack their codes into the warp's word-aligned buffer
-//    in shared memory, and the warp writes the whole words with coalesced
-//    stores.  The partial last word is carried in a register into the next
-//    step.
+//    ever waits on another.  Each warp encodes whole units by itself in 16
+//    steps of 1024 symbols; the loop has no CTA barrier at all.
+//  - A step: every lane loads its 32 bytes (two 16-byte loads, issued one
+//    step ahead), looks up the 32 table entries and keeps them in registers,
+//    sums them (the low 10 bits of a sum of entries are the sum of their
+//    lengths), a warp scan of the sums gives every lane its bit position,
+//    the lanes pack their codes into the warp's word buffer in shared
+//    memory, and the warp writes the whole words with coalesced stores.  The
+//    partial last word is carried in a register into the next step.
+//  - Packing: two funnel shifts per code into a 64-bit register; every
+//    floor(32 / longest) codes at most one word completes, and a plain store
+//    writes the last completed word (see pack32 for why every word ends with
+//    the right value without atomics); after a warp barrier each lane ORs
+//    its last partial word into the next lane's first word.
 //  - Code table in shared memory, replicated per lane ([byte][lane]), so
 //    the 32 lookups of a warp never collide in a bank.  Entry =
-//    (code << (32 - len)) | len for codes up to 24 bits: the funnel shifts
-//    take the length from the entry's low 5 bits, so appending a code is two
-//    SHF instructions, and the emit check runs once per floor(32 / longest)
-//    codes.  Longer codes (up to 32 bits) use split code / length tables and
-//    a 64-bit accumulator.
+//    (code << (32 - len)) | len for codes up to 22 bits: the funnel shifts
+//    take the length from the entry's low 5 bits.  Longer codes (up to 32
+//    bits) use split code / length tables, 16 symbols per lane and a 64-bit
+//    accumulator.
 //  - The word a unit shares with the unit before it is completed by the later
 //    unit: it re-codes the last <= 31 bits of its predecessor from the 32
 //    input bytes before it, so no warp waits for another's output and the
@@ -33,12 +36,10 @@ namespace {
 
 using namespace enc;
 
-// One CTA of 24 warps per SM: one copy of the 32 KiB code table per SM and
-// the rest of shared memory left to L1 (measured on 1 GiB text: 0.89 ms
-// with three 8-warp CTAs per SM, 0.86 ms with two 12-warp CTAs, 0.80 ms
-// with one 24-warp CTA; 28 warps spill more and take 0.82 ms, 20 warps
-// without spills 0.84 ms).
-constexpr int kEncBlock = 768;
+// One CTA of 16 warps per SM: one copy of the 32 KiB code table per SM; a
+// step keeps 32 table entries per lane in registers (~120 per thread), so
+// 16 warps are what fit without spills.
+constexpr int kEncBlock = 512;
 constexpr int kEncWarps = kEncBlock / 32;
 constexpr int kEncSmemBytes = (kTblWords + kEncWarps * kWarpObuf) * 4;
 

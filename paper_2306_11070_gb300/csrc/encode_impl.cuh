@@ -7,12 +7,24 @@
 namespace huff {
 namespace enc {
 
-constexpr int kSymsPerThread = 16;
-constexpr int kStepSyms = 32 * kSymsPerThread;          // 512 per warp step
-constexpr int kStepsPerUnit = kUnitSymbols / kStepSyms;  // 32
-constexpr int kTblWords = 256 * 32;                      // 32 KiB
-constexpr int kWarpObuf = kStepSyms + 8;                 // 32-bit codes + alignment
-constexpr int kFastMaxLen = 24;
+constexpr int kTblWords = 256 * 32;  // [byte][lane] table, 32 KiB
+// fast path (codes of at most kFastMaxLen bits): 32 symbols per lane and
+// step, 1024 per warp step, 16 steps per unit
+constexpr int kFastSyms = 32;
+constexpr int kFastStep = 32 * kFastSyms;
+constexpr int kFastSteps = kUnitSymbols / kFastStep;
+// the low 10 bits of a sum of 32 entries are the sum of their lengths while
+// every length is at most 22 (the code sits above bit 9 of its entry)
+constexpr uint32_t kFastMaxLen = 22;
+constexpr uint32_t kSumMask = 1023;
+// long codes (23..32 bits): 16 symbols per lane and step
+constexpr int kLongSyms = 16;
+constexpr int kLongStep = 32 * kLongSyms;
+constexpr int kLongSteps = kUnitSymbols / kLongStep;
+// warp buffer: a guard word, then the words of one step (a fast step writes
+// at most 1024 x 22 / 32 = 704 words after the < 32 carried bits, a long one
+// 512 x 32 / 32 = 512), rounded up
+constexpr int kWarpObuf = 1 + kFastStep * (int)kFastMaxLen / 32 + 15;  // 720 words
 
 // One stream being written: input, unit offsets, output layout.
 struct Job {
@@ -85,7 +97,9 @@ __device__ __forceinline__ uint32_t tbl_at(uint32_t a)
     return v;
 }
 
-// Per-lane replicated code table (all threads of the CTA take part).
+// Per-lane replicated code table (all threads of the CTA take part).  Fast
+// entry = (code << (32 - len)) | len: the code left-aligned, its length in
+// the low bits, zeros between them (len <= 22 leaves bits 5..9 clear).
 __device__ __forceinline__ void build_table(const huff_codebook_t *cb, uint32_t *tbl, bool fast)
 {
     if (fast) {
@@ -103,60 +117,64 @@ __device__ __forceinline__ void build_table(const huff_codebook_t *cb, uint32_t 
     }
 }
 
-__device__ __forceinline__ uint32_t byte_of(const uint32_t (&w)[4], int k)
+// Zero this warp's buffer (kWarpObuf words at wob); every step leaves the
+// words it used zero again, so this runs once per unit.
+__device__ __forceinline__ void clear_buffer(uint32_t *wob, int lane)
+{
+    for (int j = lane; j < kWarpObuf; j += 32)
+        wob[j] = 0u;
+    __syncwarp();
+}
+
+template <int N>
+__device__ __forceinline__ uint32_t byte_of(const uint32_t (&w)[N], int k)
 {
     return __byte_perm(w[k >> 2], 0u, 0x4440u | (uint32_t)(k & 3));
 }
 
-// A word of the warp buffer, written under a predicate without a branch:
-// OR-ed when `shared` (the word also holds another lane's bits), else stored.
-__device__ __forceinline__ void put_word(uint32_t f, uint32_t shared, uint32_t a, uint32_t v)
+__device__ __forceinline__ void red_or(uint32_t a, uint32_t v)
 {
-    asm volatile("{\n\t.reg .pred p, q, ps, pn;\n\t"
-                 "setp.ne.u32 p, %2, 0;\n\t"
-                 "setp.ne.u32 q, %3, 0;\n\t"
-                 "and.pred ps, p, q;\n\t"
-                 "and.pred pn, p, !q;\n\t"
-                 "@pn st.shared.u32 [%0], %1;\n\t"
-                 "@ps red.shared.or.b32 [%0], %1;\n\t}"
-                 ::"r"(a), "r"(v), "r"(f), "r"(shared)
-                 : "memory");
+    asm volatile("red.shared.or.b32 [%0], %1;" ::"r"(a), "r"(v) : "memory");
 }
 
-// Append the 16 codes of one lane (fast table entries, len <= 24) at bit p0
-// of the warp's word-aligned buffer (shared address wob).  s[k] is the
-// total length of codes 0..k.  With G = floor(32 / longest code), G codes
-// always fit beside fewer than 32 pending bits in the 64-bit accumulator,
-// so a word can complete only at every G-th code; the check there is
-// straight-line code.  Words are whole and owned by this lane except the
-// first one when p0 is not word aligned (it holds the end of the previous
-// lane's bits) and the final partial one: those two are OR-ed, all others
-// are plain stores.
-template <int G>
-__device__ __forceinline__ void pack16(const uint32_t (&e)[kSymsPerThread],
-                                       const uint32_t (&s)[kSymsPerThread], uint32_t p0,
-                                       uint32_t wob)
+// Pack the 32 codes of one lane (fast entries e, sums sc at every emit
+// check) into the warp's word buffer, the lane's bits starting at bit p0.
+// hi:lo holds the lane's last 64 bits.  With G = floor(32 / longest) codes
+// between checks, at most one word boundary is crossed per check; each check
+// writes the last completed word (its bits of this lane: bits of this lane
+// that were not yet shifted in are zero), so a word is written once or, with
+// the same bits, again.  A check before the lane's first word is complete
+// writes zeros to the word before it (the guard word for lane 0).
+//  - kSts (a full step: every lane has 32 codes, so at least 32 bits):
+//    plain stores.  Such a zero word can only land on the previous lane's
+//    last complete word, and only at a check before the last one, while
+//    that lane writes the word again at its last check; so every complete
+//    word ends with its owner's value, with no atomics and no clearing.
+//  - otherwise a lane may have no bits at all: OR into a zeroed buffer.
+// Returns the end of the lane's bits and its last partial word (zero bits
+// when there is none), high-aligned.
+template <int G, bool kSts>
+__device__ __forceinline__ uint32_t pack32(const uint32_t (&e)[kFastSyms],
+                                           const uint32_t (&sc)[(kFastSyms + G - 1) / G], uint32_t p0,
+                                           uint32_t wob_s, uint32_t &part)
 {
-    uint32_t hi = 0u, lo = 0u;
-    uint32_t wa = imad(p0 >> 5, kc[kFour], wob);  // the word being filled
-    uint32_t nbe = p0 & 31u;                      // its bits before this lane, - 32 per word out
-    uint32_t shared = nbe != 0;
+    uint32_t hi = 0u, lo = 0u, E = p0;
 #pragma unroll
-    for (int k = 0; k < kSymsPerThread; ++k) {
+    for (int k = 0; k < kFastSyms; ++k) {
         const uint32_t x = e[k];
         hi = __funnelshift_l(lo, hi, x);  // (hi:lo) <<= len
         lo = __funnelshift_l(x, lo, x);   //   ... | code
-        if ((k + 1) % G == 0 || k == kSymsPerThread - 1) {
-            const uint32_t nb = nbe + s[k];        // pending bits, < 64
-            const uint32_t f = nb >> 5;            // a whole word is ready
-            put_word(f, shared, wa, __funnelshift_r(lo, hi, nb));  // shift by nb - 32
-            wa = imad(f, kc[kFour], wa);
-            nbe = imad(f, kc[kMinus32], nbe);
-            shared &= f ^ 1u;
+        if ((k + 1) % G == 0 || k == kFastSyms - 1) {
+            E = p0 + (sc[k / G] & kSumMask);  // end of the lane's bits so far
+            const uint32_t a = imad(E >> 5, kc[kFour], wob_s - 4), v = __funnelshift_r(lo, hi, E);
+            if (kSts)
+                sts(a, v);
+            else
+                red_or(a, v);
         }
     }
-    const uint32_t rest = (nbe + s[kSymsPerThread - 1]) & 31u;
-    put_word(rest, 1u, wa, __funnelshift_lc(0u, lo, 32 - rest));  // lo << (32 - rest)
+    part = __funnelshift_lc(0u, lo, 32u - (E & 31u));
+    return E;
 }
 
 // The last r (< 32) bits of the code stream before symbol `base` (> 0), as the
@@ -186,14 +204,13 @@ __device__ __forceinline__ uint32_t seam_word(const uint8_t *in, uint64_t base, 
     return __reduce_or_sync(0xffffffffu, part);
 }
 
-// Shared per-unit setup of the encoders below.
+// Shared per-unit state of the encoders below.
 struct UnitState {
     uint64_t base;   // first symbol of the unit
     uint64_t gbit;   // stream bit of the next step's first symbol
     uint32_t carry;  // bits of the partial word before the step, high-aligned
     uint32_t lead;   // distance from the step start to the next chunk start
     uint64_t next_chunk;  // index of that chunk
-    uint4 nxt;       // this lane's 16 input bytes of the coming step
 };
 
 __device__ __forceinline__ UnitState unit_start(const Job &J, uint64_t u, const uint32_t *tbl,
@@ -208,32 +225,24 @@ __device__ __forceinline__ UnitState unit_start(const Job &J, uint64_t u, const 
     const uint32_t umod = (uint32_t)(st.base % J.cs);
     st.lead = umod ? J.cs - umod : 0u;
     st.next_chunk = (st.base + st.lead) / J.cs;
-    st.nxt = make_uint4(0, 0, 0, 0);
-    if (st.base + (uint64_t)lane * kSymsPerThread + kSymsPerThread <= J.n)
-        st.nxt = ld_stream16(J.in + st.base + lane * kSymsPerThread);
     return st;
 }
 
-// This lane's 16 input bytes of the step starting at symbol sb (m of them
-// real, the rest zero), and the load of the next step's bytes.
-__device__ __forceinline__ int step_input(const Job &J, UnitState &st, int step, uint64_t sb,
-                                          int lane, uint32_t (&w)[4])
+// This lane's SPT input bytes of the step starting at symbol sb (m of them
+// real, the rest zero), read straight from the input (partial steps only).
+template <int SPT>
+__device__ __forceinline__ int step_input_tail(const Job &J, uint64_t sb, int lane,
+                                               uint32_t (&w)[SPT / 4])
 {
-    const uint64_t i0 = sb + (uint64_t)lane * kSymsPerThread;
-    const int m = i0 >= J.n ? 0 : (J.n - i0 >= kSymsPerThread ? kSymsPerThread : (int)(J.n - i0));
-    w[0] = st.nxt.x;
-    w[1] = st.nxt.y;
-    w[2] = st.nxt.z;
-    w[3] = st.nxt.w;
-    if (step + 1 < kStepsPerUnit && i0 + kStepSyms + kSymsPerThread <= J.n)
-        st.nxt = ld_stream16(J.in + i0 + kStepSyms);  // one step ahead
-    if (m < kSymsPerThread) {
-        w[0] = w[1] = w[2] = w[3] = 0u;
+    const uint64_t i0 = sb + (uint64_t)lane * SPT;
+    const int m = i0 >= J.n ? 0 : (J.n - i0 >= (uint64_t)SPT ? SPT : (int)(J.n - i0));
 #pragma unroll
-        for (int k = 0; k < kSymsPerThread; ++k)
-            if (k < m)
-                w[k >> 2] |= (uint32_t)J.in[i0 + k] << (8 * (k & 3));
-    }
+    for (int j = 0; j < SPT / 4; ++j)
+        w[j] = 0u;
+#pragma unroll
+    for (int k = 0; k < SPT; ++k)
+        if (k < m)
+            w[k >> 2] |= (uint32_t)J.in[i0 + k] << (8 * (k & 3));
     return m;
 }
 
@@ -252,177 +261,227 @@ __device__ __forceinline__ void scan_bits(uint32_t bits, int lane, uint32_t &pos
 }
 
 // Chunk offsets: the stream bit of every chunk that starts at one of this
-// lane's symbols (a chunk starts at a multiple of cs, itself a multiple of
-// 16, so only at a lane's first symbol).
-__device__ __forceinline__ void step_chunks(const Job &J, const UnitState &st, uint64_t sb,
-                                            int lane, uint32_t pos)
+// lane's symbols.  A chunk starts at a multiple of cs, itself a multiple of
+// 16, so only at lane offset 0 or 16 (mid16: the bits of the lane's first 16
+// symbols; only used when SPT = 32).
+template <int SPT, int STEP>
+__device__ __forceinline__ void step_chunks(const Job &J, const UnitState &st, uint64_t sb, int lane,
+                                            uint32_t pos, uint32_t mid16)
 {
     if (!J.table_fits)
         return;
-    const uint32_t d = (uint32_t)lane * kSymsPerThread;
     uint64_t *offs = reinterpret_cast<uint64_t *>(J.out + kHeaderBytes);
-    if (J.cs >= (uint32_t)kStepSyms) {  // at most one start per step
-        stg64_if(d == st.lead && sb + d < J.n, offs + st.next_chunk, st.gbit + pos);
-    } else if (d >= st.lead && (d - st.lead) % J.cs == 0 && sb + d < J.n) {
-        offs[(sb + d) / J.cs] = st.gbit + pos;
+#pragma unroll
+    for (int off = 0; off < SPT; off += 16) {
+        const uint32_t d = (uint32_t)lane * SPT + off;
+        const uint64_t bit = st.gbit + pos + (off ? mid16 : 0u);
+        if (J.cs >= (uint32_t)STEP) {  // at most one start per step
+            stg64_if(d == st.lead && sb + d < J.n, offs + st.next_chunk, bit);
+        } else if (d >= st.lead && (d - st.lead) % J.cs == 0 && sb + d < J.n) {
+            offs[(sb + d) / J.cs] = bit;
+        }
     }
 }
 
+template <int STEP>
 __device__ __forceinline__ void step_advance(const Job &J, UnitState &st, uint32_t step_bits)
 {
     st.gbit += step_bits;
-    if (st.lead >= (uint32_t)kStepSyms) {
-        st.lead -= kStepSyms;
-    } else if (J.cs >= (uint32_t)kStepSyms) {
-        st.lead = J.cs - (kStepSyms - st.lead);
+    if (st.lead >= (uint32_t)STEP) {
+        st.lead -= STEP;
+    } else if (J.cs >= (uint32_t)STEP) {
+        st.lead = J.cs - (STEP - st.lead);
         ++st.next_chunk;
     } else {
-        st.lead = (J.cs - (kStepSyms - st.lead) % J.cs) % J.cs;
+        st.lead = (J.cs - (STEP - st.lead) % J.cs) % J.cs;
     }
 }
 
 // Whole words of the step out (coalesced); the partial last word is carried
 // into the next step, or left to the next unit's seam at the unit end.
-__device__ __forceinline__ bool step_output(const Job &J, UnitState &st, uint64_t sb,
-                                            uint32_t step_bits, const uint32_t *wob, int lane)
+// kChecked: bound checks against the output capacity (else the words surely
+// fit) and every word read cleared again for the next step's OR-ing.
+// Returns true on overflow.
+template <bool kChecked>
+__device__ __forceinline__ bool step_output(const Job &J, UnitState &st, bool last, uint32_t step_bits,
+                                            uint32_t *wob, int lane)
 {
     uint32_t *pay = reinterpret_cast<uint32_t *>(J.out + J.pay0);
     const uint32_t r = (uint32_t)(st.gbit & 31);
     const uint32_t nw = (r + step_bits + 31) >> 5;
-    const bool last = sb + kStepSyms >= J.n;
     const uint32_t tail = (r + step_bits) & 31u;
     const uint32_t nwrite = (last || tail == 0) ? nw : nw - 1;
     const uint64_t wbase = st.gbit >> 5;
     bool overflow = false;
-    if (wbase + nwrite <= J.cap_words) {
-        // warp-uniform trip count; reading past nwrite stays inside the buffer
-        for (uint32_t j0 = 0; j0 < nwrite; j0 += 32) {
+    const uint32_t carry = tail ? wob[nw - 1] : 0u;
+    if (!kChecked || wbase + nwrite <= J.cap_words) {
+        for (uint32_t j0 = 0; j0 < nw; j0 += 32) {
             const uint32_t j = j0 + lane;
-            stg_if(j < nwrite, pay + wbase + j, wob[j]);
+            const uint32_t v = j < nw ? wob[j] : 0u;
+            stg_if(j < nwrite, pay + wbase + j, v);
+            if (kChecked && j < nw)
+                wob[j] = 0u;
         }
     } else {
-        for (uint32_t j = lane; j < nwrite; j += 32) {
-            if (wbase + j < J.cap_words)
-                pay[wbase + j] = wob[j];
-            else
-                overflow = true;
+        for (uint32_t j = lane; j < nw; j += 32) {
+            if (j < nwrite) {
+                if (wbase + j < J.cap_words)
+                    pay[wbase + j] = wob[j];
+                else
+                    overflow = true;
+            }
+            wob[j] = 0u;
         }
     }
-    st.carry = tail ? wob[nw - 1] : 0u;
+    st.carry = carry;
     return overflow;
 }
 
-// One 512-symbol step of the fast encoder (codes of at most 24 bits, G =
-// floor(32 / longest)).  kInner: the step and the next one lie inside the
-// input, the unit is not the last one and its words fit the output, so the
-// step needs none of the bound checks.
+// One 1024-symbol step of the fast encoder (codes of at most 22 bits, G =
+// floor(32 / longest)).  kInner: the step lies inside the input, the unit
+// is not the last one and its words fit the output, so the step needs none
+// of the bound checks; its 32 input bytes per lane (w) were loaded ahead.
 template <int G, bool kInner>
 __device__ __forceinline__ bool fast_step(const Job &J, UnitState &st, int step, int lane,
-                                          uint32_t tcol_s, uint32_t wob_s, uint32_t *wob)
+                                          uint32_t tcol_s, uint32_t wob_s, uint32_t *wob,
+                                          const uint32_t (&w)[8])
 {
-    const uint64_t sb = st.base + (uint64_t)step * kStepSyms;
-    uint32_t w[4];
-    int m = kSymsPerThread;
+    constexpr int NC = (kFastSyms + G - 1) / G;
+    const uint64_t sb = st.base + (uint64_t)step * kFastStep;
+    int m = kFastSyms;
+    uint32_t tw[8];
     if (kInner) {
-        w[0] = st.nxt.x;
-        w[1] = st.nxt.y;
-        w[2] = st.nxt.z;
-        w[3] = st.nxt.w;
-        if (step + 1 < kStepsPerUnit)
-            st.nxt = ld_stream16(J.in + sb + kStepSyms + lane * kSymsPerThread);
+#pragma unroll
+        for (int j = 0; j < 8; ++j)
+            tw[j] = w[j];
     } else {
-        m = step_input(J, st, step, sb, lane, w);
+        m = step_input_tail<kFastSyms>(J, sb, lane, tw);
     }
 
-    // table entries of this lane's symbols and their running bit counts
-    uint32_t e[kSymsPerThread], s[kSymsPerThread];
-    uint32_t bits = 0;
+    // table entries of this lane's symbols; s accumulates whole entries,
+    // whose low 10 bits sum the lengths
+    uint32_t e[kFastSyms], sc[NC];
+    uint32_t s = 0, mid16 = 0;
 #pragma unroll
-    for (int k = 0; k < kSymsPerThread; ++k) {
-        e[k] = tbl_at(imad(byte_of(w, k), kc[k128], tcol_s));
+    for (int k = 0; k < kFastSyms; ++k) {
+        e[k] = tbl_at(imad(byte_of(tw, k), kc[k128], tcol_s));
         if (!kInner && k >= m)
             e[k] = 0u;
-        bits += e[k] & 31u;
-        s[k] = bits;
+        s = imad(e[k], kc[kOne], s);
+        if ((k + 1) % G == 0 || k == kFastSyms - 1)
+            sc[k / G] = s;
+        if (k == 15)
+            mid16 = s & kSumMask;
     }
+    const uint32_t bits = s & kSumMask;
     uint32_t pos, step_bits;
     scan_bits(bits, lane, pos, step_bits);
-    const uint32_t p0 = (uint32_t)(st.gbit & 31) + pos, pend = p0 + bits;
+    const uint32_t p0 = (uint32_t)(st.gbit & 31) + pos;
 
-    // words that will be OR-ed start at zero: word 0 holds the carried bits,
-    // and each lane clears the word it ends in when that word is shared with
-    // the lanes after it
-    sts_if(lane == 0, wob_s, st.carry);
-    sts_if((pend & 31u) && (pend >> 5), imad(pend >> 5, kc[kFour], wob_s), 0u);
-    __syncwarp();
-    step_chunks(J, st, sb, lane, pos);
-    pack16<G>(e, s, p0, wob_s);
-    __syncwarp();
-    bool overflow = false;
+    step_chunks<kFastSyms, kFastStep>(J, st, sb, lane, pos, mid16);
+    uint32_t part;
     if (kInner) {
-        // whole words out; the partial last word is carried
-        uint32_t *pay = reinterpret_cast<uint32_t *>(J.out + J.pay0);
-        const uint32_t r = (uint32_t)(st.gbit & 31);
-        const uint32_t tail = (r + step_bits) & 31u;
-        const uint32_t nwrite = (r + step_bits) >> 5;
-        const uint64_t wbase = st.gbit >> 5;
-        for (uint32_t j0 = 0; j0 < nwrite; j0 += 32) {
-            const uint32_t j = j0 + lane;
-            stg_if(j < nwrite, pay + wbase + j, wob[j]);
-        }
-        st.carry = tail ? wob[nwrite] : 0u;
+        // complete words by plain stores, then each lane ORs its last partial
+        // word into the next lane's first word (the last lane stores it: no
+        // lane writes that word), and lane 0 ORs the carried bits into word 0
+        const uint32_t E = pack32<G, true>(e, sc, p0, wob_s, part);
+        __syncwarp();
+        const uint32_t pa = imad(E >> 5, kc[kFour], wob_s);
+        if (lane == 31)
+            sts(pa, part);
+        else
+            red_or(pa, part);
+        if (lane == 0)
+            red_or(wob_s, st.carry);
     } else {
-        overflow = step_output(J, st, sb, step_bits, wob, lane);
+        // word 0 starts with the carried bits; every other word is zero
+        sts_if(lane == 0, wob_s, st.carry);
+        __syncwarp();
+        const uint32_t E = pack32<G, false>(e, sc, p0, wob_s, part);
+        red_or(imad(E >> 5, kc[kFour], wob_s), part);
     }
     __syncwarp();
-    step_advance(J, st, step_bits);
+    const bool last = sb + kFastStep >= J.n;
+    const bool overflow = step_output<!kInner>(J, st, last, step_bits, wob, lane);
+    __syncwarp();
+    step_advance<kFastStep>(J, st, step_bits);
     return overflow;
 }
 
-// Encode unit u of job J with the calling warp, codes of at most 24 bits.
-// wob is the warp's buffer of kWarpObuf words, tbl the CTA's table.
-// Returns true if a payload word fell outside the output capacity.
+__device__ __forceinline__ void load32(const uint8_t *p, uint32_t (&w)[8])
+{
+    const uint4 a = ld_stream16(p), b = ld_stream16(p + 16);
+    w[0] = a.x;
+    w[1] = a.y;
+    w[2] = a.z;
+    w[3] = a.w;
+    w[4] = b.x;
+    w[5] = b.y;
+    w[6] = b.z;
+    w[7] = b.w;
+}
+
+// Encode unit u of job J with the calling warp, codes of at most 22 bits.
+// wob is the warp's buffer of kWarpObuf words (word 0 is the guard), tbl the
+// CTA's table.  Returns true if a payload word fell outside the output
+// capacity.
 template <int G>
 __device__ __forceinline__ bool encode_unit_fast(const Job &J, uint64_t u, const uint32_t *tbl,
                                                  uint32_t *wob)
 {
     const int lane = threadIdx.x & 31;
-    const uint32_t tcol_s = smem_u32(tbl + lane), wob_s = smem_u32(wob);
+    const uint32_t tcol_s = smem_u32(tbl + lane), wob_s = smem_u32(wob + 1);
     UnitState st = unit_start(J, u, tbl, true, lane);
     const bool inner = st.base + kUnitSymbols < J.n && (J.unit_off[u + 1] >> 5) < J.cap_words;
+    if (!inner)
+        clear_buffer(wob, lane);
     bool overflow = false;
     if (inner) {  // warp-uniform
-        for (int step = 0; step < kStepsPerUnit; ++step)
-            fast_step<G, true>(J, st, step, lane, tcol_s, wob_s, wob);
+        const uint8_t *p = J.in + st.base + lane * kFastSyms;
+        uint32_t w[8];
+        load32(p, w);
+        for (int step = 0; step < kFastSteps; ++step) {
+            uint32_t nx[8];
+            if (step + 1 < kFastSteps)
+                load32(p + (step + 1) * kFastStep, nx);  // one step ahead
+            fast_step<G, true>(J, st, step, lane, tcol_s, wob_s, wob + 1, w);
+#pragma unroll
+            for (int j = 0; j < 8; ++j)
+                w[j] = nx[j];
+        }
     } else {
-        for (int step = 0; step < kStepsPerUnit; ++step) {
-            if (st.base + (uint64_t)step * kStepSyms >= J.n)
+        const uint32_t none[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+        for (int step = 0; step < kFastSteps; ++step) {
+            if (st.base + (uint64_t)step * kFastStep >= J.n)
                 break;  // warp-uniform
-            overflow |= fast_step<G, false>(J, st, step, lane, tcol_s, wob_s, wob);
+            overflow |= fast_step<G, false>(J, st, step, lane, tcol_s, wob_s, wob + 1, none);
         }
     }
     return overflow;
 }
 
-// The same for codes of up to 32 bits: split code / length tables and a
-// 64-bit accumulator (rare: only very skewed inputs have codes this long).
+// The same for codes of up to 32 bits: split code / length tables, 16
+// symbols per lane and a 64-bit accumulator (rare: only very skewed inputs
+// have codes this long).
 __device__ __forceinline__ bool encode_unit_long(const Job &J, uint64_t u, const uint32_t *tbl,
-                                              uint32_t *wob)
+                                                 uint32_t *wob_all)
 {
     const int lane = threadIdx.x & 31;
+    clear_buffer(wob_all, lane);
+    uint32_t *wob = wob_all + 1;
     bool overflow = false;
     UnitState st = unit_start(J, u, tbl, false, lane);
-    for (int step = 0; step < kStepsPerUnit; ++step) {
-        const uint64_t sb = st.base + (uint64_t)step * kStepSyms;
+    for (int step = 0; step < kLongSteps; ++step) {
+        const uint64_t sb = st.base + (uint64_t)step * kLongStep;
         if (sb >= J.n)
             break;  // warp-uniform
         uint32_t w[4];
-        const int m = step_input(J, st, step, sb, lane, w);
-        uint32_t e[kSymsPerThread], l2[kSymsPerThread];
+        const int m = step_input_tail<kLongSyms>(J, sb, lane, w);
+        uint32_t e[kLongSyms], l2[kLongSyms];
         uint32_t bits = 0;
         const int col = lane & 15;
 #pragma unroll
-        for (int k = 0; k < kSymsPerThread; ++k) {
+        for (int k = 0; k < kLongSyms; ++k) {
             const uint32_t b = byte_of(w, k);
             e[k] = k < m ? tbl[(b << 4) | col] : 0u;
             l2[k] = k < m ? tbl[256 * 16 + ((b << 4) | col)] : 0u;
@@ -431,16 +490,15 @@ __device__ __forceinline__ bool encode_unit_long(const Job &J, uint64_t u, const
         uint32_t pos, step_bits;
         scan_bits(bits, lane, pos, step_bits);
         const uint32_t r = (uint32_t)(st.gbit & 31);
-        const uint32_t nw = (r + step_bits + 31) >> 5;
-        for (uint32_t j = lane; j < nw; j += 32)
-            wob[j] = j == 0 ? st.carry : 0u;  // word 0 starts with the carried bits
+        if (lane == 0)
+            wob[0] = st.carry;  // word 0 starts with the carried bits
         __syncwarp();
-        step_chunks(J, st, sb, lane, pos);
+        step_chunks<kLongSyms, kLongStep>(J, st, sb, lane, pos, 0u);
         if (m > 0) {
             uint32_t wi = (r + pos) >> 5, nb = (r + pos) & 31u;
             uint64_t acc = 0;
 #pragma unroll
-            for (int k = 0; k < kSymsPerThread; ++k) {
+            for (int k = 0; k < kLongSyms; ++k) {
                 const uint32_t L = l2[k];
                 acc = L ? ((acc << L) | e[k]) : acc;
                 nb += L;
@@ -454,9 +512,9 @@ __device__ __forceinline__ bool encode_unit_long(const Job &J, uint64_t u, const
                 atomicOr(wob + wi, (uint32_t)acc << (32 - nb));
         }
         __syncwarp();
-        overflow |= step_output(J, st, sb, step_bits, wob, lane);
+        overflow |= step_output<true>(J, st, sb + kLongStep >= J.n, step_bits, wob, lane);
         __syncwarp();
-        step_advance(J, st, step_bits);
+        step_advance<kLongStep>(J, st, step_bits);
     }
     return overflow;
 }
