@@ -291,6 +291,10 @@ huff_status_t huff_batch_info(const huff_batch_plan_t *plan, huff_batch_params_t
  *   rounded up to 16; zero bytes between streams.
  * Both calls run the batched engine (one fused launch) and SYNCHRONIZE the
  * stream: they plan the batch on the host and free the plan afterwards.
+ * Both ALLOCATE device memory on every call (cudaMalloc / cudaFree: the
+ * batch plan's descriptor block, and for decompression 12 bytes of scratch
+ * per segment); callers that must not allocate while they run keep a
+ * persistent plan over the segments with huff_batch_plan / huff_batch_run.
  * Decompression spreads each segment over enough lanes that the whole
  * container fills about one wave of decoders (256 lanes per SM). */
 uint64_t huff_segmented_max_size(uint64_t n, uint64_t segment_bytes, uint32_t chunk_symbols);
@@ -349,7 +353,9 @@ huff_status_t huff_bwt_inverse(const uint8_t *d_last, uint64_t n, uint32_t block
  * list 0..255; each byte is coded as its position in the list and moved to
  * the front; the inverse decodes.  Asynchronous on the stream; d_in / d_out
  * n bytes (they may be the same buffer); workspace huff_mtf_workspace_size
- * bytes, 16-byte aligned (about n / 8 + n).  Host errors only:
+ * bytes, 16-byte aligned: 516 bytes per 1 KiB segment of every block (the
+ * segments' distinct bytes, counts and starting lists) plus n, so about
+ * 1.5 n.  Host errors only:
  * HUFF_ERR_INVALID_ARG, HUFF_ERR_CUDA. */
 uint64_t huff_mtf_workspace_size(uint64_t n, uint32_t block);
 huff_status_t huff_mtf_forward(const uint8_t *d_in, uint64_t n, uint32_t block, uint8_t *d_out,

@@ -598,9 +598,18 @@ huff_status_t huff_batch_plan(const huff_batch_desc_t *descs, uint32_t count, hu
         free_plan(p);
         return HUFF_ERR_CUDA;
     }
+    // upload on a private stream: the legacy default stream would wait for
+    // (and hold up) every other blocking stream of the process
+    cudaStream_t up;
+    if (cudaStreamCreateWithFlags(&up, cudaStreamNonBlocking) != cudaSuccess) {
+        free_plan(p);
+        return HUFF_ERR_CUDA;
+    }
     std::vector<uint8_t> host(L.upload_bytes);
-    if (batch_upload(L, p->d_block, host.data(), 0) != cudaSuccess ||
-        cudaStreamSynchronize(0) != cudaSuccess) {
+    const bool uploaded = batch_upload(L, p->d_block, host.data(), up) == cudaSuccess &&
+                          cudaStreamSynchronize(up) == cudaSuccess;
+    cudaStreamDestroy(up);
+    if (!uploaded) {
         free_plan(p);
         return HUFF_ERR_CUDA;
     }

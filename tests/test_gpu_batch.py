@@ -273,3 +273,43 @@ def test_autotune_cache_file_round_trip(tmp_path):
     second = json.loads(r2.stdout.strip().splitlines()[-1])
     assert (second["decode_lanes"], second["ctas_per_sm"]) == (other, 1)
     assert len(cache.read_text().splitlines()) == 1  # served from the file
+
+
+def test_batched_workload_4096_buffers_matches_oracle():
+    """The batched workload itself: 4096 text buffers with log-uniform sizes
+    1 KiB..4 MiB (sizes seed 3) and per-buffer seeds, one plan with the
+    default parameters and one with 4096-symbol chunks; every stream equals
+    the oracle's compress of that buffer, and decompression gives every
+    buffer back."""
+    from concurrent.futures import ThreadPoolExecutor
+    count = 4096
+    sizes = synth.log_uniform_sizes(count, seed=3, lo=1024, hi=4 << 20)
+    assert sizes.min() >= 1024 and sizes.max() <= 4 << 20
+    with ThreadPoolExecutor(16) as ex:
+        xs = list(ex.map(lambda i: synth.text(int(sizes[i]), synth.batch_seed(i)), range(count)))
+    for cs in (16384, 4096):
+        with ThreadPoolExecutor(16) as ex:
+            refs = list(ex.map(lambda x: oracle.compress(x, cs), xs))
+        plan, ins, outs = _compress_batch(xs, cs)
+        plan.run()
+        torch.cuda.synchronize()
+        st = plan.status.cpu().numpy()
+        nb = plan.out_bytes.cpu().numpy()
+        assert (st == 0).all()
+        for i in range(count):
+            ost, ref = refs[i]
+            assert ost == oracle.OK
+            assert nb[i] == ref.size, i
+            assert np.array_equal(outs[i][:ref.size].cpu().numpy(), ref), i
+        streams = [outs[i][:int(nb[i])] for i in range(count)]
+        decs = [torch.empty(max(x.size, 16), dtype=torch.uint8, device="cuda") for x in xs]
+        dplan = hg.BatchPlan(streams, decs, hg.HUFF_BATCH_DECOMPRESS)
+        dplan.run()
+        torch.cuda.synchronize()
+        assert (dplan.status.cpu().numpy() == 0).all()
+        for i in range(count):
+            assert torch.equal(decs[i][:xs[i].size], ins[i]), i
+        plan.close()
+        dplan.close()
+        del plan, dplan, ins, outs, streams, decs
+        torch.cuda.empty_cache()

@@ -303,7 +303,9 @@ def test_host_argument_errors():
 # ------------------------------------------------------------------ full-size workloads
 def _full_size_check(x, cs=16384, samples=24):
     """Whole histogram, codebook and offset table against the oracle; sampled
-    chunk payloads against the oracle's packing; round trip on the GPU."""
+    chunk payloads against the oracle's packing (a fast first failure); then
+    the entire stream byte for byte against the oracle's encoder; round trip
+    on the GPU."""
     d, h, cb, st = gpu_codebook(x)
     assert np.array_equal(h.cpu().numpy().view(np.uint64), oracle.histogram(x))
     ost, oln = oracle.code_lengths(oracle.histogram(x))
@@ -336,6 +338,14 @@ def _full_size_check(x, cs=16384, samples=24):
     lastw = int(out[nbytes - 4:nbytes].cpu().numpy().view("<u4")[0])
     pad = (32 - total % 32) % 32
     assert lastw & ((1 << pad) - 1) == 0
+    # the whole stream, byte for byte, against the oracle's encoder
+    ost, ref, need = oracle.encode(x, oln, cs)
+    assert ost == oracle.OK and need == nbytes
+    got = out[:nbytes].cpu().numpy()
+    if not np.array_equal(got, ref):
+        bad = np.flatnonzero(got != ref)
+        raise AssertionError(f"{bad.size} stream bytes differ from the oracle, first at {bad[0]}")
+    del got, ref
     back, n, st = gpu_decode(out[:nbytes])
     assert st == 0 and n == x.size
     assert torch.equal(back[:n], d)

@@ -7,8 +7,10 @@ array inside the library instead of a caller workspace.
 The test calls the entry point through the C ABI (ctypes) and checks that
 its stream is byte-identical to huff_encode's (integer work: the tolerance is
 exact) on two calls in a row with different inputs, so scratch left over by
-the first call would show up in the second.  It runs last in collection
-order and also passes alone in a fresh process.
+the first call would show up in the second.  A third test fills the whole
+scratch array (1 GiB of text: 65,536 units) and compares the stream with the
+oracle's encoder byte for byte.  The file runs last in collection order and
+also passes alone in a fresh process.
 """
 import ctypes
 
@@ -16,6 +18,7 @@ import numpy as np
 import pytest
 import torch
 
+import oracle
 import synth
 import paper_2306_11070_gb300 as hg
 from paper_2306_11070_gb300 import build as nvbuild
@@ -85,3 +88,39 @@ def test_noalloc_rejects_inputs_beyond_its_scratch():
             ctypes.c_void_p(out.data_ptr()), out.numel(), ctypes.c_void_p(ob.data_ptr()),
             ctypes.c_void_p(st.data_ptr()), ctypes.c_void_p(0))
     assert rc == hg.HUFF_ERR_BUDGET
+
+
+def test_noalloc_full_scratch_matches_oracle():
+    """1 GiB of text, the scratch array's full size (65,536 units), twice in a
+    row; the stream equals the oracle's encoder with the same code lengths."""
+    fn = _noalloc_fn()
+    x = synth.make("text_1g")
+    assert x.size == 1 << 30
+    d = torch.from_numpy(x).cuda()
+    h = hg.huff_histogram(d)
+    cb, st = hg.huff_build_codebook(h)
+    torch.cuda.synchronize()
+    assert int(st.item()) == 0
+    ln = hg.parse_codebook(cb)[0]
+    ost, ref, need = oracle.encode(x, ln, 16384)
+    assert ost == oracle.OK
+    for _ in range(2):
+        got, ngot = _noalloc(fn, d, cb, 16384)
+        assert ngot == need
+        assert np.array_equal(got, ref)
+
+
+@pytest.mark.skipif(torch.cuda.device_count() < 2, reason="needs two GPUs")
+def test_noalloc_on_two_devices():
+    """The library's launch set-up (dynamic shared memory limits, scratch
+    address) is per device: the no-allocation encoder runs on device 0, then
+    on device 1, and both streams equal huff_encode's on device 0."""
+    fn = _noalloc_fn()
+    x = synth.text(3 * 16384 + 77, 21)
+    ref_cb, ref, nref = _reference(torch.from_numpy(x).cuda(0), 16384)
+    for devno in (0, 1):
+        with torch.cuda.device(devno):
+            d = torch.from_numpy(x).cuda(devno)
+            cb = ref_cb.to(f"cuda:{devno}")
+            got, ngot = _noalloc(fn, d, cb, 16384)
+            assert ngot == nref and np.array_equal(got, ref)
