@@ -19,6 +19,7 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "huff_oracle.c")
+_SRC_LZSS = os.path.join(_HERE, "lzss_oracle.c")
 _HDR = os.path.join(_HERE, "huff_oracle.h")
 _LIB = os.path.join(_HERE, "libhuff_oracle.so")
 _lib = None
@@ -34,13 +35,26 @@ MAX_CODE_LEN = 32
 DEFAULT_CHUNK = 16384
 
 
+class LzssParams(ctypes.Structure):
+    """oracle_lzss_params: window W (bits), shortest / longest match (bits),
+    literal block (bits), dictionary mode (1: counting numbers, 2: the first
+    W bits stored)."""
+    _fields_ = [("window", ctypes.c_uint32), ("min_len", ctypes.c_uint32),
+                ("max_len", ctypes.c_uint32), ("block", ctypes.c_uint32),
+                ("dict", ctypes.c_uint32)]
+
+
+# the paper's LZSS configuration "1024/24/12/8" with the stored-prefix window
+PAPER_LZSS = (1024, 12, 24, 8, 2)
+
+
 def build(force: bool = False) -> str:
     """Compile the oracle with gcc (-O2, no FP contraction; integer code)."""
-    newest = max(os.path.getmtime(_SRC), os.path.getmtime(_HDR))
+    newest = max(os.path.getmtime(_SRC), os.path.getmtime(_SRC_LZSS), os.path.getmtime(_HDR))
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < newest:
         tmp = f"{_LIB}.tmp{os.getpid()}"
         subprocess.check_call(["gcc", "-O2", "-std=c99", "-fPIC", "-shared",
-                               "-ffp-contract=off", "-o", tmp, _SRC])
+                               "-ffp-contract=off", "-o", tmp, _SRC, _SRC_LZSS])
         os.replace(tmp, _LIB)
     return _LIB
 
@@ -79,8 +93,22 @@ def _configure(lib):
     lib.oracle_mtf.argtypes = [u8p, u64, u32, u8p]
     lib.oracle_imtf.restype = ctypes.c_int
     lib.oracle_imtf.argtypes = [u8p, u64, u32, u8p]
+    lp = ctypes.POINTER(LzssParams)
+    lib.oracle_lzss_params_ok.restype = ctypes.c_int
+    lib.oracle_lzss_params_ok.argtypes = [lp]
+    lib.oracle_lzss_max_bits.restype = u64
+    lib.oracle_lzss_max_bits.argtypes = [u64, lp]
+    lib.oracle_lzss_encode.restype = ctypes.c_int
+    lib.oracle_lzss_encode.argtypes = [u8p, u64, lp, u8p, u64, u64p]
+    lib.oracle_lzss_decode.restype = ctypes.c_int
+    lib.oracle_lzss_decode.argtypes = [u8p, u64, lp, u8p, u64]
+    lib.oracle_lzss_segmented_max_size.restype = u64
+    lib.oracle_lzss_segmented_max_size.argtypes = [u64, u64, lp]
+    lib.oracle_lzss_segmented_compress.restype = ctypes.c_int
+    lib.oracle_lzss_segmented_compress.argtypes = [u8p, u64, u64, lp, u8p, u64, u64p]
+    lib.oracle_lzss_segmented_decompress.restype = ctypes.c_int
+    lib.oracle_lzss_segmented_decompress.argtypes = [u8p, u64, u8p, u64, u64p]
     return lib
-
 
 def _load():
     global _lib
@@ -393,3 +421,70 @@ def m3_decompress(c, cap: int | None = None):
     if stages & 1:
         L = imtf(L, block)
     return OK, ibwt(L, block, prim), n
+
+
+# ---------------------------------------------------------------- LZSS (Section III-B)
+def _lzss_params(params):
+    w, lmin, lmax, blk, dct = params
+    return LzssParams(w, lmin, lmax, blk, dct)
+
+
+def lzss_encode(x, params=PAPER_LZSS):
+    """LZSS Method 1 of one segment: (status, code bytes, code bits).
+    params = (window, min_len, max_len, block, dict)."""
+    a = _bytes(x)
+    P = _lzss_params(params)
+    lib = _load()
+    if not lib.oracle_lzss_params_ok(ctypes.byref(P)):
+        return ERR_INVALID_ARG, np.zeros(0, np.uint8), 0
+    cap = (int(lib.oracle_lzss_max_bits(a.size, ctypes.byref(P))) + 7) // 8
+    out = np.zeros(max(cap, 1), dtype=np.uint8)
+    bits = ctypes.c_uint64(0)
+    st = lib.oracle_lzss_encode(_p(a, ctypes.c_uint8), a.size, ctypes.byref(P),
+                                _p(out, ctypes.c_uint8), cap, ctypes.byref(bits))
+    nb = int(bits.value)
+    return st, out[:(nb + 7) // 8], nb
+
+
+def lzss_decode(code, bits: int, m: int, params=PAPER_LZSS):
+    """Inverse of :func:`lzss_encode` for an m-byte segment: (status, bytes)."""
+    c = _bytes(code)
+    if c.size == 0:
+        c = np.zeros(1, np.uint8)
+    P = _lzss_params(params)
+    out = np.zeros(max(m, 1), dtype=np.uint8)
+    st = _load().oracle_lzss_decode(_p(c, ctypes.c_uint8), bits, ctypes.byref(P),
+                                    _p(out, ctypes.c_uint8), m)
+    return st, out[:m]
+
+
+def lzss_segmented_max_size(n: int, seg: int, params=PAPER_LZSS) -> int:
+    P = _lzss_params(params)
+    return int(_load().oracle_lzss_segmented_max_size(n, seg, ctypes.byref(P)))
+
+
+def lzss_segmented_compress(x, seg: int, params=PAPER_LZSS):
+    """LZSS Method 2: (status, container bytes)."""
+    a = _bytes(x)
+    P = _lzss_params(params)
+    cap = lzss_segmented_max_size(a.size, seg, params)
+    out = np.zeros(max(cap, 1), dtype=np.uint8)
+    ob = ctypes.c_uint64(0)
+    st = _load().oracle_lzss_segmented_compress(_p(a, ctypes.c_uint8), a.size, seg,
+                                                ctypes.byref(P), _p(out, ctypes.c_uint8), cap,
+                                                ctypes.byref(ob))
+    return st, (out[:int(ob.value)] if st == OK else out[:0])
+
+
+def lzss_segmented_decompress(c, cap: int | None = None):
+    """Inverse of :func:`lzss_segmented_compress`: (status, bytes, n)."""
+    a = _bytes(c)
+    if cap is None:
+        cap = int.from_bytes(bytes(a[0:8]), "little") if a.size >= 8 else 0
+        cap = min(cap, 1 << 34)
+    out = np.zeros(max(cap, 1), dtype=np.uint8)
+    n = ctypes.c_uint64(0)
+    st = _load().oracle_lzss_segmented_decompress(_p(a, ctypes.c_uint8), a.size,
+                                                  _p(out, ctypes.c_uint8), cap, ctypes.byref(n))
+    nn = int(n.value)
+    return st, (out[:nn] if st == OK else out[:0]), nn

@@ -40,4 +40,25 @@ int oracle_ibwt(const uint8_t *L, uint64_t n, uint32_t block, const uint32_t *pr
 /* Method 3's optional second stage: move-to-front coding per block */
 int oracle_mtf(const uint8_t *x, uint64_t n, uint32_t block, uint8_t *out);
 int oracle_imtf(const uint8_t *idx, uint64_t n, uint32_t block, uint8_t *out);
+/* LZSS Method 1 (one segment) and Method 2 (segmented container); the
+ * paper's Section III-B, readings Z1-Z7 in lzss_oracle.c */
+typedef struct {
+    uint32_t window;  /* W: window bits, a power of two in [2, 65536] */
+    uint32_t min_len; /* Lmin: shortest match, bits */
+    uint32_t max_len; /* Lmax: longest match, bits (<= 32) */
+    uint32_t block;   /* B: bits per literal (<= 32) */
+    uint32_t dict;    /* 1: counting-numbers window; 2: first W bits stored */
+} oracle_lzss_params;
+int oracle_lzss_params_ok(const oracle_lzss_params *P);
+uint64_t oracle_lzss_max_bits(uint64_t m, const oracle_lzss_params *P);
+int oracle_lzss_encode(const uint8_t *x, uint64_t m, const oracle_lzss_params *P, uint8_t *out,
+                       uint64_t cap_bytes, uint64_t *bits_out);
+int oracle_lzss_decode(const uint8_t *code, uint64_t code_bits, const oracle_lzss_params *P,
+                       uint8_t *y, uint64_t m);
+uint64_t oracle_lzss_segmented_max_size(uint64_t n, uint64_t seg, const oracle_lzss_params *P);
+int oracle_lzss_segmented_compress(const uint8_t *x, uint64_t n, uint64_t seg,
+                                   const oracle_lzss_params *P, uint8_t *out, uint64_t cap,
+                                   uint64_t *out_bytes);
+int oracle_lzss_segmented_decompress(const uint8_t *c, uint64_t bytes, uint8_t *out, uint64_t cap,
+                                     uint64_t *n_out);
 #endif

@@ -15,6 +15,10 @@ Workloads (sizes, distributions and seeds):
   80 characters (64 MiB and 1 GiB, seed 1).
 * ``uniform`` / ``geometric`` / ``single``: the distribution stress inputs
   (uniform bytes, P(k) = 2^-(k+1), one repeated byte 0x61; seeds 40, 41).
+* ``bitstream``: a stand-in for the FPGA configuration bitstreams the
+  paper's LZSS section codes (Section III-B; not available): zero runs,
+  repeated frame templates with a few flipped bits, random stretches
+  (256 MiB, seed 7, in 64 KiB segments for the GPU LZSS measurement).
 * ``log_uniform_sizes`` and ``batch_seed``: the sizes and per-buffer seeds of
   the batched workload (4096 buffers, 1 KiB..4 MiB, sizes seed 3).
 * ``poisson_trace``: open-loop arrivals for the served workload (seed 5).
@@ -65,6 +69,8 @@ def _load():
             fn.argtypes = [u8p, ctypes.c_uint64, ctypes.c_uint64]
         lib.synth_geometric_p.restype = None
         lib.synth_geometric_p.argtypes = [u8p, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_double]
+        lib.synth_bitstream.restype = ctypes.c_int
+        lib.synth_bitstream.argtypes = [u8p, ctypes.c_uint64, ctypes.c_uint64]
         lib.synth_shuffle.restype = None
         lib.synth_shuffle.argtypes = [u8p, ctypes.c_uint64, ctypes.c_uint64]
         lib.synth_log_uniform_sizes.restype = None
@@ -125,6 +131,15 @@ def geometric_p(n: int, seed: int, p: float, out=None) -> np.ndarray:
     return a[:n]
 
 
+def bitstream(n: int, seed: int = 7, out=None) -> np.ndarray:
+    """Stand-in for FPGA configuration bitstreams (LZSS inputs): zero runs,
+    templates repeated with a few flipped bits, random stretches."""
+    a = _out(n, out)
+    if _load().synth_bitstream(_ptr(a, ctypes.c_uint8), n, seed) != 0:
+        raise MemoryError("synth_bitstream")
+    return a[:n]
+
+
 def single(n: int, byte: int = 0x61, out=None) -> np.ndarray:
     a = _out(n, out)
     a[:n] = byte
@@ -176,6 +191,7 @@ WORKLOADS = {
     "uniform_1g": (uniform, 1 * GiB, 40),
     "geometric_1g": (geometric, 1 * GiB, 41),
     "single_1g": (lambda n, seed, out=None: single(n, 0x61, out=out), 1 * GiB, 42),
+    "bitstream_256m": (bitstream, 256 * MiB, 7),
 }
 
 

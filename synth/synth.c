@@ -247,3 +247,53 @@ void synth_shuffle(uint8_t *buf, uint64_t n, uint64_t seed)
         buf[j] = t;
     }
 }
+
+/* A stand-in for FPGA configuration bitstreams (the paper's LZSS inputs, not
+ * available): long runs of zero bytes (unused frames), copies of a few
+ * frame templates with one to three bits flipped (repeated configuration
+ * with small differences), and stretches of random bytes.  Record kinds in
+ * proportion 55 / 30 / 15 %; zero runs 16 + Exp(mean 500) bytes, templates
+ * 32..255 bytes (16 of them, drawn first), random stretches 8 + Exp(mean 64)
+ * bytes. */
+int synth_bitstream(uint8_t *out, uint64_t n, uint64_t seed)
+{
+    uint64_t st = seed;
+    enum { T = 16 };
+    uint8_t *tpl = (uint8_t *)malloc(T * 256);
+    uint32_t tlen[T];
+    if (!tpl)
+        return -1;
+    for (int t = 0; t < T; ++t) {
+        tlen[t] = 32 + below(&st, 224);
+        for (uint32_t i = 0; i < tlen[t]; ++i)
+            tpl[t * 256 + i] = (uint8_t)sm64(&st);
+    }
+    uint64_t i = 0;
+    while (i < n) {
+        const double r = u01(&st);
+        uint64_t len;
+        if (r < 0.55) {
+            len = 16 + (uint64_t)(-log(1.0 - u01(&st)) * 500.0);
+            for (uint64_t k = 0; k < len && i < n; ++k)
+                out[i++] = 0;
+        } else if (r < 0.85) {
+            const uint32_t t = below(&st, T);
+            const uint64_t at = i;
+            len = tlen[t];
+            for (uint64_t k = 0; k < len && i < n; ++k)
+                out[i++] = tpl[t * 256 + k];
+            const uint32_t flips = 1 + below(&st, 3);
+            for (uint32_t f = 0; f < flips; ++f) {
+                const uint64_t bit = below(&st, (uint32_t)(8 * len));
+                if (at + bit / 8 < n)
+                    out[at + bit / 8] ^= (uint8_t)(0x80u >> (bit % 8));
+            }
+        } else {
+            len = 8 + (uint64_t)(-log(1.0 - u01(&st)) * 64.0);
+            for (uint64_t k = 0; k < len && i < n; ++k)
+                out[i++] = (uint8_t)sm64(&st);
+        }
+    }
+    free(tpl);
+    return 0;
+}
