@@ -118,10 +118,11 @@ def _build(tmp_path, name, old, new):
     d.mkdir()
     c = d / "huff_oracle.c"
     c.write_text(src.replace(old, new))
-    hdr = os.path.join(os.path.dirname(_SRC), "huff_oracle.h")
-    (d / "huff_oracle.h").write_text(open(hdr).read())
+    for f in ("huff_oracle.h", "lzss_oracle.c"):  # the rest of the oracle, unchanged
+        (d / f).write_text(open(os.path.join(os.path.dirname(_SRC), f)).read())
     so = d / "libmutant.so"
-    subprocess.check_call(["gcc", "-O1", "-std=c99", "-fPIC", "-shared", "-o", str(so), str(c)])
+    subprocess.check_call(["gcc", "-O1", "-std=c99", "-fPIC", "-shared", "-o", str(so), str(c),
+                           str(d / "lzss_oracle.c")])
     return str(so)
 
 
