@@ -493,7 +493,66 @@ def measure_next_rows(hg, synth, torch, oracle=None):
                                    "sample": "the first 16 MiB, compress only",
                                    "compress_gbs": sample.size / dt / 1e9}
     res["segmented"] = seg_row
+    del x2, c, back
+    torch.cuda.empty_cache()
+    res["lzss"] = measure_lzss(hg, synth, torch, t_ms, oracle)
     return res
+
+
+def measure_lzss(hg, synth, torch, t_ms, oracle=None):
+    """LZSS Method 2 (Section III-B) with the paper's configuration
+    "1024/24/12/8" (window, longest and shortest match, literal block, in
+    bits) and the stored-prefix window, on 256 MiB of the bitstream stand-in
+    in 64 KiB segments, with pre-allocated buffers (no allocation or host
+    synchronisation inside a call)."""
+    n, seg = 256 << 20, 64 << 10
+    params = hg.LZSS_PAPER
+    x = torch.from_numpy(synth.make("bitstream_256m")).cuda()
+    L = hg.lib()
+    P = hg._lzss_params(params)
+    out = torch.empty(L.huff_lzss_max_size(n, seg, P), dtype=torch.uint8, device="cuda")
+    ws = torch.empty(L.huff_lzss_workspace_size(n, seg, P), dtype=torch.uint8, device="cuda")
+    ob = torch.zeros(1, dtype=torch.int64, device="cuda")
+    st = torch.zeros(1, dtype=torch.int32, device="cuda")
+
+    def comp():
+        hg.huff_lzss_compress(x, seg, params, d_out=out, d_out_bytes=ob, d_ws=ws, d_status=st)
+
+    tc = t_ms(comp, reps=3, warm=1)
+    comp()
+    torch.cuda.synchronize()
+    size = int(ob.item())
+    c = out[:size]
+    y = torch.empty(n, dtype=torch.uint8, device="cuda")
+    dn = torch.zeros(1, dtype=torch.int64, device="cuda")
+    st2 = torch.zeros(1, dtype=torch.int32, device="cuda")
+    dws = torch.empty(L.huff_lzss_decompress_workspace_size(size), dtype=torch.uint8,
+                      device="cuda")
+
+    def decomp():
+        hg.huff_lzss_decompress(c, d_out=y, d_n=dn, d_ws=dws, d_status=st2)
+
+    td = t_ms(decomp, reps=3, warm=1)
+    decomp()
+    torch.cuda.synchronize()
+    row = {"workload": "bitstream stand-in 256 MiB (seed 7), 64 KiB segments, 1024/24/12/8, "
+                       "stored-prefix window",
+           "compress_ms": tc, "compress_gbs": n / tc / 1e6,
+           "decompress_ms": td, "decompress_gbs": n / td / 1e6,
+           "ratio": size / n,
+           "round_trip_ok": int(st.item()) == 0 and int(st2.item()) == 0 and
+           int(dn.item()) == n and bool(torch.equal(y, x)),
+           "paper_context": "Table V-VI, Method 2 with Dict 2 on 4 cores: adder bitstream "
+                            "(763 kB) 43.4% saved in 5.8 s, processor (1.8 MB) 29.1% in 12.11 s"}
+    if oracle is not None:
+        sample = x[:256 << 10].cpu().numpy()
+        t0 = time.perf_counter()
+        oracle.lzss_segmented_compress(sample, seg, params)
+        dt = time.perf_counter() - t0
+        row["cpu_baseline"] = {"kind": "oracle", "cores": 1,
+                               "sample": "the first 256 KiB, compress only",
+                               "compress_gbs": sample.size / dt / 1e9}
+    return row
 
 
 def measure_served(hg, synth, oracle, torch, loads=(10.0, 20.0, 50.0, 100.0, 150.0, 200.0),

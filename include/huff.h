@@ -492,6 +492,64 @@ huff_status_t huff_server_release(huff_server_t *server, uint64_t ticket);
 /* Finish the queued and running requests, stop the thread, free everything. */
 void huff_server_destroy(huff_server_t *server);
 
+/* ---- LZSS Method 2: segmented LZSS (Section III-B) ------------------------
+ * The data is cut into equal segments of segment_bytes (the last may be
+ * shorter), each coded on its own against a sliding window of its most
+ * recent bits; the segments' code lengths and codes are packed together.
+ * The paper counts the window and match lengths in bits ("1024/24/12/8":
+ * a 1024-bit window, matches of 12..24 bits, 8-bit literal blocks).
+ * Readings: bits are read most significant bit of each byte first; the
+ * window starts from the counting numbers (dict = 1: bytes 0, 1, 2, ...
+ * before the segment) or from the segment's first `window` bits, stored as
+ * they are (dict = 2; then no match reaches before the segment); at each
+ * position the longest match of min_len .. min(max_len, bits left) bits is
+ * taken, the smallest distance among equally long ones, and the source may
+ * run into the bits being coded; a match is the bit 1, distance - 1 in
+ * log2(window) bits and length - min_len in ceil(log2(max_len - min_len +
+ * 1)) bits, a literal the bit 0 and the next min(block, bits left) bits.
+ * Container (integers LE): [0,8) n; [8,16) segment_bytes; [16,20) window;
+ * [20,24) min_len; [24,28) max_len; [28,32) block; [32,36) dict; [36,40)
+ * zero; [40,48) count = ceil(n / segment_bytes); count u32 code lengths in
+ * bits; then segment i's code, MSB first in bytes, from a 16-byte boundary
+ * (the first after the table), zero padded to the next 16-byte boundary. */
+typedef struct {
+    uint32_t window;  /* bits, a power of two in [2, 65536] */
+    uint32_t min_len; /* shortest match, bits, >= 1 */
+    uint32_t max_len; /* longest match, bits, min_len .. 32 */
+    uint32_t block;   /* bits per literal, 1 .. 32 */
+    uint32_t dict;    /* 1: counting numbers; 2: the first `window` bits stored */
+} huff_lzss_params_t;
+/* Capacity that always holds the container, and compression's device
+ * workspace; 0 for invalid parameters or segment sizes (segment_bytes a
+ * multiple of 16 in [16, 2^24]). */
+uint64_t huff_lzss_max_size(uint64_t n, uint64_t segment_bytes, const huff_lzss_params_t *params);
+uint64_t huff_lzss_workspace_size(uint64_t n, uint64_t segment_bytes,
+                                  const huff_lzss_params_t *params);
+/* Compress d_in[0, n) into the container at d_out.  Asynchronous on the
+ * stream, no host synchronisation and no allocation: one warp per segment
+ * codes into a worst-case slot of d_ws, one CTA lays out the header and
+ * table, a gather moves the codes into place.  *d_status is cleared first;
+ * *d_out_bytes receives the container size; HUFF_ERR_CAPACITY in *d_status
+ * when it exceeds out_cap.  d_in, d_out, d_ws 16-byte aligned (the caller's
+ * buffers).  Host errors: HUFF_ERR_INVALID_ARG, HUFF_ERR_CUDA. */
+huff_status_t huff_lzss_compress(const uint8_t *d_in, uint64_t n, uint64_t segment_bytes,
+                                 const huff_lzss_params_t *params, uint8_t *d_out,
+                                 uint64_t out_cap, uint64_t *d_out_bytes, void *d_ws,
+                                 uint64_t ws_bytes, int32_t *d_status, huff_stream_t stream);
+/* Workspace of decompression for a container of in_bytes bytes. */
+uint64_t huff_lzss_decompress_workspace_size(uint64_t in_bytes);
+/* Decompress a container into d_out[0, n); asynchronous, no allocation.
+ * *d_n receives n once the header and table are consistent; an
+ * inconsistent header or table, a distance or length out of range, or a
+ * segment whose tokens do not end exactly at its recorded length is
+ * HUFF_ERR_CORRUPT_STREAM in *d_status (the output is then unspecified);
+ * n > out_cap is HUFF_ERR_CAPACITY.  One thread decodes each segment.
+ * d_in, d_out, d_ws 16-byte aligned.  Host errors: HUFF_ERR_INVALID_ARG,
+ * HUFF_ERR_CUDA. */
+huff_status_t huff_lzss_decompress(const uint8_t *d_in, uint64_t in_bytes, uint8_t *d_out,
+                                   uint64_t out_cap, uint64_t *d_n, void *d_ws, uint64_t ws_bytes,
+                                   int32_t *d_status, huff_stream_t stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -56,6 +56,18 @@ class BatchParams(ctypes.Structure):
                 ("barrier_extra", ctypes.c_uint32)]
 
 
+class LzssParams(ctypes.Structure):
+    """huff_lzss_params_t"""
+    _fields_ = [("window", ctypes.c_uint32), ("min_len", ctypes.c_uint32),
+                ("max_len", ctypes.c_uint32), ("block", ctypes.c_uint32),
+                ("dict", ctypes.c_uint32)]
+
+
+# the paper's LZSS configuration "1024/24/12/8" (window, shortest and longest
+# match, literal block, in bits) with the stored-prefix window
+LZSS_PAPER = (1024, 12, 24, 8, 2)
+
+
 class ServerConfig(ctypes.Structure):
     """huff_server_cfg_t"""
     _fields_ = [("device_budget", ctypes.c_uint64), ("max_rounds", ctypes.c_uint32),
@@ -180,6 +192,17 @@ def lib() -> ctypes.CDLL:
         L.huff_batch_autotune.argtypes = [ctypes.POINTER(BatchDesc), u32, ctypes.c_int,
                                           ctypes.POINTER(BatchParams), u32,
                                           ctypes.POINTER(BatchParams), vp]
+        lp = ctypes.POINTER(LzssParams)
+        L.huff_lzss_max_size.restype = u64
+        L.huff_lzss_max_size.argtypes = [u64, u64, lp]
+        L.huff_lzss_workspace_size.restype = u64
+        L.huff_lzss_workspace_size.argtypes = [u64, u64, lp]
+        L.huff_lzss_compress.restype = i32
+        L.huff_lzss_compress.argtypes = [vp, u64, u64, lp, vp, u64, vp, vp, u64, vp, vp]
+        L.huff_lzss_decompress_workspace_size.restype = u64
+        L.huff_lzss_decompress_workspace_size.argtypes = [u64]
+        L.huff_lzss_decompress.restype = i32
+        L.huff_lzss_decompress.argtypes = [vp, u64, vp, u64, vp, vp, u64, vp, vp]
         _lib = L
     return _lib
 
@@ -515,6 +538,69 @@ def huff_segmented_decompress(d_container: torch.Tensor, out_cap: int | None = N
            "huff_segmented_decompress")
     n = int(dn.item())
     return out[:n], n, st
+
+
+# ---------------------------------------------------------------- LZSS Method 2
+def _lzss_params(params) -> LzssParams:
+    w, lmin, lmax, blk, dct = params
+    return LzssParams(w, lmin, lmax, blk, dct)
+
+
+def huff_lzss_compress(d_in: torch.Tensor, segment_bytes: int, params=LZSS_PAPER,
+                       d_out=None, d_out_bytes=None, d_ws=None, d_status=None, stream=None):
+    """(container uint8 tensor, status int32[1]); params = (window, min_len,
+    max_len, block, dict).  With d_out / d_out_bytes / d_ws / d_status
+    given, nothing is allocated and nothing is synchronised: the container
+    is d_out[:d_out_bytes] once the stream has run."""
+    n = d_in.numel()
+    L = lib()
+    P = _lzss_params(params)
+    cap = L.huff_lzss_max_size(n, segment_bytes, ctypes.byref(P))
+    wsb = L.huff_lzss_workspace_size(n, segment_bytes, ctypes.byref(P))
+    if cap == 0 or wsb == 0:
+        raise HuffError(HUFF_ERR_INVALID_ARG, "huff_lzss_compress")
+    dev = d_in.device
+    sync = d_out is None
+    out = d_out if d_out is not None else torch.empty(cap, dtype=torch.uint8, device=dev)
+    ws = d_ws if d_ws is not None else torch.empty(max(wsb, 16), dtype=torch.uint8, device=dev)
+    ob = d_out_bytes if d_out_bytes is not None else torch.zeros(1, dtype=torch.int64, device=dev)
+    st = d_status if d_status is not None else new_status(dev)
+    _check(L.huff_lzss_compress(_ptr(d_in) if n else None, n, segment_bytes, ctypes.byref(P),
+                                _ptr(out), out.numel(), _ptr(ob), _ptr(ws), ws.numel(), _ptr(st),
+                                _stream(stream)), "huff_lzss_compress")
+    if not sync:
+        return out, st
+    size = int(ob.item())
+    return (out[:size] if int(st.item()) == 0 else out[:0]), st
+
+
+def huff_lzss_decompress(d_container: torch.Tensor, out_cap: int | None = None, d_out=None,
+                         d_n=None, d_ws=None, d_status=None, stream=None):
+    """(decoded uint8 tensor, n, status int32[1]).  With d_out / d_n / d_ws /
+    d_status given, nothing is allocated and nothing is synchronised (n is
+    then None: read d_n after the stream has run)."""
+    dev = d_container.device
+    L = lib()
+    nb = d_container.numel()
+    sync = d_out is None
+    dn = d_n if d_n is not None else torch.zeros(1, dtype=torch.int64, device=dev)
+    st = d_status if d_status is not None else new_status(dev)
+    if d_out is None:
+        if out_cap is None:
+            out_cap = int.from_bytes(bytes(d_container[:8].cpu().numpy()), "little") \
+                if nb >= 8 else 0
+        d_out = torch.empty(max(out_cap, 16), dtype=torch.uint8, device=dev)
+    elif out_cap is None:
+        out_cap = d_out.numel()
+    wsb = L.huff_lzss_decompress_workspace_size(nb)
+    ws = d_ws if d_ws is not None else torch.empty(max(wsb, 16), dtype=torch.uint8, device=dev)
+    _check(L.huff_lzss_decompress(_ptr(d_container), nb, _ptr(d_out), out_cap, _ptr(dn),
+                                  _ptr(ws), ws.numel(), _ptr(st), _stream(stream)),
+           "huff_lzss_decompress")
+    if not sync:
+        return d_out, None, st
+    n = int(dn.item())
+    return d_out[:n], n, st
 
 
 # ---------------------------------------------------------------- Method 3

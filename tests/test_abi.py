@@ -102,3 +102,23 @@ def test_next_row_sizes_and_argument_checks(lib):
     assert lib.huff_mtf_inverse(none, 16, 0, none, none, 0, none) == hg.HUFF_ERR_INVALID_ARG
     assert lib.huff_m3_compress(none, 16, 4, 16, 16384, 2, none, 0, none, none, 0, none,
                                 none) == hg.HUFF_ERR_INVALID_ARG
+
+
+@pytest.mark.parametrize("params", [(1024, 12, 24, 8, 2), (8, 2, 5, 4, 1), (4096, 16, 32, 8, 1),
+                                    (2, 1, 1, 1, 1)])
+def test_lzss_sizes_bound_the_oracle(lib, params):
+    """huff_lzss_max_size holds the oracle's container on real inputs and its
+    own worst-case bound; invalid parameters and segment sizes give 0."""
+    import numpy as np
+    import synth
+    P = hg._lzss_params(params)
+    for n, seg in [(0, 16), (1, 16), (100, 16), (3000, 1024), (5000, 4096)]:
+        bound = lib.huff_lzss_max_size(n, seg, P)
+        assert bound >= oracle.lzss_segmented_max_size(n, seg, params)
+        for x in (synth.bitstream(n, 1), synth.uniform(n, 2)):
+            st, c = oracle.lzss_segmented_compress(x, seg, params)
+            assert st == oracle.OK and c.size <= bound
+        assert lib.huff_lzss_workspace_size(n, seg, P) > 0
+    assert lib.huff_lzss_max_size(100, 24, P) == 0  # segment not a multiple of 16
+    bad = hg._lzss_params((1000, 12, 24, 8, 2))
+    assert lib.huff_lzss_max_size(100, 16, bad) == 0
