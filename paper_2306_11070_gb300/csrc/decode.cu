@@ -41,9 +41,11 @@
 // emits nothing: the lane waits on it until the next window resolves it.
 // Between windows each lane tops up its input ring in shared memory with
 // 16-byte cp.async copies that bypass L1 (eight 16-byte cells per lane) and
-// stores every completed 16-byte group of its 128-byte output ring (laid out
-// [word][lane], so a warp's accesses never share a bank) with one 16-byte
-// global store.  The next input word is always preloaded, so the ring's
+// stores every completed group of its 128-byte output ring (laid out
+// [word][lane], so a warp's accesses never share a bank) with one global
+// store: 32-byte groups and 256-bit stores where the chunk's output is
+// 32-byte aligned (each lane's write a whole sector), else 16-byte groups.
+// The ring holds < 32 unflushed bytes, a window's <= 65 and 3 pending.  The next input word is always preloaded, so the ring's
 // latency stays off the per-codeword dependency chain.  The decoded codeword
 // sequence is exactly the sequential one, so the stream checks are those of
 // a sequential decoder.

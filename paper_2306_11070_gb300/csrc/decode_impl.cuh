@@ -691,6 +691,30 @@ __device__ __forceinline__ void flush_groups(uint8_t *ob, const OutQ &ow, uint32
     }
 }
 
+// Store the complete 32-byte groups of [fl, q) from the output ring, for an
+// output ob that is 32-byte aligned: one 256-bit store per group, so each
+// lane's write is a whole sector (measured on 1 GiB text: 0.87 -> 0.80 ms
+// against 16-byte groups).
+__device__ __forceinline__ void flush_groups32(uint8_t *ob, const OutQ &ow, uint32_t &fl, uint32_t q)
+{
+    uint32_t hs = fl & ~31u;
+    while (q >= hs + 32) {
+        if (fl == hs) {
+            const uint32_t w = hs >> 2;
+            asm volatile("st.global.v8.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};" ::"l"(ob + hs),
+                         "r"(ow.word_row(w)), "r"(ow.word_row(w + 1)), "r"(ow.word_row(w + 2)),
+                         "r"(ow.word_row(w + 3)), "r"(ow.word_row(w + 4)), "r"(ow.word_row(w + 5)),
+                         "r"(ow.word_row(w + 6)), "r"(ow.word_row(w + 7))
+                         : "memory");
+        } else {
+            for (uint32_t b = fl; b < hs + 32; ++b)
+                ob[b] = (uint8_t)ow.byte_at(b);
+        }
+        hs += 32;
+        fl = hs;
+    }
+}
+
 // Decode warp task `task` of stream si with S lanes per chunk (32/S chunks
 // per warp).  in_col / out_col: shared addresses of this lane's columns of
 // the warp's rings (the output block 4 KiB aligned).  Returns true
@@ -870,6 +894,7 @@ __device__ __forceinline__ bool decode_task_s(const StreamInfo &si, uint32_t S_a
         OutQ ow;
         bool act = todo > 0;
         uint8_t *const ob = si.out + c * cs;  // chunk output, 16-byte aligned
+        const bool wide = (reinterpret_cast<uintptr_t>(ob) & 31u) == 0;
         const uint32_t qend = O + todo;
         uint32_t pos = entry, q = O, fl = O;  // q: next byte, fl: first unflushed byte
         ow.start(out_s, O);
@@ -966,8 +991,12 @@ __device__ __forceinline__ bool decode_task_s(const StreamInfo &si, uint32_t S_a
                     rs.top_up();
             }
             cp_async_wait<3>();
-            if (!bad)
-                flush_groups(ob, ow, fl, q);
+            if (!bad) {
+                if (wide)
+                    flush_groups32(ob, ow, fl, q);
+                else
+                    flush_groups(ob, ow, fl, q);
+            }
         }
         cp_async_wait<0>();
         if (!bad) {
