@@ -13,7 +13,11 @@
 // until no group has two members or the compared prefix covers the longest
 // block (then the remaining groups are equal rotations, already in start
 // order since every pass is stable and the first order is by position).
-// The sorts are stable LSD radix passes over only the key bits in use.
+// The sorts are stable LSD radix passes over only the key bits in use.  In
+// rounds r >= 1 the active list is already in group order, so only each
+// group's members need sorting: groups that fit one CTA's window (most of
+// them on text) are sorted in shared memory in place, and only the members
+// of the larger groups go through the global radix passes.
 //
 // Inverse: LF[p] = the slot of row p's last byte in a stable sort of the
 // last column by (block, byte); the block is the walk p -> LF[p] from the
@@ -97,6 +101,233 @@ __global__ void k_bwt_round_keys(const uint32_t *sa, const uint32_t *rk, const u
     }
 }
 
+// ---- sorting the small groups of a round in shared memory ------------------
+// The active list of round r >= 1 is in group order (its keys' high bits, the
+// group number, never decrease), so sorting it means sorting every group's
+// members by the low bits.  CTA t takes the groups that start in the window
+// [t W, (t+1) W) of the list; they end before the first group start of the
+// next window, so its range [a, b) is at most 2 W long, unless the last group
+// starting in the window runs past the next one: such a group (more than W
+// members) is left out (range [a, L)) and marked uncovered for the global
+// passes.  Sorting within groups keeps every key's group bits at its index,
+// so the start tests of neighbouring CTAs read the same groups whether or
+// not a range beside them has been rewritten; ranges are disjoint and each is
+// read into registers before it is written back.  In shared memory a key is
+// (group index within the range, low bits): group numbers skip the groups
+// already resolved, so the range's own numbering keeps the key to 32 bits
+// (else the range is left to the global passes).  Stable 8-bit passes rank
+// like the global scatter (warps own consecutive elements, equal digits in
+// order by __match_any_sync and per-warp running counts); the group bits
+// written back are those already at each index.
+constexpr int kSegThreads = 512;
+constexpr int kSegWarps = kSegThreads / 32;
+constexpr uint32_t kSegWin = 2048;
+constexpr uint32_t kSegCap = 2 * kSegWin;
+constexpr uint32_t kSegItems = kSegCap / kSegThreads;     // 8 consecutive elements per thread
+constexpr uint32_t kSegSteps = kSegCap / kSegWarps / 32;  // 8 warp steps per pass
+constexpr size_t kSegSmem = (4 * (size_t)kSegCap + (size_t)kSegWarps * 256 + 256) * 4;
+
+__global__ void __launch_bounds__(kSegThreads) k_seg_sort(uint64_t *key, uint32_t *val, uint32_t count,
+                                                          uint32_t lo_bits, uint32_t *cov)
+{
+    extern __shared__ __align__(16) uint32_t seg_sm[];
+    uint32_t *sk = seg_sm;                    // [2][kSegCap] range keys
+    uint32_t *sv = sk + 2 * kSegCap;          // [2][kSegCap] values
+    uint32_t *wcnt = sv + 2 * kSegCap;        // [kSegWarps][256]
+    uint32_t *dstart = wcnt + kSegWarps * 256;  // [256]
+    __shared__ uint32_t s_a, s_b, s_l, s_ws[kSegWarps];
+    const uint32_t tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    const uint64_t w0 = (uint64_t)blockIdx.x * kSegWin;
+    const uint64_t w1 = w0 + kSegWin < count ? w0 + kSegWin : count;
+    const uint64_t w2 = w0 + kSegCap < count ? w0 + kSegCap : count;
+    if (tid == 0) {
+        s_a = kNil;
+        s_b = kNil;
+        s_l = 0;
+    }
+    __syncthreads();
+    {  // group starts in [w0, w2): 8 consecutive elements per thread, one atomic per warp
+        uint32_t a = kNil, l = 0, b = kNil;
+        const uint64_t k0 = w0 + (uint64_t)tid * kSegItems;
+        uint64_t prev = k0 > 0 && k0 - 1 < count ? key[k0 - 1] >> lo_bits : ~0ull;
+#pragma unroll
+        for (uint32_t j = 0; j < kSegItems; ++j) {
+            const uint64_t k = k0 + j;
+            if (k < w2) {
+                const uint64_t g = key[k] >> lo_bits;
+                if (k == 0 || g != prev) {
+                    const uint32_t r = (uint32_t)(k - w0);
+                    if (k < w1) {
+                        a = r < a ? r : a;
+                        l = r > l ? r : l;
+                    } else {
+                        b = r < b ? r : b;
+                    }
+                }
+                prev = g;
+            }
+        }
+        a = __reduce_min_sync(0xffffffffu, a);
+        b = __reduce_min_sync(0xffffffffu, b);
+        l = __reduce_max_sync(0xffffffffu, l);
+        if (lane == 0) {
+            atomicMin(&s_a, a);
+            atomicMin(&s_b, b);
+            atomicMax(&s_l, l);
+        }
+    }
+    __syncthreads();
+    const uint32_t a = s_a;
+    if (a == kNil)
+        return;  // no group starts in this window
+    const uint32_t b = s_b != kNil ? s_b : (w2 == count ? (uint32_t)(w2 - w0) : s_l);
+    if (b <= a)
+        return;
+    const uint32_t m = b - a;
+    const uint64_t lo_mask = (1ull << lo_bits) - 1;
+    // the range into registers, 8 consecutive elements per thread, with the
+    // index of each element's group within the range
+    const uint64_t r0 = w0 + a + (uint64_t)tid * kSegItems;
+    uint64_t kk[kSegItems];
+    uint32_t gl[kSegItems];
+    uint32_t starts = 0;
+    {
+        uint64_t prev = tid > 0 && tid * kSegItems < m ? key[r0 - 1] >> lo_bits : 0ull;
+#pragma unroll
+        for (uint32_t j = 0; j < kSegItems; ++j) {
+            const uint32_t i = tid * kSegItems + j;
+            kk[j] = i < m ? key[r0 + j] : 0ull;
+            const uint64_t g = kk[j] >> lo_bits;
+            starts += (i > 0 && i < m && g != prev) ? 1u : 0u;
+            gl[j] = starts;  // inclusive count within the thread
+            prev = g;
+        }
+    }
+    uint32_t groups;
+    const uint32_t before = srt::block_excl_scan(starts, s_ws, groups);  // 512 threads
+    if (((uint64_t)(groups + 1) << lo_bits) - 1 > 0xffffffffull)
+        return;  // keys of this range wider than 32 bits: global passes
+    const uint32_t bits = 64 - __clzll((long long)((((uint64_t)groups + 1) << lo_bits) - 1));
+#pragma unroll
+    for (uint32_t j = 0; j < kSegItems; ++j) {
+        const uint32_t i = tid * kSegItems + j;
+        if (i < m) {
+            sk[i] = (uint32_t)(((uint64_t)(before + gl[j]) << lo_bits) | (kk[j] & lo_mask));
+            sv[i] = val[r0 + j];
+        }
+    }
+    // warp w ranks the elements [w * steps * 32, (w + 1) * steps * 32): every
+    // warp takes an equal share of the range, in element order
+    const uint32_t steps = (m + kSegThreads - 1) / kSegThreads;
+    uint32_t cur = 0;
+    for (uint32_t shift = 0; shift < bits; shift += 8) {
+        for (uint32_t i = tid; i < kSegWarps * 256; i += kSegThreads)
+            wcnt[i] = 0;
+        __syncthreads();
+        const uint32_t *ck = sk + cur * kSegCap, *cv = sv + cur * kSegCap;
+        uint32_t rank[kSegSteps], dg[kSegSteps];
+#pragma unroll
+        for (uint32_t j = 0; j < kSegSteps; ++j) {
+            if (j >= steps)
+                break;
+            const uint32_t e = (w * steps + j) * 32 + lane;
+            const uint32_t d = e < m ? (ck[e] >> shift) & 255u : 256u;
+            const uint32_t mask = __match_any_sync(0xffffffffu, d);
+            rank[j] = d < 256u ? wcnt[w * 256 + d] + __popc(mask & srt::lanemask_lt()) : 0u;
+            __syncwarp();
+            if (d < 256u && lane == (uint32_t)__ffs(mask) - 1)
+                wcnt[w * 256 + d] += __popc(mask);
+            __syncwarp();
+            dg[j] = d;
+        }
+        __syncthreads();
+        // per digit: exclusive prefix over the warps, then over the digits
+        uint32_t run = 0, x = 0;
+        if (tid < 256) {
+#pragma unroll
+            for (int ww = 0; ww < kSegWarps; ++ww) {
+                const uint32_t t = wcnt[ww * 256 + tid];
+                wcnt[ww * 256 + tid] = run;
+                run += t;
+            }
+            x = run;
+#pragma unroll
+            for (int d = 1; d < 32; d <<= 1) {
+                const uint32_t y = __shfl_up_sync(0xffffffffu, x, d);
+                if (lane >= (uint32_t)d)
+                    x += y;
+            }
+            if (lane == 31)
+                s_ws[w] = x;
+        }
+        __syncthreads();
+        if (tid < 256) {
+            uint32_t pre = 0;
+            for (uint32_t ww = 0; ww < w; ++ww)
+                pre += s_ws[ww];
+            dstart[tid] = pre + x - run;
+        }
+        __syncthreads();
+        uint32_t *nk = sk + (cur ^ 1) * kSegCap, *nv = sv + (cur ^ 1) * kSegCap;
+#pragma unroll
+        for (uint32_t j = 0; j < kSegSteps; ++j) {
+            if (j >= steps)
+                break;
+            const uint32_t e = (w * steps + j) * 32 + lane;
+            if (dg[j] < 256u) {
+                const uint32_t q = dstart[dg[j]] + wcnt[w * 256 + dg[j]] + rank[j];
+                nk[q] = ck[e];
+                nv[q] = cv[e];
+            }
+        }
+        __syncthreads();
+        cur ^= 1;
+    }
+    const uint32_t *ck = sk + cur * kSegCap, *cv = sv + cur * kSegCap;
+#pragma unroll
+    for (uint32_t j = 0; j < kSegItems; ++j) {
+        const uint32_t i = tid * kSegItems + j;
+        if (i < m) {
+            key[r0 + j] = (kk[j] & ~lo_mask) | ((uint64_t)ck[i] & lo_mask);
+            val[r0 + j] = cv[i];
+            cov[r0 + j] = 1u;
+        }
+    }
+}
+
+// flags[k] = 1 - cov[k]: the members of groups left to the global passes
+__global__ void k_uncovered(uint32_t *cov, uint32_t count)
+{
+    for (uint32_t k = blockIdx.x * kEw + threadIdx.x; k < count; k += gridDim.x * kEw)
+        cov[k] = 1u - cov[k];
+}
+
+// gather the uncovered elements (inclusive scan of their flags in incl) in
+// list order, with their list indices
+__global__ void k_gather_uncovered(const uint64_t *key, const uint32_t *val, const uint32_t *incl,
+                                   uint32_t count, uint64_t *gk, uint32_t *gv, uint32_t *idx)
+{
+    for (uint32_t k = blockIdx.x * kEw + threadIdx.x; k < count; k += gridDim.x * kEw) {
+        const uint32_t c = incl[k];
+        if (c != (k ? incl[k - 1] : 0u)) {
+            gk[c - 1] = key[k];
+            gv[c - 1] = val[k];
+            idx[c - 1] = k;
+        }
+    }
+}
+
+// the sorted uncovered elements back to their list indices: each large group
+// owns the same indices before and after, so list order is kept
+__global__ void k_scatter_uncovered(const uint64_t *gk, const uint32_t *gv, const uint32_t *idx,
+                                    uint32_t count, uint64_t *key, uint32_t *val)
+{
+    for (uint32_t j = blockIdx.x * kEw + threadIdx.x; j < count; j += gridDim.x * kEw) {
+        key[idx[j]] = gk[j];
+        val[idx[j]] = gv[j];
+    }
+}
+
 // ---- refining the groups of a sorted active list ---------------------------
 // Element k of the sorted list starts a group when its key differs from
 // k-1's (head), and its group has two members or more unless it is a head
@@ -104,7 +335,11 @@ __global__ void k_bwt_round_keys(const uint32_t *sa, const uint32_t *rk, const u
 // element, the number of heads up to it (its group's number + 1), the number
 // of flagged elements before it (its place in the next active list) and the
 // largest head slot up to it (its group's first slot: slots increase along
-// the list, so the last head wins), the three carried together.
+// the list, so the last head wins), the three carried together.  From round 1
+// on, a head that also starts a group of the round before (the key's group
+// bits change there) carries a mark in the slot's low bit: elements whose
+// last head is marked keep the first slot they had, so their rank is not
+// written again.
 constexpr int kRfThreads = 512;
 constexpr int kRfItems = 8;
 constexpr uint32_t kRfTile = kRfThreads * kRfItems;
@@ -160,7 +395,7 @@ struct RfItems {
 
 // the values of this thread's kRfItems consecutive elements
 __device__ __forceinline__ RfItems rf_items(const uint64_t *key, const uint32_t *act,
-                                            uint32_t count, uint64_t base)
+                                            uint32_t count, uint64_t base, uint32_t gbits)
 {
     uint64_t kk[kRfItems + 2];
 #pragma unroll
@@ -175,20 +410,22 @@ __device__ __forceinline__ RfItems rf_items(const uint64_t *key, const uint32_t 
         const bool ok = k < count;
         const bool hd = ok && (k == 0 || kk[j + 1] != kk[j]);
         const bool nh = k + 1 >= count || kk[j + 2] != kk[j + 1];
+        // gbits < 64: the key's bits from gbits up are the previous round's group
+        const bool old = gbits < 64 && hd && (k == 0 || (kk[j + 1] >> gbits) != (kk[j] >> gbits));
         r.head[j] = hd ? 1u : 0u;
         r.flag[j] = (ok && !(hd && nh)) ? 1u : 0u;
-        r.slot[j] = hd ? act[k] : 0u;
+        r.slot[j] = hd ? (act[k] << 1) | (old ? 1u : 0u) : 0u;
     }
     return r;
 }
 
 __global__ void __launch_bounds__(kRfThreads) k_refine_tiles(const uint64_t *key, const uint32_t *act,
-                                                             uint32_t count, uint32_t *ph,
-                                                             uint32_t *pf, uint32_t *pm)
+                                                             uint32_t count, uint32_t gbits,
+                                                             uint32_t *ph, uint32_t *pf, uint32_t *pm)
 {
     __shared__ uint32_t ws[kRfThreads / 32];
     const uint64_t base = (uint64_t)blockIdx.x * kRfTile + (uint64_t)threadIdx.x * kRfItems;
-    const RfItems r = rf_items(key, act, count, base);
+    const RfItems r = rf_items(key, act, count, base, gbits);
     uint32_t h = 0, f = 0, m = 0;
 #pragma unroll
     for (int j = 0; j < kRfItems; ++j) {
@@ -240,13 +477,13 @@ __global__ void __launch_bounds__(kRfThreads) k_refine_parts(uint32_t *ph, uint3
 // elements of groups still unresolved appended to the next active list with
 // their group numbers
 __global__ void __launch_bounds__(kRfThreads) k_refine_apply(
-    const uint64_t *key, const uint32_t *val, const uint32_t *act, uint32_t count,
+    const uint64_t *key, const uint32_t *val, const uint32_t *act, uint32_t count, uint32_t gbits,
     const uint32_t *ph, const uint32_t *pf, const uint32_t *pm, uint32_t *sa, uint32_t *rk,
     uint32_t *act2, uint32_t *grp2)
 {
     __shared__ uint32_t ws[kRfThreads / 32];
     const uint64_t base = (uint64_t)blockIdx.x * kRfTile + (uint64_t)threadIdx.x * kRfItems;
-    const RfItems r = rf_items(key, act, count, base);
+    const RfItems r = rf_items(key, act, count, base, gbits);
     uint32_t h = 0, f = 0, m = 0;
 #pragma unroll
     for (int j = 0; j < kRfItems; ++j) {
@@ -269,7 +506,8 @@ __global__ void __launch_bounds__(kRfThreads) k_refine_apply(
         gm = r.slot[j] > gm ? r.slot[j] : gm;
         const uint32_t a = act[k], v = val[k];
         sa[a] = v;
-        rk[v] = gm;
+        if (!(gm & 1u))  // else the group's first slot is unchanged
+            rk[v] = gm >> 1;
         if (r.flag[j]) {
             act2[gf] = a;
             grp2[gf] = gh - 1;
@@ -339,16 +577,57 @@ cudaError_t sort_keys(FwdWs &w, uint32_t count, uint32_t bits, cudaStream_t s, u
     return e;
 }
 
+// sort a round's active list (keys in k0/v0, already in group order) by its
+// key bits [0, bits): small groups in shared memory in place, the members of
+// the others gathered into k1/v1 (the second half as the ping-pong buffer),
+// sorted by the global passes and put back.  If they are more than half the
+// list, the whole list takes the global passes.  act2 / grp2 are free until
+// the refinement and hold the indices and flags.
+cudaError_t sort_groups(FwdWs &w, uint32_t count, uint32_t lo_bits, uint32_t bits, cudaStream_t s,
+                        uint64_t *&ks, uint32_t *&vs)
+{
+    static KernelSetup setup;
+    int per_sm = 0;
+    cudaError_t e = kernel_setup(setup, (const void *)k_seg_sort, kSegThreads, kSegSmem, &per_sm);
+    if (e != cudaSuccess)
+        return e;
+    uint32_t *cov = w.grp2, *idx = w.act2;
+    if ((e = cudaMemsetAsync(cov, 0, 4ull * count, s)) != cudaSuccess)
+        return e;
+    k_seg_sort<<<div_up(count, kSegWin), kSegThreads, kSegSmem, s>>>(w.k0, w.v0, count, lo_bits, cov);
+    k_uncovered<<<ew_grid(count), kEw, 0, s>>>(cov, count);
+    if ((e = scan_u32(cov, cov, count, true, w.part, w.scal + 2, s)) != cudaSuccess)
+        return e;
+    uint32_t big = 0;
+    if ((e = cudaMemcpyAsync(&big, w.scal + 2, sizeof(big), cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
+        (e = cudaStreamSynchronize(s)) != cudaSuccess)
+        return e;
+    ks = w.k0;
+    vs = w.v0;
+    if (big == 0)
+        return cudaSuccess;
+    if (2ull * big > count)
+        return sort_keys(w, count, bits, s, ks, vs);
+    k_gather_uncovered<<<ew_grid(count), kEw, 0, s>>>(w.k0, w.v0, cov, count, w.k1, w.v1, idx);
+    bool f = false;
+    if ((e = radix_sort_bits(w.k1, w.v1, w.k1 + big, w.v1 + big, big, 0, bits, w.radix, s, f)) !=
+        cudaSuccess)
+        return e;
+    k_scatter_uncovered<<<ew_grid(big), kEw, 0, s>>>(f ? w.k1 + big : w.k1, f ? w.v1 + big : w.v1,
+                                                      idx, big, w.k0, w.v0);
+    return cudaGetLastError();
+}
+
 // split the groups of the sorted active list; returns the number still
 // unresolved and the number of groups of the list (host values)
 cudaError_t refine(FwdWs &w, const uint64_t *ks, const uint32_t *vs, uint32_t count,
-                   cudaStream_t s, uint32_t &n_act, uint32_t &groups)
+                   uint32_t gbits, cudaStream_t s, uint32_t &n_act, uint32_t &groups)
 {
     const uint32_t tiles = div_up(count, kRfTile);
     uint32_t *ph = w.part, *pf = w.part + tiles, *pm = w.part + 2 * tiles;
-    k_refine_tiles<<<tiles, kRfThreads, 0, s>>>(ks, w.act, count, ph, pf, pm);
+    k_refine_tiles<<<tiles, kRfThreads, 0, s>>>(ks, w.act, count, gbits, ph, pf, pm);
     k_refine_parts<<<1, kRfThreads, 0, s>>>(ph, pf, pm, tiles, w.scal);
-    k_refine_apply<<<tiles, kRfThreads, 0, s>>>(ks, vs, w.act, count, ph, pf, pm, w.sa, w.rk,
+    k_refine_apply<<<tiles, kRfThreads, 0, s>>>(ks, vs, w.act, count, gbits, ph, pf, pm, w.sa, w.rk,
                                                  w.act2, w.grp2);
     uint32_t h[2];
     cudaError_t e;
@@ -622,15 +901,15 @@ huff_status_t huff_bwt_forward(const uint8_t *d_in, uint64_t n, uint32_t block, 
     if (sort_keys(w, N, 32 + bit_width(blocks - 1), s, ks, vs) != cudaSuccess)
         return HUFF_ERR_CUDA;
     uint32_t n_act = 0, groups = 0;
-    if (refine(w, ks, vs, N, s, n_act, groups) != cudaSuccess)
+    if (refine(w, ks, vs, N, 64, s, n_act, groups) != cudaSuccess)
         return HUFF_ERR_CUDA;
     for (uint64_t h = 4; n_act > 0 && h < mmax; h *= 2) {
         const uint32_t lo_bits = bit_width(mmax - 1);
         k_bwt_round_keys<<<ew_grid(n_act), kEw, 0, s>>>(w.sa, w.rk, w.act, w.grp, n_act, N, block, h,
                                                         lo_bits, w.k0, w.v0);
-        if (sort_keys(w, n_act, lo_bits + bit_width(groups - 1), s, ks, vs) != cudaSuccess)
+        if (sort_groups(w, n_act, lo_bits, lo_bits + bit_width(groups - 1), s, ks, vs) != cudaSuccess)
             return HUFF_ERR_CUDA;
-        if (refine(w, ks, vs, n_act, s, n_act, groups) != cudaSuccess)
+        if (refine(w, ks, vs, n_act, lo_bits, s, n_act, groups) != cudaSuccess)
             return HUFF_ERR_CUDA;
     }
     k_bwt_output<<<ew_grid(n), kEw, 0, s>>>(d_in, w.sa, N, block, d_last, d_primary);

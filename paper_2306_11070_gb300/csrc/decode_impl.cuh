@@ -1002,6 +1002,8 @@ __device__ __forceinline__ bool decode_task_s(const StreamInfo &si, uint32_t S_a
         if (!bad) {
             if (todo)
                 ow.store_partial();  // the bytes of the word being filled
+            if (wide)
+                flush_groups32(ob, ow, fl, q);
             for (uint32_t b = fl; b < q; ++b)
                 ob[b] = (uint8_t)ow.byte_at(b);
             if (todo && final_seg && c + 1 < chunks && pos != lim)
