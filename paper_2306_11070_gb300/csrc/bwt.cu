@@ -123,48 +123,50 @@ constexpr int kSegThreads = 512;
 constexpr int kSegWarps = kSegThreads / 32;
 constexpr uint32_t kSegWin = 2048;
 constexpr uint32_t kSegCap = 2 * kSegWin;
-constexpr uint32_t kSegItems = kSegCap / kSegThreads;     // 8 consecutive elements per thread
-constexpr uint32_t kSegSteps = kSegCap / kSegWarps / 32;  // 8 warp steps per pass
-constexpr size_t kSegSmem = (4 * (size_t)kSegCap + (size_t)kSegWarps * 256 + 256) * 4;
+constexpr uint32_t kSegSteps = kSegCap / kSegWarps / 32;  // at most 8 warp steps per pass
+constexpr size_t kSegSmem = (5 * (size_t)kSegCap + (size_t)kSegWarps * 256 + 256) * 4;
 
 __global__ void __launch_bounds__(kSegThreads) k_seg_sort(uint64_t *key, uint32_t *val, uint32_t count,
                                                           uint32_t lo_bits, uint32_t *cov)
 {
     extern __shared__ __align__(16) uint32_t seg_sm[];
-    uint32_t *sk = seg_sm;                    // [2][kSegCap] range keys
-    uint32_t *sv = sk + 2 * kSegCap;          // [2][kSegCap] values
-    uint32_t *wcnt = sv + 2 * kSegCap;        // [kSegWarps][256]
+    uint32_t *sk = seg_sm;                      // [2][kSegCap] range keys
+    uint32_t *sv = sk + 2 * kSegCap;            // [2][kSegCap] values
+    uint32_t *sg = sv + 2 * kSegCap;            // [kSegCap] group numbers of [w0, w2)
+    uint32_t *wcnt = sg + kSegCap;              // [kSegWarps][256]
     uint32_t *dstart = wcnt + kSegWarps * 256;  // [256]
-    __shared__ uint32_t s_a, s_b, s_l, s_ws[kSegWarps];
+    __shared__ uint32_t s_a, s_b, s_l, s_gprev, s_ws[kSegWarps];
     const uint32_t tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
     const uint64_t w0 = (uint64_t)blockIdx.x * kSegWin;
     const uint64_t w1 = w0 + kSegWin < count ? w0 + kSegWin : count;
     const uint64_t w2 = w0 + kSegCap < count ? w0 + kSegCap : count;
+    const uint32_t span = (uint32_t)(w2 - w0), win = (uint32_t)(w1 - w0);
+    const uint64_t lo_mask = (1ull << lo_bits) - 1;
+    // [w0, w2) into shared memory, coalesced: group numbers (they fit 32 bits:
+    // fewer than count) and low bits (in the second key buffer for now)
+    for (uint32_t i = tid; i < span; i += kSegThreads) {
+        const uint64_t k = key[w0 + i];
+        sg[i] = (uint32_t)(k >> lo_bits);
+        sk[kSegCap + i] = (uint32_t)(k & lo_mask);
+    }
     if (tid == 0) {
         s_a = kNil;
         s_b = kNil;
         s_l = 0;
+        s_gprev = w0 > 0 ? (uint32_t)(key[w0 - 1] >> lo_bits) : kNil;
     }
     __syncthreads();
-    {  // group starts in [w0, w2): 8 consecutive elements per thread, one atomic per warp
+    {  // group starts in [w0, w2), one atomic per warp
         uint32_t a = kNil, l = 0, b = kNil;
-        const uint64_t k0 = w0 + (uint64_t)tid * kSegItems;
-        uint64_t prev = k0 > 0 && k0 - 1 < count ? key[k0 - 1] >> lo_bits : ~0ull;
-#pragma unroll
-        for (uint32_t j = 0; j < kSegItems; ++j) {
-            const uint64_t k = k0 + j;
-            if (k < w2) {
-                const uint64_t g = key[k] >> lo_bits;
-                if (k == 0 || g != prev) {
-                    const uint32_t r = (uint32_t)(k - w0);
-                    if (k < w1) {
-                        a = r < a ? r : a;
-                        l = r > l ? r : l;
-                    } else {
-                        b = r < b ? r : b;
-                    }
+        for (uint32_t i = tid; i < span; i += kSegThreads) {
+            const bool st = i == 0 ? (w0 == 0 || sg[0] != s_gprev) : sg[i] != sg[i - 1];
+            if (st) {
+                if (i < win) {
+                    a = i < a ? i : a;
+                    l = i > l ? i : l;
+                } else {
+                    b = i < b ? i : b;
                 }
-                prev = g;
             }
         }
         a = __reduce_min_sync(0xffffffffu, a);
@@ -180,45 +182,41 @@ __global__ void __launch_bounds__(kSegThreads) k_seg_sort(uint64_t *key, uint32_
     const uint32_t a = s_a;
     if (a == kNil)
         return;  // no group starts in this window
-    const uint32_t b = s_b != kNil ? s_b : (w2 == count ? (uint32_t)(w2 - w0) : s_l);
+    const uint32_t b = s_b != kNil ? s_b : (w2 == count ? span : s_l);
     if (b <= a)
         return;
     const uint32_t m = b - a;
-    const uint64_t lo_mask = (1ull << lo_bits) - 1;
-    // the range into registers, 8 consecutive elements per thread, with the
-    // index of each element's group within the range
-    const uint64_t r0 = w0 + a + (uint64_t)tid * kSegItems;
-    uint64_t kk[kSegItems];
-    uint32_t gl[kSegItems];
-    uint32_t starts = 0;
-    {
-        uint64_t prev = tid > 0 && tid * kSegItems < m ? key[r0 - 1] >> lo_bits : 0ull;
-#pragma unroll
-        for (uint32_t j = 0; j < kSegItems; ++j) {
-            const uint32_t i = tid * kSegItems + j;
-            kk[j] = i < m ? key[r0 + j] : 0ull;
-            const uint64_t g = kk[j] >> lo_bits;
-            starts += (i > 0 && i < m && g != prev) ? 1u : 0u;
-            gl[j] = starts;  // inclusive count within the thread
-            prev = g;
-        }
+    // warp w ranks the elements [w * steps * 32, (w + 1) * steps * 32) of the
+    // range in every pass: an equal share each, in element order
+    const uint32_t steps = (m + kSegThreads - 1) / kSegThreads;
+    // each element's group index within the range: starts counted by ballots
+    // over the warp's elements, then across the warps
+    uint32_t mine = 0;
+    for (uint32_t j = 0; j < steps; ++j) {
+        const uint32_t i = (w * steps + j) * 32 + lane;
+        const bool st = i > 0 && i < m && sg[a + i] != sg[a + i - 1];
+        mine += __popc(__ballot_sync(0xffffffffu, st));
     }
     uint32_t groups;
-    const uint32_t before = srt::block_excl_scan(starts, s_ws, groups);  // 512 threads
+    const uint32_t wbefore = srt::block_excl_scan(lane == 0 ? mine : 0u, s_ws, groups);
+    const uint32_t wbase = __shfl_sync(0xffffffffu, wbefore, 0);
     if (((uint64_t)(groups + 1) << lo_bits) - 1 > 0xffffffffull)
         return;  // keys of this range wider than 32 bits: global passes
     const uint32_t bits = 64 - __clzll((long long)((((uint64_t)groups + 1) << lo_bits) - 1));
-#pragma unroll
-    for (uint32_t j = 0; j < kSegItems; ++j) {
-        const uint32_t i = tid * kSegItems + j;
-        if (i < m) {
-            sk[i] = (uint32_t)(((uint64_t)(before + gl[j]) << lo_bits) | (kk[j] & lo_mask));
-            sv[i] = val[r0 + j];
+    {
+        uint32_t run = wbase;
+        for (uint32_t j = 0; j < steps; ++j) {
+            const uint32_t i = (w * steps + j) * 32 + lane;
+            const bool st = i > 0 && i < m && sg[a + i] != sg[a + i - 1];
+            const uint32_t mask = __ballot_sync(0xffffffffu, st);
+            if (i < m)
+                sk[i] = ((run + __popc(mask & srt::lanemask_le())) << lo_bits) | sk[kSegCap + a + i];
+            run += __popc(mask);
         }
     }
-    // warp w ranks the elements [w * steps * 32, (w + 1) * steps * 32): every
-    // warp takes an equal share of the range, in element order
-    const uint32_t steps = (m + kSegThreads - 1) / kSegThreads;
+    for (uint32_t i = tid; i < m; i += kSegThreads)
+        sv[i] = val[w0 + a + i];
+    __syncthreads();
     uint32_t cur = 0;
     for (uint32_t shift = 0; shift < bits; shift += 8) {
         for (uint32_t i = tid; i < kSegWarps * 256; i += kSegThreads)
@@ -284,14 +282,10 @@ __global__ void __launch_bounds__(kSegThreads) k_seg_sort(uint64_t *key, uint32_
         cur ^= 1;
     }
     const uint32_t *ck = sk + cur * kSegCap, *cv = sv + cur * kSegCap;
-#pragma unroll
-    for (uint32_t j = 0; j < kSegItems; ++j) {
-        const uint32_t i = tid * kSegItems + j;
-        if (i < m) {
-            key[r0 + j] = (kk[j] & ~lo_mask) | ((uint64_t)ck[i] & lo_mask);
-            val[r0 + j] = cv[i];
-            cov[r0 + j] = 1u;
-        }
+    for (uint32_t i = tid; i < m; i += kSegThreads) {
+        key[w0 + a + i] = ((uint64_t)sg[a + i] << lo_bits) | ((uint64_t)ck[i] & lo_mask);
+        val[w0 + a + i] = cv[i];
+        cov[w0 + a + i] = 1u;
     }
 }
 
@@ -393,16 +387,43 @@ struct RfItems {
     uint32_t head[kRfItems], flag[kRfItems], slot[kRfItems];
 };
 
-// the values of this thread's kRfItems consecutive elements
-__device__ __forceinline__ RfItems rf_items(const uint64_t *key, const uint32_t *act,
-                                            uint32_t count, uint64_t base, uint32_t gbits)
+// A tile's keys and slots staged in shared memory with coalesced loads, so
+// that each thread then reads its kRfItems consecutive elements from there.
+// Index t is stored at t + t / 8: a thread's 8 consecutive words and a warp's
+// consecutive fills then fall in distinct banks.
+__device__ __forceinline__ uint32_t rf_pad(uint32_t t) { return t + (t >> 3); }
+constexpr uint32_t kRfKeyWords = kRfTile + 2 + (kRfTile + 2) / 8 + 1;  // keys of [t0 - 1, t0 + kRfTile + 1)
+constexpr uint32_t kRfIdxWords = kRfTile + kRfTile / 8;
+constexpr size_t kRfTilesSmem = 8 * (size_t)kRfKeyWords + 4 * (size_t)kRfIdxWords;
+constexpr size_t kRfApplySmem = kRfTilesSmem + 4 * (size_t)kRfIdxWords;
+
+__device__ __forceinline__ void rf_stage(const uint64_t *key, const uint32_t *act, const uint32_t *val,
+                                         uint32_t count, uint64_t t0, uint64_t *skey, uint32_t *sact,
+                                         uint32_t *sval)
 {
+    for (uint32_t t = threadIdx.x; t < kRfTile + 2; t += kRfThreads) {
+        const uint64_t k = t0 + t;  // element k - 1
+        skey[rf_pad(t)] = (k >= 1 && k - 1 < count) ? key[k - 1] : 0ull;
+    }
+    for (uint32_t t = threadIdx.x; t < kRfTile; t += kRfThreads) {
+        const uint64_t k = t0 + t;
+        sact[rf_pad(t)] = k < count ? act[k] : 0u;
+        if (val)
+            sval[rf_pad(t)] = k < count ? val[k] : 0u;
+    }
+    __syncthreads();
+}
+
+// the values of this thread's kRfItems consecutive elements (from the stage)
+__device__ __forceinline__ RfItems rf_items(const uint64_t *skey, const uint32_t *sact, uint32_t count,
+                                            uint64_t t0, uint32_t gbits)
+{
+    const uint32_t t = threadIdx.x * kRfItems;
+    const uint64_t base = t0 + t;
     uint64_t kk[kRfItems + 2];
 #pragma unroll
-    for (int j = 0; j < kRfItems + 2; ++j) {
-        const uint64_t k = base + j;  // element k - 1
-        kk[j] = (k >= 1 && k - 1 < count) ? key[k - 1] : 0ull;
-    }
+    for (int j = 0; j < kRfItems + 2; ++j)
+        kk[j] = skey[rf_pad(t + j)];  // element base + j - 1
     RfItems r;
 #pragma unroll
     for (int j = 0; j < kRfItems; ++j) {
@@ -414,7 +435,7 @@ __device__ __forceinline__ RfItems rf_items(const uint64_t *key, const uint32_t 
         const bool old = gbits < 64 && hd && (k == 0 || (kk[j + 1] >> gbits) != (kk[j] >> gbits));
         r.head[j] = hd ? 1u : 0u;
         r.flag[j] = (ok && !(hd && nh)) ? 1u : 0u;
-        r.slot[j] = hd ? (act[k] << 1) | (old ? 1u : 0u) : 0u;
+        r.slot[j] = hd ? (sact[rf_pad(t + j)] << 1) | (old ? 1u : 0u) : 0u;
     }
     return r;
 }
@@ -423,9 +444,13 @@ __global__ void __launch_bounds__(kRfThreads) k_refine_tiles(const uint64_t *key
                                                              uint32_t count, uint32_t gbits,
                                                              uint32_t *ph, uint32_t *pf, uint32_t *pm)
 {
+    extern __shared__ __align__(16) uint64_t rf_sm[];
+    uint64_t *skey = rf_sm;
+    uint32_t *sact = reinterpret_cast<uint32_t *>(rf_sm + kRfKeyWords);
     __shared__ uint32_t ws[kRfThreads / 32];
-    const uint64_t base = (uint64_t)blockIdx.x * kRfTile + (uint64_t)threadIdx.x * kRfItems;
-    const RfItems r = rf_items(key, act, count, base, gbits);
+    const uint64_t t0 = (uint64_t)blockIdx.x * kRfTile;
+    rf_stage(key, act, nullptr, count, t0, skey, sact, nullptr);
+    const RfItems r = rf_items(skey, sact, count, t0, gbits);
     uint32_t h = 0, f = 0, m = 0;
 #pragma unroll
     for (int j = 0; j < kRfItems; ++j) {
@@ -475,15 +500,25 @@ __global__ void __launch_bounds__(kRfThreads) k_refine_parts(uint32_t *ph, uint3
 
 // sorted slots back into SA, new ranks scattered to the positions, and the
 // elements of groups still unresolved appended to the next active list with
-// their group numbers
+// their group numbers (staged in shared memory, where the keys were, and
+// written out coalesced)
 __global__ void __launch_bounds__(kRfThreads) k_refine_apply(
     const uint64_t *key, const uint32_t *val, const uint32_t *act, uint32_t count, uint32_t gbits,
     const uint32_t *ph, const uint32_t *pf, const uint32_t *pm, uint32_t *sa, uint32_t *rk,
     uint32_t *act2, uint32_t *grp2)
 {
+    extern __shared__ __align__(16) uint64_t rf_sm[];
+    uint64_t *skey = rf_sm;
+    uint32_t *sact = reinterpret_cast<uint32_t *>(rf_sm + kRfKeyWords);
+    uint32_t *sval = sact + kRfIdxWords;
+    uint32_t *so_act = reinterpret_cast<uint32_t *>(rf_sm);  // after the keys are read
+    uint32_t *so_grp = so_act + kRfIdxWords;
     __shared__ uint32_t ws[kRfThreads / 32];
-    const uint64_t base = (uint64_t)blockIdx.x * kRfTile + (uint64_t)threadIdx.x * kRfItems;
-    const RfItems r = rf_items(key, act, count, base, gbits);
+    const uint64_t t0 = (uint64_t)blockIdx.x * kRfTile;
+    rf_stage(key, act, val, count, t0, skey, sact, sval);
+    for (uint32_t t = threadIdx.x; t < kRfTile && t0 + t < count; t += kRfThreads)
+        sa[sact[rf_pad(t)]] = sval[rf_pad(t)];
+    const RfItems r = rf_items(skey, sact, count, t0, gbits);
     uint32_t h = 0, f = 0, m = 0;
 #pragma unroll
     for (int j = 0; j < kRfItems; ++j) {
@@ -493,26 +528,30 @@ __global__ void __launch_bounds__(kRfThreads) k_refine_apply(
     }
     uint32_t th, tf, tm;
     uint32_t gh = ph[blockIdx.x] + rf_block_scan(h, ws, th, AddOp(), 0u);
-    uint32_t gf = pf[blockIdx.x] + rf_block_scan(f, ws, tf, AddOp(), 0u);
-    const uint32_t xm = rf_block_scan(m, ws, tm, MaxOp(), 0u);
+    uint32_t lf = rf_block_scan(f, ws, tf, AddOp(), 0u);  // flagged before, within the tile
+    const uint32_t xm = rf_block_scan(m, ws, tm, MaxOp(), 0u);  // (its barriers: keys all read)
     const uint32_t pmb = pm[blockIdx.x];
     uint32_t gm = xm > pmb ? xm : pmb;
+    const uint32_t t = threadIdx.x * kRfItems;
 #pragma unroll
     for (int j = 0; j < kRfItems; ++j) {
-        const uint64_t k = base + j;
-        if (k >= count)
+        if (t0 + t + j >= count)
             break;
         gh += r.head[j];
         gm = r.slot[j] > gm ? r.slot[j] : gm;
-        const uint32_t a = act[k], v = val[k];
-        sa[a] = v;
         if (!(gm & 1u))  // else the group's first slot is unchanged
-            rk[v] = gm >> 1;
+            rk[sval[rf_pad(t + j)]] = gm >> 1;
         if (r.flag[j]) {
-            act2[gf] = a;
-            grp2[gf] = gh - 1;
+            so_act[rf_pad(lf)] = sact[rf_pad(t + j)];
+            so_grp[rf_pad(lf)] = gh - 1;
         }
-        gf += r.flag[j];
+        lf += r.flag[j];
+    }
+    __syncthreads();
+    const uint32_t pfb = pf[blockIdx.x];
+    for (uint32_t i = threadIdx.x; i < tf; i += kRfThreads) {
+        act2[pfb + i] = so_act[rf_pad(i)];
+        grp2[pfb + i] = so_grp[rf_pad(i)];
     }
 }
 
@@ -625,12 +664,19 @@ cudaError_t refine(FwdWs &w, const uint64_t *ks, const uint32_t *vs, uint32_t co
 {
     const uint32_t tiles = div_up(count, kRfTile);
     uint32_t *ph = w.part, *pf = w.part + tiles, *pm = w.part + 2 * tiles;
-    k_refine_tiles<<<tiles, kRfThreads, 0, s>>>(ks, w.act, count, gbits, ph, pf, pm);
-    k_refine_parts<<<1, kRfThreads, 0, s>>>(ph, pf, pm, tiles, w.scal);
-    k_refine_apply<<<tiles, kRfThreads, 0, s>>>(ks, vs, w.act, count, gbits, ph, pf, pm, w.sa, w.rk,
-                                                 w.act2, w.grp2);
-    uint32_t h[2];
+    static KernelSetup setup_tiles, setup_apply;
+    int per_sm = 0;
     cudaError_t e;
+    if ((e = kernel_setup(setup_tiles, (const void *)k_refine_tiles, kRfThreads, kRfTilesSmem,
+                          &per_sm)) != cudaSuccess ||
+        (e = kernel_setup(setup_apply, (const void *)k_refine_apply, kRfThreads, kRfApplySmem,
+                          &per_sm)) != cudaSuccess)
+        return e;
+    k_refine_tiles<<<tiles, kRfThreads, kRfTilesSmem, s>>>(ks, w.act, count, gbits, ph, pf, pm);
+    k_refine_parts<<<1, kRfThreads, 0, s>>>(ph, pf, pm, tiles, w.scal);
+    k_refine_apply<<<tiles, kRfThreads, kRfApplySmem, s>>>(ks, vs, w.act, count, gbits, ph, pf, pm,
+                                                           w.sa, w.rk, w.act2, w.grp2);
+    uint32_t h[2];
     if ((e = cudaGetLastError()) != cudaSuccess ||
         (e = cudaMemcpyAsync(h, w.scal, sizeof(h), cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
         (e = cudaStreamSynchronize(s)) != cudaSuccess)

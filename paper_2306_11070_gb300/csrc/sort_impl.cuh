@@ -151,6 +151,12 @@ __device__ __forceinline__ uint32_t lanemask_lt()
     asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
     return m;
 }
+__device__ __forceinline__ uint32_t lanemask_le()
+{
+    uint32_t m;
+    asm("mov.u32 %0, %%lanemask_le;" : "=r"(m));
+    return m;
+}
 
 __global__ void __launch_bounds__(kRadixThreads) k_radix_count(const uint64_t *keys, uint32_t count,
                                                                uint32_t shift, uint32_t *hist,
