@@ -172,6 +172,27 @@ def test_stream_bit_exact_and_round_trip(gen, n):
     _check_roundtrip(GENS[gen](n, 11 + n % 97))
 
 
+@pytest.mark.parametrize("shift", [16, 32])
+def test_decode_into_offset_output(shift):
+    """The decoder stores whole 32-byte groups only where a chunk's output is
+    32-byte aligned; an output 16 bytes past an aligned address takes the
+    16-byte path in every chunk (and 32 bytes the wide one), same bytes."""
+    n = (1 << 20) + 12345
+    x = synth.text(n, 21)
+    d, h, cb, st = gpu_codebook(x)
+    assert st == 0
+    out, nbytes, st = gpu_encode(d, cb, 16384)
+    assert st == 0
+    buf = torch.full((n + 64,), 0xA5, dtype=torch.uint8, device="cuda")
+    view = buf[shift:shift + n]
+    _, dn, dst = hg.huff_decode(out[:nbytes], d_out=view, out_cap=n)
+    torch.cuda.synchronize()
+    assert int(dst.item()) == 0 and int(dn.item()) == n
+    got = buf.cpu().numpy()
+    assert np.array_equal(got[shift:shift + n], x)
+    assert (got[:shift] == 0xA5).all() and (got[shift + n:] == 0xA5).all()
+
+
 @pytest.mark.parametrize("cs", [16, 32, 48, 1024, 4096, 4112, 65536])
 def test_chunk_sizes(cs):
     _check_roundtrip(synth.text(5 * 4096 + 77, 5), cs)
