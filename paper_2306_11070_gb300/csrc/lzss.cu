@@ -23,9 +23,14 @@
 // Compression: one warp per segment.  For each token the 32 lanes search
 // the window together: lane j tries distances j + 1, j + 33, j + 65, ...;
 // their sources all start at the same bit offset within a word, so each
-// candidate costs one new window word (read through L1), a funnel shift, an
-// XOR with the 32 look-ahead bits and a count of leading zeros; one warp max
-// over (length, -distance) keys picks the token.  Every lane keeps the same
+// candidate costs one window word, a funnel shift, an XOR with the 32
+// look-ahead bits (its bits past the longest allowed match forced to 1, so
+// the count of leading zeros is already capped) and a count of leading
+// zeros; one warp max over (length, -distance) keys picks the token, and a
+// match shorter than Lmin then reads as a literal.  For windows of 64 to
+// 16384 bits the words come from a per-warp ring in shared memory, filled 32
+// words at a time as the position advances and stored twice (at i and
+// i + R), so a token's candidates read one straight run of words, no wrap.  Every lane keeps the same
 // 64-bit output accumulator and lane 0 stores the completed words into the
 // segment's worst-case slot of the workspace; a one-CTA scan then lays out
 // the header and length table and a gather moves every code into place.
@@ -46,6 +51,9 @@ constexpr int kLzWarps = 8;                // compress: segments per CTA
 constexpr int kLzBlock = 32 * kLzWarps;
 constexpr int kScanBlock = 1024;
 constexpr uint32_t kMaxWindow = 65536;
+constexpr uint32_t kRingMaxWindow = 16384;  // the shared-memory window ring
+// dynamic shared memory of the largest ring (W = 16384: 1024 words, twice, per warp)
+constexpr size_t kMaxRingSmem = (size_t)kLzWarps * 2 * 1024 * 4;
 constexpr uint64_t kMaxSegment = 1ull << 24;
 
 struct LzParams {
@@ -189,6 +197,51 @@ struct WarpBits {
     }
 };
 
+// Ring words per warp (R, a power of two): the window's W/32 words, the
+// look-ahead's two and a batch of 32 loaded at once.  Stored twice.
+__host__ __device__ __forceinline__ uint32_t ring_words(uint32_t W)
+{
+    uint32_t r = 64;
+    while (r < W / 32 + 36)
+        r <<= 1;
+    return r;
+}
+__host__ __device__ __forceinline__ bool ring_ok(const LzParams &P)
+{
+    return P.W >= 64 && P.W <= kRingMaxWindow;
+}
+
+// The best key over this lane's candidates from a straight run of window
+// words: w points at the word after the one where candidate 0's source
+// begins; candidate k's source begins k words lower.
+// key = (capped match length << 16) - 32 k; the caller adds 65535 - lane.
+template <int NK>
+__device__ __forceinline__ int32_t search_run(const uint32_t *w, uint32_t nk, uint32_t sh, uint32_t X,
+                                              uint32_t cap)
+{
+    int32_t best = INT32_MIN;
+    uint32_t hiw = w[0];
+    if (NK > 0) {
+#pragma unroll
+        for (int k = 0; k < NK; ++k) {
+            const uint32_t low = w[-(k + 1)];
+            const uint32_t src = __funnelshift_l(hiw, low, sh);
+            hiw = low;
+            const int32_t key = (int32_t)(__clz((src ^ X) | cap) << 16) - 32 * k;
+            best = key > best ? key : best;
+        }
+    } else {
+        for (uint32_t k = 0; k < nk; ++k) {
+            const uint32_t low = w[-(int)(k + 1)];
+            const uint32_t src = __funnelshift_l(hiw, low, sh);
+            hiw = low;
+            const int32_t key = (int32_t)(__clz((src ^ X) | cap) << 16) - 32 * (int32_t)k;
+            best = key > best ? key : best;
+        }
+    }
+    return best;
+}
+
 __global__ void __launch_bounds__(kLzBlock)
     k_lzss_compress(const uint8_t *__restrict__ in, uint64_t n, uint64_t seg, LzParams P,
                     uint8_t *__restrict__ slots, uint32_t *__restrict__ bits_out,
@@ -196,9 +249,13 @@ __global__ void __launch_bounds__(kLzBlock)
 {
     if (chain_failed(status))
         return;
+    extern __shared__ uint32_t lz_ring[];
     const int lane = threadIdx.x & 31;
     const uint64_t count = n ? (n + seg - 1) / seg : 0;
     const uint64_t sbytes = slot_bytes(seg, P);
+    const bool use_ring = ring_ok(P);
+    const uint32_t R = ring_words(P.W);
+    uint32_t *ring = lz_ring + (threadIdx.x >> 5) * 2 * R;  // used only when use_ring
     const uint64_t nwarps = (uint64_t)gridDim.x * kLzWarps;
     for (uint64_t s = (uint64_t)blockIdx.x * kLzWarps + (threadIdx.x >> 5); s < count; s += nwarps) {
         const uint8_t *x = in + s * seg;
@@ -218,15 +275,43 @@ __global__ void __launch_bounds__(kLzBlock)
             }
             p = raw;
         }
-        const uint64_t vbase = P.W >= 32 ? P.W : P.W;  // virtual bit of the segment's bit 0
+        const uint64_t vbase = P.W;  // virtual bit of the segment's bit 0
         const uint32_t dwords = P.W >= 32 ? P.W / 32 : 0;
         const uint32_t nk = P.W >= 32 ? P.W / 32 : 1;  // candidates per lane
+        // ring: words [hw - R, hw) of the virtual string are held (twice)
+        uint64_t hw = vbase + p >= P.W + 64 ? ((vbase + p - P.W) >> 5) - 2 : 0;
         while (p < nbits) {
             const uint64_t r = nbits - p;
             const uint32_t maxlen = r < P.lmax ? (uint32_t)r : P.lmax;
-            const uint32_t X = vbits(x, m, P.W, vbase + p);  // the 32 look-ahead bits
+            uint32_t X;  // the 32 look-ahead bits
+            if (use_ring) {
+                const uint64_t need = ((vbase + p) >> 5) + 2;
+                while (hw < need) {  // warp-uniform: 32 words at a time
+                    const uint32_t v = vword(x, m, dwords, hw + lane);
+                    const uint32_t i = (uint32_t)(hw + lane) & (R - 1);
+                    ring[i] = v;
+                    ring[i + R] = v;
+                    hw += 32;
+                    __syncwarp();
+                }
+                const uint64_t q = (vbase + p) >> 5;
+                X = __funnelshift_l(ring[(uint32_t)(q + 1) & (R - 1)], ring[(uint32_t)q & (R - 1)],
+                                    (uint32_t)((vbase + p) & 31));
+            } else {
+                X = vbits(x, m, P.W, vbase + p);
+            }
             uint32_t key = 0;
-            if (maxlen >= P.lmin) {
+            if (maxlen >= P.lmin && use_ring && (P.dict == 1 || p >= P.W)) {
+                // every distance 1..W is allowed: the ring's straight run
+                const uint64_t v0 = vbase + p - (uint64_t)lane - 1;
+                const uint32_t *w = ring + ((uint32_t)((v0 >> 5) + 1) & (R - 1)) + R;
+                const uint32_t cap = maxlen >= 32 ? 0u : 0x80000000u >> maxlen;
+                const int32_t best = nk == 32 ? search_run<32>(w, nk, (uint32_t)(v0 & 31), X, cap)
+                                              : search_run<0>(w, nk, (uint32_t)(v0 & 31), X, cap);
+                key = __reduce_max_sync(0xffffffffu, (uint32_t)(best + (int32_t)(65535 - lane)));
+                if ((key >> 16) < P.lmin)
+                    key = 0;
+            } else if (maxlen >= P.lmin) {
                 // lane's sources: virtual bit v_k = vbase + p - (lane + 1) - 32 k
                 const uint64_t v0 = vbase + p - (uint64_t)lane - 1;
                 if (P.W >= 32) {
@@ -252,8 +337,8 @@ __global__ void __launch_bounds__(kLzBlock)
                     if ((P.dict == 1 || d <= p) && len >= P.lmin)
                         key = (len << 16) | (65535u - (d - 1));
                 }
+                key = __reduce_max_sync(0xffffffffu, key);
             }
-            key = __reduce_max_sync(0xffffffffu, key);
             if (key) {  // a match: 1, d - 1, l - Lmin
                 const uint32_t len = key >> 16, dm1 = 65535u - (key & 0xffffu);
                 out.put(1u << 31, 1, lane == 0);
@@ -688,11 +773,17 @@ huff_status_t huff_lzss_compress(const uint8_t *d_in, uint64_t n, uint64_t segme
     if (sms < 1)
         return HUFF_ERR_CUDA;
     if (count) {
+        const size_t smem = ring_ok(P) ? (size_t)kLzWarps * 2 * ring_words(P.W) * 4 : 0;
+        static KernelSetup setup;
+        int per_sm = 0;
+        if (kernel_setup(setup, (const void *)k_lzss_compress, kLzBlock, kMaxRingSmem, &per_sm) !=
+            cudaSuccess)
+            return HUFF_ERR_CUDA;
         uint64_t grid = (count + kLzWarps - 1) / kLzWarps;
         if (grid > (uint64_t)sms * 64)
             grid = (uint64_t)sms * 64;
-        k_lzss_compress<<<(unsigned)grid, kLzBlock, 0, s>>>(d_in, n, segment_bytes, P, slots, bits,
-                                                            d_status);
+        k_lzss_compress<<<(unsigned)grid, kLzBlock, smem, s>>>(d_in, n, segment_bytes, P, slots, bits,
+                                                               d_status);
     }
     k_lzss_layout<<<1, kScanBlock, 0, s>>>(n, segment_bytes, P, bits, start, d_out, out_cap,
                                            reinterpret_cast<unsigned long long *>(d_out_bytes),
