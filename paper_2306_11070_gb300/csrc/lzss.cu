@@ -55,6 +55,9 @@ constexpr uint32_t kRingMaxWindow = 16384;  // the shared-memory window ring
 // dynamic shared memory of the largest ring (W = 16384: 1024 words, twice, per warp)
 constexpr size_t kMaxRingSmem = (size_t)kLzWarps * 2 * 1024 * 4;
 constexpr uint64_t kMaxSegment = 1ull << 24;
+constexpr int kLzDecThreads = 32;              // decompress: one warp per CTA, a segment per thread
+constexpr uint32_t kDecRing = 128;             // output words kept per thread (a power of two)
+constexpr uint32_t kDecRingMaxWindow = 2048;   // windows whose words fit the ring with 4 to spare
 
 struct LzParams {
     uint32_t W, lmin, lmax, blk, dict;
@@ -524,37 +527,76 @@ __global__ void __launch_bounds__(kScanBlock)
         *ok = 1;
 }
 
-// MSB-first bit reader over a segment's code (bytes, zero past its end).
+// MSB-first bit reader over a segment's code: a 64-bit buffer refilled from
+// the code's 32-bit words (the code starts 16-byte aligned and is padded
+// with zeros to a 16-byte boundary; words past the padding read as zero).
+// The word after the buffer is always loaded one refill ahead, so the
+// load's latency is off the token chain.
 struct CodeReader {
-    const uint8_t *c;
+    const uint32_t *w;
+    uint32_t nw;     // words of the padded code
+    uint32_t next;   // next word to load
+    uint32_t nxt;    // word next - 1, loaded ahead
+    uint64_t buf;    // valid bits, left-aligned
+    uint32_t have;
     uint64_t nbits;  // the segment's code length
-    uint64_t pos;
-    __device__ __forceinline__ uint32_t peek32() const  // bits pos .. pos + 31
+    uint64_t pos;    // bits consumed
+    __device__ __forceinline__ uint32_t load(uint32_t i) const
     {
-        const uint64_t byte = pos >> 3;
-        const uint64_t nbytes = (nbits + 7) / 8;
-        uint64_t v = 0;
-        for (int k = 0; k < 5; ++k)
-            v = (v << 8) | (byte + k < nbytes ? (uint64_t)c[byte + k] : 0ull);
-        return (uint32_t)(v >> (8 - (pos & 7)));
+        return i < nw ? bswap32(__ldg(w + i)) : 0u;
+    }
+    __device__ __forceinline__ void init(const uint8_t *c, uint64_t code_bits)
+    {
+        w = reinterpret_cast<const uint32_t *>(c);
+        nw = (uint32_t)(al16((code_bits + 7) / 8) / 4);
+        buf = ((uint64_t)load(0) << 32) | load(1);
+        have = 64;
+        nxt = load(2);
+        next = 3;
+        nbits = code_bits;
+        pos = 0;
     }
     __device__ __forceinline__ uint32_t get(uint32_t k)  // k <= 32 bits, right-aligned
     {
         if (k == 0)
             return 0;
-        const uint32_t v = peek32() >> (32 - k);
+        const uint32_t v = (uint32_t)(buf >> (64 - k));
+        buf <<= k;
+        have -= k;
         pos += k;
+        if (have <= 32) {  // refill: >= 32 valid bits for the next get
+            buf |= (uint64_t)nxt << (32 - have);
+            have += 32;
+            nxt = load(next++);
+        }
         return v;
     }
 };
 
-// The bits the thread has produced so far, read back: completed words from
-// the output, the pending word from its register; positions before the
-// segment from the counting-numbers dictionary.
+// Store output word q (MSB-first bytes) of an m-byte segment output.
+__device__ __forceinline__ void store_out_word(uint8_t *y, uint64_t m, uint64_t q, uint32_t w)
+{
+    const uint64_t b = 4 * q;
+    if (b + 4 <= m) {
+        reinterpret_cast<uint32_t *>(y)[q] = bswap32(w);
+    } else {
+        for (int k = 0; k < 4; ++k)
+            if (b + k < m)
+                y[b + k] = (uint8_t)(w >> (24 - 8 * k));
+    }
+}
+
+// The bits a thread has produced so far, read back: completed words from
+// the output (or, with a ring, from the thread's ring of recent words in
+// shared memory), the pending word from its register; positions before the
+// segment from the counting-numbers dictionary.  With a ring, completed
+// words are written out four at a time with one 16-byte store.
+template <bool kRing>
 struct OutBits {
     uint8_t *y;      // the segment's output (16-byte aligned)
     uint64_t m;      // its bytes
     uint32_t W;
+    uint32_t *ring;  // kRing: kDecRing words, word q at q mod kDecRing
     uint32_t pend;   // bits of the word being filled, left-aligned
     uint32_t npend;  // their count
     uint64_t pos;    // bits produced
@@ -567,6 +609,8 @@ struct OutBits {
             return pend;
         if ((uint64_t)q > (pos >> 5))
             return 0u;
+        if (kRing)
+            return ring[(uint32_t)q & (kDecRing - 1)];
         return bswap32(__ldcg(reinterpret_cast<const uint32_t *>(y) + q));
     }
     // the 32 bits at output bit s (s may be negative: the dictionary)
@@ -599,7 +643,7 @@ struct OutBits {
         const uint64_t acc = ((uint64_t)pend << 32) | ((uint64_t)v << (32 - npend));
         const uint32_t total = npend + k;
         if (total >= 32) {
-            store_word(pos >> 5, (uint32_t)(acc >> 32));
+            complete(pos >> 5, (uint32_t)(acc >> 32));
             pend = (uint32_t)acc;
             npend = total - 32;
         } else {
@@ -608,27 +652,94 @@ struct OutBits {
         }
         pos += k;
     }
-    __device__ __forceinline__ void store_word(uint64_t q, uint32_t w) const
+    __device__ __forceinline__ void complete(uint64_t q, uint32_t w) const
     {
-        const uint64_t b = 4 * q;
-        if (b + 4 <= m) {
-            __stcg(reinterpret_cast<uint32_t *>(y) + q, bswap32(w));
-        } else {
-            for (int k = 0; k < 4; ++k)
-                if (b + k < m)
-                    y[b + k] = (uint8_t)(w >> (24 - 8 * k));
+        if (!kRing) {
+            if (4 * q + 4 <= m)
+                __stcg(reinterpret_cast<uint32_t *>(y) + q, bswap32(w));
+            else
+                store_out_word(y, m, q, w);
+            return;
+        }
+        ring[(uint32_t)q & (kDecRing - 1)] = w;
+        if ((q & 3) == 3) {  // a whole 16-byte group
+            const uint64_t g = q >> 2;
+            if (16 * g + 16 <= m) {
+                const uint32_t r = (uint32_t)(q - 3) & (kDecRing - 1);
+                *reinterpret_cast<uint4 *>(y + 16 * g) =
+                    make_uint4(bswap32(ring[r]), bswap32(ring[r + 1]), bswap32(ring[r + 2]),
+                               bswap32(ring[r + 3]));
+            } else {
+                for (uint64_t j = q - 3; j <= q; ++j)
+                    store_out_word(y, m, j, ring[(uint32_t)j & (kDecRing - 1)]);
+            }
         }
     }
     __device__ __forceinline__ void finish() const
     {
+        const uint64_t q = pos >> 5;  // the word being filled
+        if (kRing)  // completed words of the last, unfinished group
+            for (uint64_t j = q & ~3ull; j < q; ++j)
+                store_out_word(y, m, j, ring[(uint32_t)j & (kDecRing - 1)]);
         if (npend)
-            store_word(pos >> 5, pend);
+            store_out_word(y, m, q, pend);
     }
 };
 
-__global__ void k_lzss_decode(const uint8_t *__restrict__ c, const uint64_t *__restrict__ start,
-                              uint8_t *__restrict__ out, int32_t *status, const uint32_t *ok)
+// Decode one segment's tokens; false if the code is corrupt.
+template <bool kRing>
+__device__ __forceinline__ bool decode_segment(CodeReader &rd, OutBits<kRing> &ob, const LzParams &P,
+                                               uint64_t nbits)
 {
+    if (P.dict == 2) {
+        const uint64_t raw = nbits < P.W ? nbits : P.W;
+        while (ob.pos < raw) {
+            const uint32_t k = raw - ob.pos < 32 ? (uint32_t)(raw - ob.pos) : 32u;
+            if (rd.pos + k > rd.nbits)
+                return false;
+            ob.put(rd.get(k) << (32 - k), k);
+        }
+    }
+    while (ob.pos < nbits) {
+        if (rd.pos >= rd.nbits)
+            return false;
+        const uint64_t r = nbits - ob.pos;
+        if (rd.get(1)) {
+            if (rd.pos + P.ob + P.lb > rd.nbits)
+                return false;
+            const uint64_t d = (uint64_t)rd.get(P.ob) + 1;
+            const uint32_t len = rd.get(P.lb) + P.lmin;
+            if (len > P.lmax || len > r || (P.dict == 2 && d > ob.pos))
+                return false;
+            uint32_t v = ob.bits_at((int64_t)ob.pos - (int64_t)d);
+            if (d < len) {  // the source runs into these bits: period d
+                v &= ~(0xffffffffu >> d);
+                for (uint32_t sh = (uint32_t)d; sh < len; sh <<= 1)
+                    v |= v >> sh;
+            }
+            ob.put(v, len);
+        } else {
+            const uint32_t k = r < P.blk ? (uint32_t)r : P.blk;
+            if (rd.pos + k > rd.nbits)
+                return false;
+            ob.put(rd.get(k) << (32 - k), k);
+        }
+    }
+    return rd.pos == rd.nbits;
+}
+
+// One thread per segment.  Windows of up to kDecRingMaxWindow bits keep the
+// thread's recent output words in a shared-memory ring (the matches' source
+// words are read there, not back through L2, and output leaves in 16-byte
+// stores); wider windows read their sources back from the output.
+__global__ void __launch_bounds__(kLzDecThreads) k_lzss_decode(const uint8_t *__restrict__ c,
+                                                               const uint64_t *__restrict__ start,
+                                                               uint8_t *__restrict__ out,
+                                                               int32_t *status, const uint32_t *ok)
+{
+    // ring of thread t at t * (kDecRing + 1): the odd stride spreads the
+    // threads' equal ring positions over the banks
+    __shared__ uint32_t rings[kLzDecThreads * (kDecRing + 1)];
     if (!*ok || chain_failed(status))
         return;
     const uint64_t n = *reinterpret_cast<const uint64_t *>(c);
@@ -636,71 +747,40 @@ __global__ void k_lzss_decode(const uint8_t *__restrict__ c, const uint64_t *__r
     const uint32_t *f = reinterpret_cast<const uint32_t *>(c + 16);
     const LzParams P = make_params(f[0], f[1], f[2], f[3], f[4]);
     const uint64_t count = *reinterpret_cast<const uint64_t *>(c + 40);
+    const bool use_ring = P.W >= 32 && P.W <= kDecRingMaxWindow;
     for (uint64_t s = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; s < count;
          s += (uint64_t)gridDim.x * blockDim.x) {
         const uint64_t m = s + 1 < count ? seg : n - s * seg;
-        const uint64_t nbits = 8 * m;
         CodeReader rd;
-        rd.c = c + start[s];
-        rd.nbits = *reinterpret_cast<const uint32_t *>(c + kLzHead + 4 * s);
-        rd.pos = 0;
-        OutBits ob;
-        ob.y = out + s * seg;
-        ob.m = m;
-        ob.W = P.W;
-        ob.pend = 0;
-        ob.npend = 0;
-        ob.pos = 0;
-        bool bad = false;
-        if (P.dict == 2) {
-            const uint64_t raw = nbits < P.W ? nbits : P.W;
-            while (ob.pos < raw && !bad) {
-                const uint32_t k = raw - ob.pos < 32 ? (uint32_t)(raw - ob.pos) : 32u;
-                if (rd.pos + k > rd.nbits)
-                    bad = true;
-                else
-                    ob.put(rd.get(k) << (32 - k), k);
-            }
+        rd.init(c + start[s], *reinterpret_cast<const uint32_t *>(c + kLzHead + 4 * s));
+        bool good;
+        if (use_ring) {
+            OutBits<true> ob;
+            ob.y = out + s * seg;
+            ob.m = m;
+            ob.W = P.W;
+            ob.ring = rings + threadIdx.x * (kDecRing + 1);
+            ob.pend = 0;
+            ob.npend = 0;
+            ob.pos = 0;
+            good = decode_segment(rd, ob, P, 8 * m);
+            if (good)
+                ob.finish();
+        } else {
+            OutBits<false> ob;
+            ob.y = out + s * seg;
+            ob.m = m;
+            ob.W = P.W;
+            ob.ring = nullptr;
+            ob.pend = 0;
+            ob.npend = 0;
+            ob.pos = 0;
+            good = decode_segment(rd, ob, P, 8 * m);
+            if (good)
+                ob.finish();
         }
-        while (ob.pos < nbits && !bad) {
-            if (rd.pos >= rd.nbits) {
-                bad = true;
-                break;
-            }
-            const uint64_t r = nbits - ob.pos;
-            if (rd.get(1)) {
-                if (rd.pos + P.ob + P.lb > rd.nbits) {
-                    bad = true;
-                    break;
-                }
-                const uint64_t d = (uint64_t)rd.get(P.ob) + 1;
-                const uint32_t len = rd.get(P.lb) + P.lmin;
-                if (len > P.lmax || len > r || (P.dict == 2 && d > ob.pos)) {
-                    bad = true;
-                    break;
-                }
-                uint32_t v = ob.bits_at((int64_t)ob.pos - (int64_t)d);
-                if (d < len) {  // the source runs into these bits: period d
-                    v &= ~(0xffffffffu >> d);
-                    for (uint32_t sh = (uint32_t)d; sh < len; sh <<= 1)
-                        v |= v >> sh;
-                }
-                ob.put(v, len);
-            } else {
-                const uint32_t k = r < P.blk ? (uint32_t)r : P.blk;
-                if (rd.pos + k > rd.nbits) {
-                    bad = true;
-                    break;
-                }
-                ob.put(rd.get(k) << (32 - k), k);
-            }
-        }
-        if (!bad && rd.pos != rd.nbits)
-            bad = true;
-        if (bad)
+        if (!good)
             set_status(status, HUFF_ERR_CORRUPT_STREAM);
-        else
-            ob.finish();
     }
 }
 
@@ -824,12 +904,12 @@ huff_status_t huff_lzss_decompress(const uint8_t *d_in, uint64_t in_bytes, uint8
         return HUFF_ERR_CUDA;
     // one thread per segment; the count is only known on the device, so
     // bound the grid by the table size
-    uint64_t grid = (max_count + 127) / 128;
-    if (grid > (uint64_t)sms * 8)
-        grid = (uint64_t)sms * 8;
+    uint64_t grid = (max_count + kLzDecThreads - 1) / kLzDecThreads;
+    if (grid > (uint64_t)sms * 32)
+        grid = (uint64_t)sms * 32;
     if (grid < 1)
         grid = 1;
-    k_lzss_decode<<<(unsigned)grid, 128, 0, s>>>(d_in, start, d_out, d_status, ok);
+    k_lzss_decode<<<(unsigned)grid, kLzDecThreads, 0, s>>>(d_in, start, d_out, d_status, ok);
     return cudaGetLastError() == cudaSuccess ? HUFF_OK : HUFF_ERR_CUDA;
 }
 
