@@ -172,6 +172,34 @@ def test_stream_bit_exact_and_round_trip(gen, n):
     _check_roundtrip(GENS[gen](n, 11 + n % 97))
 
 
+def test_encode_with_uncovered_bytes():
+    """Against huff_encode's precondition, code input with bytes that have no
+    code (a text codebook, bytes from 128 up planted): the stream is
+    unspecified, but the kernels must stay inside their buffers, those bytes
+    must count zero bits in the unit offsets and in the coder alike (the
+    stream size says so), and the result must be repeatable."""
+    n = (2 << 20) + 777
+    x = synth.text(n, 31)
+    d, h, cb, st = gpu_codebook(x)
+    assert st == 0
+    ln = hg.parse_codebook(cb)[0]
+    assert ln[128:].sum() == 0 and 0 < ln.max() <= 11
+    y = x.copy()
+    rng = np.random.default_rng(5)
+    idx = rng.choice(n, 5000, replace=False)
+    y[idx] = rng.integers(128, 256, idx.size, dtype=np.uint8)
+    dy = dev(y)
+    a1, nb1, st1 = gpu_encode(dy, cb)
+    a2, nb2, st2 = gpu_encode(dy, cb)
+    assert st1 == 0 and st2 == 0 and nb1 == nb2
+    bits = int(ln.astype(np.int64)[y].sum())
+    chunks = (n + 16383) // 16384
+    assert nb1 == 272 + 8 * chunks + 4 * ((bits + 31) // 32)
+    assert torch.equal(a1[:nb1], a2[:nb2])
+    # and the covered input still matches the oracle byte for byte
+    _check_roundtrip(x)
+
+
 @pytest.mark.parametrize("shift", [16, 32])
 def test_decode_into_offset_output(shift):
     """The decoder stores whole 32-byte groups only where a chunk's output is
