@@ -41,7 +41,8 @@ using namespace enc;
 // 16 warps are what fit without spills.
 constexpr int kEncBlock = 512;
 constexpr int kEncWarps = kEncBlock / 32;
-constexpr int kEncSmemBytes = (kTblWords + kEncWarps * kWarpObuf) * 4;
+// the (code, 2^len) table is the larger of the two table layouts
+constexpr int kEncSmemBytes = (kTbl2Words + kEncWarps * kWarpObuf) * 4;
 
 struct EncodeArgs {
     const uint8_t *in;
@@ -58,14 +59,17 @@ struct EncodeArgs {
 __global__ void __launch_bounds__(kEncBlock, 1) k_encode(EncodeArgs a)
 {
     extern __shared__ uint4 smem_raw[];
-    uint32_t *tbl = reinterpret_cast<uint32_t *>(smem_raw);  // [256][32] or 2 x [256][16]
-    uint32_t *wob = tbl + kTblWords + (threadIdx.x >> 5) * kWarpObuf;  // this warp's buffer
+    // [256][32] (code, 2^len) pairs, or 2 x [256][16] for codes over 22 bits
+    uint32_t *tbl = reinterpret_cast<uint32_t *>(smem_raw);
+    uint32_t *wob = tbl + kTbl2Words + (threadIdx.x >> 5) * kWarpObuf;  // this warp's buffer
 
     if (chain_failed(a.status))
         return;
     const Job J = make_job(a.in, a.n, a.cs, a.unit_off, a.out, a.out_cap);
     const uint32_t max_len = a.cb->max_len;
     const bool fast = max_len <= (uint32_t)kFastMaxLen;
+    if (fast && mad_group(max_len) >= 3)
+        return;  // k_encode_mad codes this stream
     const int group = emit_group(max_len);
     if (blockIdx.x == 0)
         write_header(J, a.cb, a.out_bytes, a.status);
@@ -76,6 +80,34 @@ __global__ void __launch_bounds__(kEncBlock, 1) k_encode(EncodeArgs a)
     bool overflow = false;
     for (uint64_t u = (uint64_t)blockIdx.x * kEncWarps + (threadIdx.x >> 5); u < J.units; u += nwarps)
         overflow |= encode_unit(J, u, tbl, fast, group, wob);
+    if (overflow)
+        set_status(a.status, HUFF_ERR_CAPACITY);
+}
+
+// The same for codes of at most 10 bits, gathered by multiply-add (see
+// encode_impl.cuh); the two kernels are launched back to back and the one
+// that does not apply returns at once.
+__global__ void __launch_bounds__(kEncBlock, 1) k_encode_mad(EncodeArgs a)
+{
+    extern __shared__ uint4 smem_raw[];
+    uint32_t *tbl2 = reinterpret_cast<uint32_t *>(smem_raw);  // [256][32] (code, 2^len)
+    uint32_t *wob = tbl2 + kTbl2Words + (threadIdx.x >> 5) * kWarpObuf;
+
+    if (chain_failed(a.status))
+        return;
+    const uint32_t max_len = a.cb->max_len;
+    const int mgroup = mad_group(max_len);
+    if (!(max_len <= (uint32_t)kFastMaxLen && mgroup >= 3))
+        return;
+    const Job J = make_job(a.in, a.n, a.cs, a.unit_off, a.out, a.out_cap);
+    if (blockIdx.x == 0)
+        write_header(J, a.cb, a.out_bytes, a.status);
+    build_table2(a.cb, tbl2);
+    __syncthreads();
+    const uint64_t nwarps = (uint64_t)gridDim.x * kEncWarps;
+    bool overflow = false;
+    for (uint64_t u = (uint64_t)blockIdx.x * kEncWarps + (threadIdx.x >> 5); u < J.units; u += nwarps)
+        overflow |= encode_unit_mad_g(J, u, tbl2, mgroup, wob);
     if (overflow)
         set_status(a.status, HUFF_ERR_CAPACITY);
 }
@@ -95,9 +127,11 @@ cudaError_t launch_encode(const uint8_t *d_in, uint64_t n, const huff_codebook_t
                           void *d_ws, const uint16_t *d_unit_hist, int32_t *d_status,
                           cudaStream_t s)
 {
-    static KernelSetup setup;
-    int per_sm = 0;
+    static KernelSetup setup, setup_mad;
+    int per_sm = 0, per_sm_mad = 0;
     cudaError_t err = kernel_setup(setup, (const void *)k_encode, kEncBlock, kEncSmemBytes, &per_sm);
+    if (err == cudaSuccess)
+        err = kernel_setup(setup_mad, (const void *)k_encode_mad, kEncBlock, kEncSmemBytes, &per_sm_mad);
     if (err != cudaSuccess)
         return err;
     const int sms = device_sm_count();
@@ -130,6 +164,7 @@ cudaError_t launch_encode(const uint8_t *d_in, uint64_t n, const huff_codebook_t
         grid = want;
     if (grid < 1)
         grid = 1;
+    k_encode_mad<<<(unsigned)grid, kEncBlock, kEncSmemBytes, s>>>(a);
     k_encode<<<(unsigned)grid, kEncBlock, kEncSmemBytes, s>>>(a);
     return cudaGetLastError();
 }

@@ -460,6 +460,210 @@ __device__ __forceinline__ bool encode_unit_fast(const Job &J, uint64_t u, const
     return overflow;
 }
 
+// ---- codes gathered by multiply-add (single-stream encoder) ----------------
+// The fast path above spends two funnel shifts per code on the ALU pipe,
+// which bounds it.  Here a group of codes is gathered on the FMA pipe: the
+// table holds (code, 2^len) per byte and lane, and a = a * 2^len + code
+// appends a code to the group's bits; a starts at 1, so its leading one
+// marks the group's length (a group has at most 31 bits).  Only the group
+// then pays the funnel shifts into the 64-bit window and the emit check:
+// per code one byte extract, one table load (8 bytes) and one IMAD, per
+// group a leading-one search and three funnel shifts.  The groups of a lane
+// are cut at its 16th symbol too, where a chunk may start.  Same stream,
+// bit for bit.
+constexpr int kTbl2Words = 256 * 32 * 2;  // [byte][lane] (code, 2^len), 64 KiB
+
+__device__ __forceinline__ void build_table2(const huff_codebook_t *cb, uint32_t *tbl2)
+{
+    for (int i = threadIdx.x; i < 256 * 32; i += blockDim.x) {
+        const int b = i >> 5;
+        const uint32_t L = cb->len[b];
+        tbl2[2 * i] = L ? cb->code[b] : 0u;
+        tbl2[2 * i + 1] = 1u << L;  // 2^0 = 1 for a byte without a code: no bits
+    }
+}
+
+// Codes per group: floor(31 / longest), as a template (31: the marker bit).
+__device__ __forceinline__ int mad_group(uint32_t max_len)
+{
+    const uint32_t gq = max_len ? 31u / max_len : 16u;
+    return gq >= 16 ? 16 : gq >= 8 ? 8 : gq >= 4 ? 4 : gq >= 3 ? 3 : gq >= 2 ? 2 : 1;
+}
+
+// As seam_word, from the (code, 2^len) table.
+__device__ __forceinline__ uint32_t seam_word2(const uint8_t *in, uint64_t base, uint32_t r,
+                                               const uint32_t *tbl2, int lane)
+{
+    const uint32_t b = in[base - 1 - lane];
+    const uint2 x = reinterpret_cast<const uint2 *>(tbl2)[(b << 5) | lane];
+    const uint32_t L = 31u - __clz(x.y), code = x.x;
+    uint32_t sfx = L;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const uint32_t v = __shfl_up_sync(0xffffffffu, sfx, d);
+        if (lane >= d)
+            sfx += v;
+    }
+    const uint32_t before = sfx - L;
+    const uint32_t part = (L && before < r) ? code << (32 - r + before) : 0u;
+    return __reduce_or_sync(0xffffffffu, part);
+}
+
+__device__ __forceinline__ UnitState unit_start2(const Job &J, uint64_t u, const uint32_t *tbl2,
+                                                 int lane)
+{
+    UnitState st;
+    st.base = u * kUnitSymbols;
+    st.gbit = J.unit_off[u];
+    st.carry = (st.base > 0 && (st.gbit & 31)) ? seam_word2(J.in, st.base, (uint32_t)(st.gbit & 31), tbl2, lane)
+                                               : 0u;
+    const uint32_t umod = (uint32_t)(st.base % J.cs);
+    st.lead = umod ? J.cs - umod : 0u;
+    st.next_chunk = (st.base + st.lead) / J.cs;
+    return st;
+}
+
+// One 1024-symbol step (codes of at most 22 bits; G codes per group).
+template <int G, bool kInner>
+__device__ __forceinline__ bool mad_step(const Job &J, UnitState &st, int step, int lane,
+                                         uint32_t tcol_s, uint32_t wob_s, uint32_t *wob,
+                                         const uint32_t (&w)[8])
+{
+    constexpr int NH = (16 + G - 1) / G;  // groups per 16 symbols
+    constexpr int NG = 2 * NH;
+    const uint64_t sb = st.base + (uint64_t)step * kFastStep;
+    int m = kFastSyms;
+    uint32_t tw[8];
+    if (kInner) {
+#pragma unroll
+        for (int j = 0; j < 8; ++j)
+            tw[j] = w[j];
+    } else {
+        m = step_input_tail<kFastSyms>(J, sb, lane, tw);
+    }
+    uint32_t acc[NG], lg[NG];
+    uint32_t bits = 0, mid16 = 0;
+#pragma unroll
+    for (int g = 0; g < NG; ++g) {
+        const int k0 = (g / NH) * 16 + (g % NH) * G;
+        uint32_t a = 1u;
+#pragma unroll
+        for (int j = 0; j < G; ++j) {
+            const int k = k0 + j;
+            if ((g % NH) * G + j < 16 && (kInner || k < m)) {
+                uint2 x;
+                asm("ld.shared.v2.u32 {%0, %1}, [%2];"
+                    : "=r"(x.x), "=r"(x.y)
+                    : "r"(imad(byte_of(tw, k), kc[k128] * 2u, tcol_s)));
+                a = a * x.y + x.x;
+            }
+        }
+        acc[g] = a;
+        lg[g] = 31u - __clz(a);
+        bits += lg[g];
+        if (g == NH - 1)
+            mid16 = bits;
+    }
+    uint32_t pos, step_bits;
+    scan_bits(bits, lane, pos, step_bits);
+    const uint32_t p0 = (uint32_t)(st.gbit & 31) + pos;
+    step_chunks<kFastSyms, kFastStep>(J, st, sb, lane, pos, mid16);
+    if (!kInner) {
+        sts_if(lane == 0, wob_s, st.carry);  // word 0 starts with the carried bits
+        __syncwarp();
+    }
+    // groups into the 64-bit window hi:lo, the last completed word out after
+    // each group (see pack_codes for why plain stores are enough when every
+    // lane has 32 codes)
+    // A group that crosses no word boundary would store the same word again:
+    // only groups that cross one store (about one group in 2.4 on text),
+    // which keeps the warp-buffer stores off the L1 data pipe.
+    uint32_t hi = 0u, lo = 0u, E = p0;
+#pragma unroll
+    for (int g = 0; g < NG; ++g) {
+        const uint32_t L = lg[g];
+        const uint32_t top = __funnelshift_lc(0u, acc[g], 32u - L);  // the group's bits, high-aligned
+        hi = __funnelshift_l(lo, hi, L);
+        lo = __funnelshift_l(top, lo, L);
+        const uint32_t E0 = E;
+        E = imad(L, kc[kOne], E);
+        if ((E ^ E0) >> 5) {  // a word was completed
+            const uint32_t ad = imad(E >> 5, kc[kFour], wob_s - 4), v = __funnelshift_r(lo, hi, E);
+            if (kInner)
+                sts(ad, v);
+            else
+                red_or(ad, v);
+        }
+    }
+    const uint32_t part = __funnelshift_lc(0u, lo, 32u - (E & 31u));
+    if (kInner) {
+        __syncwarp();
+        const uint32_t pa = imad(E >> 5, kc[kFour], wob_s);
+        if (lane == 31)
+            sts(pa, part);
+        else
+            red_or(pa, part);
+        if (lane == 0)
+            red_or(wob_s, st.carry);
+    } else {
+        red_or(imad(E >> 5, kc[kFour], wob_s), part);
+    }
+    __syncwarp();
+    const bool last = sb + kFastStep >= J.n;
+    const bool overflow = step_output<!kInner>(J, st, last, step_bits, wob, lane);
+    __syncwarp();
+    step_advance<kFastStep>(J, st, step_bits);
+    return overflow;
+}
+
+template <int G>
+__device__ __forceinline__ bool encode_unit_mad(const Job &J, uint64_t u, const uint32_t *tbl2,
+                                                uint32_t *wob)
+{
+    const int lane = threadIdx.x & 31;
+    const uint32_t tcol_s = smem_u32(tbl2 + 2 * lane), wob_s = smem_u32(wob + 1);
+    UnitState st = unit_start2(J, u, tbl2, lane);
+    const bool inner = st.base + kUnitSymbols < J.n && (J.unit_off[u + 1] >> 5) < J.cap_words;
+    if (!inner)
+        clear_buffer(wob, lane);
+    bool overflow = false;
+    if (inner) {  // warp-uniform
+        const uint8_t *p = J.in + st.base + lane * kFastSyms;
+        uint32_t w[8];
+        load32(p, w);
+        for (int step = 0; step < kFastSteps; ++step) {
+            uint32_t nx[8];
+            if (step + 1 < kFastSteps)
+                load32(p + (step + 1) * kFastStep, nx);  // one step ahead
+            mad_step<G, true>(J, st, step, lane, tcol_s, wob_s, wob + 1, w);
+#pragma unroll
+            for (int j = 0; j < 8; ++j)
+                w[j] = nx[j];
+        }
+    } else {
+        const uint32_t none[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+        for (int step = 0; step < kFastSteps; ++step) {
+            if (st.base + (uint64_t)step * kFastStep >= J.n)
+                break;  // warp-uniform
+            overflow |= mad_step<G, false>(J, st, step, lane, tcol_s, wob_s, wob + 1, none);
+        }
+    }
+    return overflow;
+}
+
+// group: mad_group of the longest code, at least 3 (longer codes keep the
+// funnel-shift path, where a group of one or two codes saves nothing)
+__device__ __forceinline__ bool encode_unit_mad_g(const Job &J, uint64_t u, const uint32_t *tbl2,
+                                                  int group, uint32_t *wob)
+{
+    switch (group) {
+    case 16: return encode_unit_mad<16>(J, u, tbl2, wob);
+    case 8: return encode_unit_mad<8>(J, u, tbl2, wob);
+    case 4: return encode_unit_mad<4>(J, u, tbl2, wob);
+    default: return encode_unit_mad<3>(J, u, tbl2, wob);
+    }
+}
+
 // The same for codes of up to 32 bits: split code / length tables, 16
 // symbols per lane and a 64-bit accumulator (rare: only very skewed inputs
 // have codes this long).
