@@ -691,7 +691,10 @@ def run_ours(args):
     stream = torch.cuda.current_stream()
     # five events per timed step bracket the four calls (kernels on this stream)
     evs = [[torch.cuda.Event(enable_timing=True) for _ in range(5)] for _ in range(args.steps)]
-    launches_per_step = 6  # histogram, codebook, unit bits, unit scan, encode, decode
+    # k_histogram, k_build_codebook, k_unit_bits_hist, k_scan_tile_sums,
+    # k_scan_apply, k_encode_mad and k_encode (one of the two returns at once),
+    # k_decode
+    launches_per_step = 8
 
     def step(ev=None):
         if ev:
