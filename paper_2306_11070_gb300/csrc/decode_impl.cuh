@@ -219,9 +219,10 @@ __device__ __forceinline__ void cp_async_wait()
 // top-up also asks L2 for the line 64 words past the requests.
 struct Bits {
     uint32_t col;          // shared address of this lane's cell in row 0
-    const uint4 *groups;   // the payload's 16-byte groups (may start up to 3 words early)
-    uint64_t gend;         // virtual end: payload words + words before the payload in group 0
-    uint64_t g0;           // group holding w0
+    const uint4 *gp;       // the 16-byte group holding w0 (groups may start up to 3 words early)
+    uint32_t g0lo;         // that group's index, low bits (its ring cell)
+    uint32_t nfull;        // groups from gp that lie wholly inside the payload
+    uint32_t tailb;        // payload bytes in group nfull (0..12)
     uint32_t ph;           // w0's position in its group
     uint32_t widx;    // next word to move into the bit buffer
     uint32_t fgr;     // next group to request, counted from g0
@@ -234,7 +235,7 @@ struct Bits {
     __device__ __forceinline__ uint32_t slot(uint32_t w) const
     {
         const uint32_t v = w + ph;
-        return col + (((uint32_t)g0 + (v >> 2)) & 7u) * 512 + (v & 3u) * 4;
+        return col + ((g0lo + (v >> 2)) & 7u) * 512 + (v & 3u) * 4;
     }
     // the address after ring address a: the next word of the cell, or the
     // first word of the next cell (a carry through the lane bits, set to all
@@ -246,13 +247,9 @@ struct Bits {
     // request group fgr (four words), zero-filled past the payload
     __device__ __forceinline__ void fetch()
     {
-        const uint64_t g = g0 + fgr;
-        const uint32_t d = col + ((uint32_t)g & 7u) * 512;
-        const uint64_t vw = 4 * g;  // first virtual word of the group
-        uint32_t bytes = 16;
-        if (vw + 4 > gend)
-            bytes = vw >= gend ? 0u : (uint32_t)(gend - vw) * 4;
-        cp_async16(d, bytes ? (const void *)(groups + g) : (const void *)groups, bytes);
+        const uint32_t d = col + ((g0lo + fgr) & 7u) * 512;
+        const uint32_t bytes = fgr < nfull ? 16u : (fgr == nfull ? tailb : 0u);
+        cp_async16(d, bytes ? (const void *)(gp + fgr) : (const void *)gp, bytes);
         ++fgr;
         cp_async_commit();
     }
@@ -260,9 +257,8 @@ struct Bits {
     {
         while (4 * fgr - (widx + ph) <= (uint32_t)kInRing - 4)
             fetch();
-        const uint64_t pf = 4 * (g0 + fgr) + 64;
-        if (pf < gend)
-            asm volatile("prefetch.global.L2 [%0];" ::"l"(groups + (pf >> 2)));
+        if (fgr + 16 < nfull)  // ask L2 for the line 64 words past the requests
+            asm volatile("prefetch.global.L2 [%0];" ::"l"(gp + fgr + 16));
     }
     // start at bit `pbit` counted from the first bit of payload word word0;
     // column: this lane's cell in row 0 of a 4 KiB-aligned block
@@ -271,10 +267,16 @@ struct Bits {
     {
         col = column;
         const uint32_t lead = (uint32_t)(reinterpret_cast<uintptr_t>(pay) >> 2) & 3u;
-        groups = reinterpret_cast<const uint4 *>(pay - lead);
-        gend = nw + lead;
+        const uint4 *groups = reinterpret_cast<const uint4 *>(pay - lead);
+        const uint64_t gend = nw + lead;  // virtual end: payload words + words before it in group 0
         const uint64_t v0 = word0 + lead;
-        g0 = v0 >> 2;
+        const uint64_t g0 = v0 >> 2;  // group holding w0
+        gp = groups + g0;
+        g0lo = (uint32_t)g0;
+        const uint64_t full = gend >> 2;  // groups wholly inside the payload
+        const uint64_t nf = full > g0 ? full - g0 : 0;
+        nfull = nf < 0xffffffffull ? (uint32_t)nf : 0xffffffffu;
+        tailb = 4 * (full >= g0 ? (uint32_t)(gend & 3) : 0u);  // the partial group full, if any
         ph = (uint32_t)(v0 & 3);
         widx = pbit >> 5;
         fgr = (widx + ph) >> 2;
