@@ -66,9 +66,14 @@ def test_container_matches_oracle_paper_params(gen, n):
     _roundtrip_vs_oracle(_gen(gen, n, n + 3), 4096, hg.LZSS_PAPER)
 
 
+# windows below 64 bits and above 16384 take the compressor's L1 path, the
+# others its shared-memory ring; above 2048 the decompressor reads its
+# sources back through L2
 @pytest.mark.parametrize("params", [(1024, 12, 24, 8, 1), (8, 2, 5, 4, 1), (4, 3, 4, 2, 2),
                                     (16, 4, 12, 8, 1), (64, 6, 9, 5, 1), (64, 12, 24, 8, 2),
-                                    (256, 1, 32, 32, 1), (4096, 16, 32, 8, 2), (32, 3, 3, 1, 2)])
+                                    (256, 1, 32, 32, 1), (4096, 16, 32, 8, 2), (32, 3, 3, 1, 2),
+                                    (2048, 8, 20, 8, 1), (16384, 12, 24, 8, 1),
+                                    (65536, 20, 32, 16, 1)])
 @pytest.mark.parametrize("gen", ["bitstream", "text", "periodic"])
 def test_container_matches_oracle_other_params(params, gen):
     _roundtrip_vs_oracle(_gen(gen, 3000, sum(params)), 1024, params)

@@ -172,6 +172,17 @@ def test_stream_bit_exact_and_round_trip(gen, n):
     _check_roundtrip(GENS[gen](n, 11 + n % 97))
 
 
+@pytest.mark.parametrize("k", [2, 3, 5, 20, 100, 180])
+def test_small_alphabets_every_code_group(k):
+    """k equally likely byte values (longest codes of 1, 2, 3, 5, 7 and 8
+    bits): the encoder's multiply-add groups of 16, 8, 4 and 3 codes, whole
+    stream against the oracle over several inner units and a ragged tail."""
+    rng = np.random.default_rng(k)
+    vals = rng.choice(256, k, replace=False).astype(np.uint8)
+    x = vals[rng.integers(0, k, (1 << 20) + 12345)]
+    _check_roundtrip(x)
+
+
 def test_encode_with_uncovered_bytes():
     """Against huff_encode's precondition, code input with bytes that have no
     code (a text codebook, bytes from 128 up planted): the stream is
