@@ -4,8 +4,9 @@
 //
 // Every CTA validates the header and builds the canonical decode tables in
 // shared memory from the 256 stored lengths:
-//  - a 2^12-entry lookup table in four interleaved copies (lane l reads copy
-//    l mod 4); an entry holds the bytes of up to two codes that fit in the
+//  - a 2^12-entry lookup table (the single-stream kernel keeps one copy, the
+//    table code supports C interleaved copies, lane l reading copy l mod C);
+//    an entry holds the bytes of up to two codes that fit in the
 //    12-bit window, their total length and their number, so text decodes
 //    ~2.0 symbols per lookup; a byte table beside it holds the length of the
 //    first code alone;
@@ -30,7 +31,8 @@
 //  4. each sub-segment decodes its symbols again on the true path, checking
 //     every code and the chunk's bit limit.
 // Counting (1) and decoding (4) run in windows of lookups.  A window far
-// from every lane's segment end (32 lookups) runs with no checks and no
+// from every lane's segment end (64 lookups here, with the output flushed
+// after each 32; 32 in the batched kernel) runs with no checks and no
 // branch (warp-uniform); the others (12 lookups) check each code.  Per
 // lookup the unchecked window does one 4-byte shared-memory load of the table
 // entry, two funnel shifts by the entry itself to drop the bits, and two
@@ -40,7 +42,8 @@
 // A code longer than the table has an all-zero entry, which consumes and
 // emits nothing: the lane waits on it until the next window resolves it.
 // Between windows each lane tops up its input ring in shared memory with
-// 16-byte cp.async copies that bypass L1 (eight 16-byte cells per lane) and
+// 16-byte cp.async copies that bypass L1 (sixteen 16-byte cells per lane
+// here, eight in the batched kernel) and
 // stores every completed group of its 128-byte output ring (laid out
 // [word][lane], so a warp's accesses never share a bank) with one global
 // store: 32-byte groups and 256-bit stores where the chunk's output is
@@ -56,14 +59,18 @@ namespace {
 
 using namespace dec;
 
-// One 16-warp CTA per SM with four interleaved copies of the lookup table.
+// One 16-warp CTA per SM, one copy of the lookup table (four interleaved
+// copies measured the same: the random 12-bit indices conflict as often),
+// input rings of 16 cells per lane for 64-lookup windows.
 constexpr int kDecBlock = 512;
 constexpr int kDecWarps = kDecBlock / 32;
-constexpr int kDecCopies = 4;
-// dynamic shared memory: the tables, then (from the next 4 KiB boundary) one
-// 4 KiB output block and one 4 KiB input block per warp
+constexpr int kDecCopies = 1;
+constexpr int kDecCells = 16;
+constexpr size_t kDecInBlock = (size_t)kDecCells * 512;  // 8 KiB per warp
+// dynamic shared memory: the tables, then (from the next 8 KiB boundary) one
+// 8 KiB input block per warp, then one 4 KiB output block per warp
 constexpr size_t kDecTables = (sizeof(DecodeShared<kDecCopies>) + 15) & ~size_t(15);
-constexpr size_t kDecSmem = kDecTables + 4096 + (size_t)kDecWarps * 2 * 4096;
+constexpr size_t kDecSmem = kDecTables + kDecInBlock + (size_t)kDecWarps * (kDecInBlock + 4096);
 
 struct DecodeArgs {
     const uint8_t *stream;
@@ -80,9 +87,9 @@ __global__ void __launch_bounds__(kDecBlock, 1) k_decode(DecodeArgs a)
     extern __shared__ __align__(16) unsigned char dsm[];
     DecodeShared<kDecCopies> &sh = *reinterpret_cast<DecodeShared<kDecCopies> *>(dsm);
     const uint32_t tbl_end = smem_u32(dsm) + (uint32_t)kDecTables;
-    const uint32_t rings = (tbl_end + 4095u) & ~4095u;  // warps' output blocks, then input blocks
-    uint16_t *scratch = reinterpret_cast<uint16_t *>(dsm + (rings - smem_u32(dsm)) +
-                                                     kDecWarps * 4096);  // free while tables build
+    // warps' input blocks, then output blocks
+    const uint32_t rings = (tbl_end + (uint32_t)kDecInBlock - 1u) & ~((uint32_t)kDecInBlock - 1u);
+    uint16_t *scratch = reinterpret_cast<uint16_t *>(dsm + (rings - smem_u32(dsm)));  // free while tables build
 
     if (chain_failed(a.status))
         return;
@@ -106,13 +113,13 @@ __global__ void __launch_bounds__(kDecBlock, 1) k_decode(DecodeArgs a)
     const uint32_t S = pick_split(si.chunks, a.min_chains);
     const uint64_t tasks = (si.chunks + (32 / S) - 1) / (32 / S);
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-    const uint32_t out_s = rings + wib * 4096 + lane * 4;
-    const uint32_t in_s = rings + (kDecWarps + wib) * 4096 + lane * 16;
+    const uint32_t in_s = rings + wib * (uint32_t)kDecInBlock + lane * 16;
+    const uint32_t out_s = rings + kDecWarps * (uint32_t)kDecInBlock + wib * 4096 + lane * 4;
     // tasks are dealt to the CTAs in turn (task t to CTA t mod grid), so
     // when there are fewer tasks than warps every SM still gets its share
     const uint64_t nwarps = (uint64_t)gridDim.x * kDecWarps;
     for (uint64_t task = (uint64_t)wib * gridDim.x + blockIdx.x; task < tasks; task += nwarps) {
-        if (decode_task(si, S, task, in_s, out_s)) {
+        if (decode_task<kDecCells>(si, S, task, in_s, out_s)) {
             if (lane == 0)
                 set_status(a.status, HUFF_ERR_CORRUPT_STREAM);
             return;

@@ -9,9 +9,15 @@ namespace dec {
 
 constexpr int kLutBits = 12;
 constexpr int kLutSize = 1 << kLutBits;
-constexpr int kInRing = 32;   // input ring: words per lane
 constexpr int kOutRing = 32;  // output ring: 128 bytes per lane (one 4 KiB-aligned block per warp)
-constexpr int kWindow = 32;   // table lookups per unchecked window (an even number)
+// Input ring and window, by the ring's 16-byte cells per lane (C = 8: 4 KiB
+// per warp, 32-lookup windows; C = 16: 8 KiB per warp, 64-lookup windows
+// whose output is flushed after each 32 lookups)
+template <int C> struct RingCfg {
+    static constexpr int kInRing = 4 * C;   // words per lane
+    static constexpr int kWindow = 4 * C;   // table lookups per unchecked window
+    static constexpr int kInFlight = C / 2 - 1;  // groups left in flight at a window's end
+};
 constexpr int kCheckedWindow = 12;  // lookups per checked window
 constexpr int kMaxPerLookup = 2;
 constexpr uint32_t kFull = 0xffffffffu;
@@ -208,16 +214,18 @@ __device__ __forceinline__ void cp_async_wait()
 // so the junk never reaches the low six bits, and the wrap-mode shifts read
 // only the low five.
 //
-// Ring invariant: after every top-up more than kInRing - 4 words are
-// requested beyond the next one to read, in groups of 4, and the three most
-// recent groups may still be in flight; so the next 1 + 16 words have
-// landed, and one window moves at most 15 words into the bit buffer (a
-// checked window reads at most 12 codes of <= 32 bits, an unchecked one at
-// most one such code and 32 of <= 12 bits plus one spare refill, and the
-// buffer holds < 64 bits).
-// Requests never reach the cell of a word that has not been read.  Each
-// top-up also asks L2 for the line 64 words past the requests.
-struct Bits {
+// Ring invariant (C cells of 4 words per lane): after every top-up more than
+// 4C - 4 words are requested beyond the next one to read, in groups of 4,
+// and the C/2 - 1 most recent groups may still be in flight; so the next
+// 1 + 2C words have landed (C = 8: 17, C = 16: 33), and one window moves at
+// most C + 7 + 1 words into the bit buffer (a checked window reads at most
+// 12 codes of <= 32 bits, an unchecked one at most one such code and 4C of
+// <= 12 bits plus one spare refill: 15 and 26 words; the buffer holds < 64
+// bits).  Requests never reach the cell of a word that has not been read.
+// Each top-up also asks L2 for the line 64 words past the requests.
+template <int C>
+struct BitsT {
+    static constexpr int kInRing = 4 * C;
     uint32_t col;          // shared address of this lane's cell in row 0
     const uint4 *gp;       // the 16-byte group holding w0 (groups may start up to 3 words early)
     uint32_t g0lo;         // that group's index, low bits (its ring cell)
@@ -235,19 +243,19 @@ struct Bits {
     __device__ __forceinline__ uint32_t slot(uint32_t w) const
     {
         const uint32_t v = w + ph;
-        return col + ((g0lo + (v >> 2)) & 7u) * 512 + (v & 3u) * 4;
+        return col + ((g0lo + (v >> 2)) & (C - 1u)) * 512 + (v & 3u) * 4;
     }
     // the address after ring address a: the next word of the cell, or the
     // first word of the next cell (a carry through the lane bits, set to all
-    // ones, into the cell number), within the lane's eight cells
+    // ones, into the cell number), within the lane's C cells
     __device__ __forceinline__ uint32_t next_slot(uint32_t a, uint32_t k) const
     {
-        return (imad(k, kc[kFour], a | 0x1f0u) & 0xe0cu) | col;
+        return (imad(k, kc[kFour], a | 0x1f0u) & ((C - 1u) * 512u + 12u)) | col;
     }
     // request group fgr (four words), zero-filled past the payload
     __device__ __forceinline__ void fetch()
     {
-        const uint32_t d = col + ((g0lo + fgr) & 7u) * 512;
+        const uint32_t d = col + ((g0lo + fgr) & (C - 1u)) * 512;
         const uint32_t bytes = fgr < nfull ? 16u : (fgr == nfull ? tailb : 0u);
         cp_async16(d, bytes ? (const void *)(gp + fgr) : (const void *)gp, bytes);
         ++fgr;
@@ -261,7 +269,7 @@ struct Bits {
             asm volatile("prefetch.global.L2 [%0];" ::"l"(gp + fgr + 16));
     }
     // start at bit `pbit` counted from the first bit of payload word word0;
-    // column: this lane's cell in row 0 of a 4 KiB-aligned block
+    // column: this lane's cell in row 0 of a (C * 512)-byte aligned block
     __device__ __forceinline__ void init(uint32_t column, const uint32_t *pay, uint64_t nw,
                                          uint64_t word0, uint32_t pbit)
     {
@@ -722,10 +730,12 @@ __device__ __forceinline__ void flush_groups32(uint8_t *ob, const OutQ &ow, uint
 // the warp's rings (the output block 4 KiB aligned).  Returns true
 // (warp-uniform) if the stream is corrupt.  kWhole: S == 1, one lane per
 // chunk, compiled without the count / settle / scan phases.
-template <bool kWhole>
+template <bool kWhole, int C>
 __device__ __forceinline__ bool decode_task_s(const StreamInfo &si, uint32_t S_arg, uint64_t task,
                                               uint32_t in_s, uint32_t out_s)
 {
+    constexpr int kWindow = RingCfg<C>::kWindow;
+    constexpr int kInFlight = RingCfg<C>::kInFlight;
     const uint32_t S = kWhole ? 1u : S_arg;
     const Tables &T = si.T;
     const int lane = threadIdx.x & 31;
@@ -768,7 +778,7 @@ __device__ __forceinline__ bool decode_task_s(const StreamInfo &si, uint32_t S_a
     SyncMap bmap;
     bmap.clear();
     if (S > 1) {  // uniform: every lane of the warp takes this branch
-        Bits rs = {};
+        BitsT<C> rs = {};
         bool act = work && k + 1 < S && g < stop;
         if (act)
             rs.init(in_s, pw, pay_words, cbase >> 5, b0 + g);
@@ -848,7 +858,7 @@ __device__ __forceinline__ bool decode_task_s(const StreamInfo &si, uint32_t S_a
             }
             if (act)
                 rs.top_up();
-            cp_async_wait<3>();
+            cp_async_wait<kInFlight>();
         }
         cp_async_wait<0>();  // the ring is reused below
         if (work && k + 1 < S && g < stop) {
@@ -892,7 +902,7 @@ __device__ __forceinline__ bool decode_task_s(const StreamInfo &si, uint32_t S_a
 
     // 4. decode on the true path and write the bytes
     {
-        Bits rs = {};
+        BitsT<C> rs = {};
         OutQ ow;
         bool act = todo > 0;
         uint8_t *const ob = si.out + c * cs;  // chunk output, 16-byte aligned
@@ -910,7 +920,7 @@ __device__ __forceinline__ bool decode_task_s(const StreamInfo &si, uint32_t S_a
             // either.
             const bool easy = act && qend - q >= 1 + kMaxPerLookup * kWindow &&
                               lim - pos >= 32 + kLutBits * kWindow;
-            const uint32_t q0 = q, row0 = ow.row(), p0 = ow.pending();
+            uint32_t q0 = q, row0 = ow.row(), p0 = ow.pending();
             if (__all_sync(kFull, easy)) {
                 rs.refill();
                 if (lut_ld(lut_l, stride, rs.bh) == 0) {  // a long code (rare)
@@ -935,16 +945,35 @@ __device__ __forceinline__ bool decode_task_s(const StreamInfo &si, uint32_t S_a
                 // load for a lookup beyond the window are harmless (one more
                 // word at most, within the ring bound).
                 uint32_t ent = lut_ld(lut_l, stride, rs.bh);
+#pragma unroll 1
+                for (int half = 0; half < kWindow / 32; ++half) {
 #pragma unroll 4
-                for (int p = 0; p < kWindow / 2; ++p) {
-                    rs.consume_t(ent);
-                    const uint32_t ent1 = lut_ld(lut_l, stride, rs.bh);
-                    ow.merge(ent);
-                    rs.consume_t(ent1);
-                    rs.refill();
-                    ent = lut_ld(lut_l, stride, rs.bh);
-                    ow.merge(ent1);
-                    ow.store();
+                    for (int p = 0; p < 16; ++p) {
+                        rs.consume_t(ent);
+                        const uint32_t ent1 = lut_ld(lut_l, stride, rs.bh);
+                        ow.merge(ent);
+                        rs.consume_t(ent1);
+                        rs.refill();
+                        ent = lut_ld(lut_l, stride, rs.bh);
+                        ow.merge(ent1);
+                        ow.store();
+                    }
+                    if (half + 1 < kWindow / 32) {
+                        // a 64-lookup window flushes after its first 32 lookups
+                        // (at most 65 bytes and 17 rows so far), so the output
+                        // ring never holds more than one half's bytes
+                        const uint32_t qm = q0 + 4 * ((ow.row() - row0) & (kOutRing - 1)) +
+                                            ow.pending() - p0;
+                        if (!bad) {
+                            if (wide)
+                                flush_groups32(ob, ow, fl, qm);
+                            else
+                                flush_groups(ob, ow, fl, qm);
+                        }
+                        q0 = qm;
+                        row0 = ow.row();
+                        p0 = ow.pending();
+                    }
                 }
             } else {
 #pragma unroll 1
@@ -992,7 +1021,7 @@ __device__ __forceinline__ bool decode_task_s(const StreamInfo &si, uint32_t S_a
                 if (act)
                     rs.top_up();
             }
-            cp_async_wait<3>();
+            cp_async_wait<kInFlight>();
             if (!bad) {
                 if (wide)
                     flush_groups32(ob, ow, fl, q);
@@ -1015,11 +1044,14 @@ __device__ __forceinline__ bool decode_task_s(const StreamInfo &si, uint32_t S_a
     return __any_sync(kFull, bad);
 }
 
+// C: input ring cells per lane (8: 32-lookup windows; 16: 64-lookup windows
+// and twice the input ring)
+template <int C = 8>
 __device__ __forceinline__ bool decode_task(const StreamInfo &si, uint32_t S, uint64_t task,
                                             uint32_t in_s, uint32_t out_s)
 {
-    return S == 1 ? decode_task_s<true>(si, 1, task, in_s, out_s)
-                  : decode_task_s<false>(si, S, task, in_s, out_s);
+    return S == 1 ? decode_task_s<true, C>(si, 1, task, in_s, out_s)
+                  : decode_task_s<false, C>(si, S, task, in_s, out_s);
 }
 
 }  // namespace dec
