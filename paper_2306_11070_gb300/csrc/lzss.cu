@@ -539,8 +539,8 @@ struct CodeReader {
     uint32_t nxt;    // word next - 1, loaded ahead
     uint64_t buf;    // valid bits, left-aligned
     uint32_t have;
-    uint64_t nbits;  // the segment's code length
-    uint64_t pos;    // bits consumed
+    uint32_t nbits;  // the segment's code length (< 2^28: segments are at most 16 MiB)
+    uint32_t pos;    // bits consumed
     __device__ __forceinline__ uint32_t load(uint32_t i) const
     {
         return i < nw ? bswap32(__ldg(w + i)) : 0u;
@@ -553,7 +553,7 @@ struct CodeReader {
         have = 64;
         nxt = load(2);
         next = 3;
-        nbits = code_bits;
+        nbits = (uint32_t)code_bits;
         pos = 0;
     }
     __device__ __forceinline__ uint32_t get(uint32_t k)  // k <= 32 bits, right-aligned
@@ -594,35 +594,35 @@ __device__ __forceinline__ void store_out_word(uint8_t *y, uint64_t m, uint64_t 
 template <bool kRing>
 struct OutBits {
     uint8_t *y;      // the segment's output (16-byte aligned)
-    uint64_t m;      // its bytes
+    uint32_t m;      // its bytes (at most 16 MiB)
     uint32_t W;
     uint32_t *ring;  // kRing: kDecRing words, word q at q mod kDecRing
     uint32_t pend;   // bits of the word being filled, left-aligned
     uint32_t npend;  // their count
-    uint64_t pos;    // bits produced
-    __device__ __forceinline__ uint32_t word_at(int64_t q) const  // output word q (may be < 0)
+    uint32_t pos;    // bits produced (< 2^27)
+    __device__ __forceinline__ uint32_t word_at(int32_t q) const  // output word q (may be < 0)
     {
         if (q < 0) {  // the dictionary: virtual word q + W/32 (W >= 32 here)
-            return dict_word((uint32_t)(q + (int64_t)(W / 32)));
+            return dict_word((uint32_t)(q + (int32_t)(W / 32)));
         }
-        if ((uint64_t)q == (pos >> 5))
+        if ((uint32_t)q == (pos >> 5))
             return pend;
-        if ((uint64_t)q > (pos >> 5))
+        if ((uint32_t)q > (pos >> 5))
             return 0u;
         if (kRing)
             return ring[(uint32_t)q & (kDecRing - 1)];
         return bswap32(__ldcg(reinterpret_cast<const uint32_t *>(y) + q));
     }
     // the 32 bits at output bit s (s may be negative: the dictionary)
-    __device__ __forceinline__ uint32_t bits_at(int64_t s) const
+    __device__ __forceinline__ uint32_t bits_at(int32_t s) const
     {
         if (W < 32 && s < 0) {  // narrow dictionary, bit by bit
             uint32_t out = 0;
             for (int i = 0; i < 32; ++i) {
-                const int64_t t = s + i;
+                const int32_t t = s + i;
                 uint32_t b;
                 if (t < 0) {
-                    const uint64_t j = (uint64_t)(t + (int64_t)W);
+                    const uint32_t j = (uint32_t)(t + (int32_t)W);
                     b = (((uint32_t)(j >> 3) & 255) >> (7 - (j & 7))) & 1;
                 } else {
                     b = (word_at(t >> 5) >> (31 - (t & 31))) & 1;
@@ -631,7 +631,7 @@ struct OutBits {
             }
             return out;
         }
-        const int64_t q = s >> 5;  // floor
+        const int32_t q = s >> 5;  // floor
         const uint32_t sh = (uint32_t)(s & 31);
         const uint32_t a = word_at(q), b = word_at(q + 1);
         return sh ? __funnelshift_l(b, a, sh) : a;
@@ -652,7 +652,7 @@ struct OutBits {
         }
         pos += k;
     }
-    __device__ __forceinline__ void complete(uint64_t q, uint32_t w) const
+    __device__ __forceinline__ void complete(uint32_t q, uint32_t w) const
     {
         if (!kRing) {
             if (4 * q + 4 <= m)
@@ -663,23 +663,23 @@ struct OutBits {
         }
         ring[(uint32_t)q & (kDecRing - 1)] = w;
         if ((q & 3) == 3) {  // a whole 16-byte group
-            const uint64_t g = q >> 2;
+            const uint32_t g = q >> 2;
             if (16 * g + 16 <= m) {
                 const uint32_t r = (uint32_t)(q - 3) & (kDecRing - 1);
                 *reinterpret_cast<uint4 *>(y + 16 * g) =
                     make_uint4(bswap32(ring[r]), bswap32(ring[r + 1]), bswap32(ring[r + 2]),
                                bswap32(ring[r + 3]));
             } else {
-                for (uint64_t j = q - 3; j <= q; ++j)
+                for (uint32_t j = q - 3; j <= q; ++j)
                     store_out_word(y, m, j, ring[(uint32_t)j & (kDecRing - 1)]);
             }
         }
     }
     __device__ __forceinline__ void finish() const
     {
-        const uint64_t q = pos >> 5;  // the word being filled
+        const uint32_t q = pos >> 5;  // the word being filled
         if (kRing)  // completed words of the last, unfinished group
-            for (uint64_t j = q & ~3ull; j < q; ++j)
+            for (uint32_t j = q & ~3u; j < q; ++j)
                 store_out_word(y, m, j, ring[(uint32_t)j & (kDecRing - 1)]);
         if (npend)
             store_out_word(y, m, q, pend);
@@ -689,10 +689,10 @@ struct OutBits {
 // Decode one segment's tokens; false if the code is corrupt.
 template <bool kRing>
 __device__ __forceinline__ bool decode_segment(CodeReader &rd, OutBits<kRing> &ob, const LzParams &P,
-                                               uint64_t nbits)
+                                               uint32_t nbits)
 {
     if (P.dict == 2) {
-        const uint64_t raw = nbits < P.W ? nbits : P.W;
+        const uint32_t raw = nbits < P.W ? nbits : P.W;
         while (ob.pos < raw) {
             const uint32_t k = raw - ob.pos < 32 ? (uint32_t)(raw - ob.pos) : 32u;
             if (rd.pos + k > rd.nbits)
@@ -703,18 +703,18 @@ __device__ __forceinline__ bool decode_segment(CodeReader &rd, OutBits<kRing> &o
     while (ob.pos < nbits) {
         if (rd.pos >= rd.nbits)
             return false;
-        const uint64_t r = nbits - ob.pos;
+        const uint32_t r = nbits - ob.pos;
         if (rd.get(1)) {
             if (rd.pos + P.ob + P.lb > rd.nbits)
                 return false;
-            const uint64_t d = (uint64_t)rd.get(P.ob) + 1;
+            const uint32_t d = rd.get(P.ob) + 1;
             const uint32_t len = rd.get(P.lb) + P.lmin;
             if (len > P.lmax || len > r || (P.dict == 2 && d > ob.pos))
                 return false;
-            uint32_t v = ob.bits_at((int64_t)ob.pos - (int64_t)d);
+            uint32_t v = ob.bits_at((int32_t)ob.pos - (int32_t)d);
             if (d < len) {  // the source runs into these bits: period d
                 v &= ~(0xffffffffu >> d);
-                for (uint32_t sh = (uint32_t)d; sh < len; sh <<= 1)
+                for (uint32_t sh = d; sh < len; sh <<= 1)
                     v |= v >> sh;
             }
             ob.put(v, len);
@@ -757,25 +757,25 @@ __global__ void __launch_bounds__(kLzDecThreads) k_lzss_decode(const uint8_t *__
         if (use_ring) {
             OutBits<true> ob;
             ob.y = out + s * seg;
-            ob.m = m;
+            ob.m = (uint32_t)m;
             ob.W = P.W;
             ob.ring = rings + threadIdx.x * (kDecRing + 1);
             ob.pend = 0;
             ob.npend = 0;
             ob.pos = 0;
-            good = decode_segment(rd, ob, P, 8 * m);
+            good = decode_segment(rd, ob, P, (uint32_t)(8 * m));
             if (good)
                 ob.finish();
         } else {
             OutBits<false> ob;
             ob.y = out + s * seg;
-            ob.m = m;
+            ob.m = (uint32_t)m;
             ob.W = P.W;
             ob.ring = nullptr;
             ob.pend = 0;
             ob.npend = 0;
             ob.pos = 0;
-            good = decode_segment(rd, ob, P, 8 * m);
+            good = decode_segment(rd, ob, P, (uint32_t)(8 * m));
             if (good)
                 ob.finish();
         }
