@@ -573,7 +573,7 @@ __device__ __forceinline__ bool mad_step(const Job &J, UnitState &st, int step, 
         __syncwarp();
     }
     // groups into the 64-bit window hi:lo, the last completed word out after
-    // each group (see pack_codes for why plain stores are enough when every
+    // each group (see pack32 for why plain stores are enough when every
     // lane has 32 codes)
     // A group that crosses no word boundary would store the same word again:
     // only groups that cross one store (about one group in 2.4 on text),
