@@ -95,6 +95,12 @@ __device__ __forceinline__ uint32_t find_owner(const uint64_t *base, uint32_t co
     return lo;
 }
 
+// The first input byte of a unit from its owner entry.
+__device__ __forceinline__ const uint8_t *unit_ptr(uint4 o)
+{
+    return reinterpret_cast<const uint8_t *>((uint64_t)o.x | ((uint64_t)o.y << 32));
+}
+
 // A status word read once by thread 0 and broadcast, so that every thread of
 // the CTA takes the same branch even while other CTAs may be setting it.
 __device__ __forceinline__ bool uniform_failed(const int32_t *status)
@@ -119,8 +125,27 @@ __device__ __forceinline__ unsigned int take_ticket(unsigned int *ctl, int phase
     return t;
 }
 
+// Thread 0's value of t, for every thread of the CTA (a CTA barrier first,
+// so it also ends the work of the item before).  The ticket loops below take
+// their next ticket in thread 0 when an item starts and broadcast it when
+// the item ends, so the atomic's round trip overlaps the item's work.
+__device__ __forceinline__ unsigned int cta_broadcast(unsigned int t)
+{
+    __shared__ unsigned int s_b;
+    __syncthreads();
+    if (threadIdx.x == 0)
+        s_b = t;
+    __syncthreads();
+    return s_b;
+}
+
+__device__ __forceinline__ unsigned int prefetch_ticket(unsigned int *ctl, int phase)
+{
+    return threadIdx.x == 0 ? atomicAdd(ctl + kCtlTicket0 + phase, 1u) : 0u;
+}
+
 // ------------------------------------------------------------------ compress
-__global__ void __launch_bounds__(kBatchBlock, 3) k_batch_compress(BatchArgs a)
+__global__ void __launch_bounds__(kBatchBlock, 2) k_batch_compress(BatchArgs a)
 {
     extern __shared__ uint4 smem_raw[];
     __shared__ unsigned long long s_hist[256];
@@ -129,44 +154,84 @@ __global__ void __launch_bounds__(kBatchBlock, 3) k_batch_compress(BatchArgs a)
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const uint64_t total_units = a.unit_base[a.count];
 
-    // phase 0: clear the per-buffer statuses
+    // phase 0: clear the per-buffer statuses; record the owner of every unit
+    // and encode item (one search each, all at once), so that the phases
+    // below find a unit's or an item's buffer with one load
     for (uint32_t b = blockIdx.x * kBatchBlock + tid; b < a.count; b += gridDim.x * kBatchBlock)
         *a.bufs[b].status = 0;
+    const uint64_t total_items = a.item_base[a.count];
+    {
+        const uint64_t t0 = (uint64_t)blockIdx.x * kBatchBlock + tid, nt = (uint64_t)gridDim.x * kBatchBlock;
+        for (uint64_t g = t0; g < total_units; g += nt) {
+            const uint32_t b = find_owner(a.unit_base, a.count, g);
+            const uint64_t at = (g - a.unit_base[b]) * kUnitSymbols, n = a.bufs[b].in_bytes;
+            const uintptr_t p = reinterpret_cast<uintptr_t>(a.bufs[b].in + at);
+            a.unit_owner[g] = make_uint4((uint32_t)p, (uint32_t)((uint64_t)p >> 32),
+                                         (uint32_t)(n - at < kUnitSymbols ? n - at : kUnitSymbols), b);
+        }
+        for (uint64_t it = t0; it < total_items; it += nt) {
+            const uint32_t b = find_owner(a.item_base, a.count, it);
+            const uint64_t u0 = a.unit_base[b];
+            a.item_owner[it] = make_uint4(b, (uint32_t)(it - a.item_base[b]), (uint32_t)u0,
+                                          (uint32_t)(u0 >> 32));
+        }
+    }
     if (!grid_barrier(a.ctl, a.fail, a.barrier_extra)) {
         fail_all(a.bufs, a.count);
         return;
     }
 
-    // phase 1: per-unit histograms (columns never cleared: folds are differenced)
+    // phase 1: per-unit histograms (columns never cleared: folds are
+    // differenced).  Two sets of columns, used by alternate units: a unit's
+    // counts go to one set while the other set's fold of the unit before may
+    // still run, so one CTA barrier per unit suffices (the next unit counted
+    // into a set starts after the barrier that follows the fold of that set)
     {
-        uint32_t *cnt = reinterpret_cast<uint32_t *>(smem_raw);
-        for (int i = tid; i < 256 * 32; i += kBatchBlock)
+        uint32_t *cnt = reinterpret_cast<uint32_t *>(smem_raw);  // [2][256][32]
+        for (int i = tid; i < 2 * 256 * 32; i += kBatchBlock)
             cnt[i] = 0;
-        const uint32_t col = smem_u32(cnt) + 4u * lane;
-        uint32_t prev = 0;
+        const uint32_t col0 = smem_u32(cnt) + 4u * lane;
+        uint32_t prev0 = 0u, prev1 = 0u;  // folds of each set at its previous unit
+        uint32_t set = 0;
         uint4 v[hst::kVecPerThread];
+        // a unit is counted while the next two units' bytes and the owner
+        // entry of the one after them are in flight
+        const uint64_t G = gridDim.x;
         uint64_t g = blockIdx.x;
-        uint32_t b = g < total_units ? find_owner(a.unit_base, a.count, g) : 0;
+        const uint4 none = make_uint4(0u, 0u, 0u, 0u);
+        uint4 o0 = g < total_units ? a.unit_owner[g] : none;
+        uint4 o1 = g + G < total_units ? a.unit_owner[g + G] : none;
+        uint4 o2 = g + 2 * G < total_units ? a.unit_owner[g + 2 * G] : none;
+        uint4 v2[hst::kVecPerThread];
         if (g < total_units)
-            hst::load_unit(a.bufs[b].in, a.bufs[b].in_bytes, g - a.unit_base[b], v);
+            hst::load_unit(unit_ptr(o0), o0.z, 0, v);
+        if (g + G < total_units)
+            hst::load_unit(unit_ptr(o1), o1.z, 0, v2);
         __syncthreads();
-        for (; g < total_units; g += gridDim.x) {
+        for (; g < total_units; g += G) {
             uint4 cur[hst::kVecPerThread];
 #pragma unroll
-            for (int j = 0; j < hst::kVecPerThread; ++j)
+            for (int j = 0; j < hst::kVecPerThread; ++j) {
                 cur[j] = v[j];
-            const uint32_t cb = b;
-            const uint64_t gn = g + gridDim.x;
-            if (gn < total_units) {
-                b = find_owner(a.unit_base, a.count, gn);
-                hst::load_unit(a.bufs[b].in, a.bufs[b].in_bytes, gn - a.unit_base[b], v);
+                v[j] = v2[j];
             }
-            hst::count_unit(a.bufs[cb].in, a.bufs[cb].in_bytes, g - a.unit_base[cb], cur, col);
+            const uint4 co = o0;
+            o0 = o1;
+            o1 = o2;
+            if (g + 2 * G < total_units) {
+                hst::load_unit(unit_ptr(o1), o1.z, 0, v2);
+                if (g + 3 * G < total_units)
+                    o2 = a.unit_owner[g + 3 * G];
+            }
+            hst::count_unit(unit_ptr(co), co.z, 0, cur, col0 + set * (256 * 32 * 4));
             __syncthreads();
-            const uint32_t s = hst::fold_bin(cnt, tid);
-            a.unit_hist[g * 256 + tid] = (uint16_t)(s - prev);
-            prev = s;
-            __syncthreads();
+            const uint32_t s = hst::fold_bin(cnt + set * (256 * 32), tid);
+            a.unit_hist[g * 256 + tid] = (uint16_t)(s - (set ? prev1 : prev0));
+            if (set)
+                prev1 = s;
+            else
+                prev0 = s;
+            set ^= 1u;
         }
     }
     if (!grid_barrier(a.ctl, a.fail, a.barrier_extra)) {
@@ -177,10 +242,8 @@ __global__ void __launch_bounds__(kBatchBlock, 3) k_batch_compress(BatchArgs a)
     // phase 2: per buffer codebook, unit offsets and header
     {
         cbk::CodebookShared &csh = *reinterpret_cast<cbk::CodebookShared *>(smem_raw);
-        for (;;) {
-            const unsigned int b = take_ticket(a.ctl, 0);
-            if (b >= a.count)
-                break;
+        for (unsigned int b = take_ticket(a.ctl, 0); b < a.count;) {
+            const unsigned int nxt = prefetch_ticket(a.ctl, 0);
             const BatchBuf B = a.bufs[b];
             const uint64_t u0 = a.unit_base[b], nu = a.unit_base[b + 1] - u0;
             unsigned long long h = 0;
@@ -230,7 +293,7 @@ __global__ void __launch_bounds__(kBatchBlock, 3) k_batch_compress(BatchArgs a)
             const enc::Job J = enc::make_job(B.in, B.in_bytes, a.cs, off, B.out, B.out_cap);
             if (!uniform_failed(B.status))
                 enc::write_header(J, a.cbs + b, B.out_bytes, B.status);
-            __syncthreads();
+            b = cta_broadcast(nxt);
         }
     }
     if (!grid_barrier(a.ctl, a.fail, a.barrier_extra)) {
@@ -242,36 +305,34 @@ __global__ void __launch_bounds__(kBatchBlock, 3) k_batch_compress(BatchArgs a)
     {
         uint32_t *tbl = reinterpret_cast<uint32_t *>(smem_raw);
         uint32_t *wob = tbl + enc::kTblWords + warp * enc::kWarpObuf;
-        const uint64_t total_items = a.item_base[a.count];
         uint32_t have = 0xffffffffu;  // buffer whose table is loaded
         bool fast = true;
         int group = 1;
-        for (;;) {
-            const unsigned int it = take_ticket(a.ctl, 1);
-            if (it >= total_items)
-                break;
-            const uint32_t b = find_owner(a.item_base, a.count, it);
+        for (unsigned int it = take_ticket(a.ctl, 1); it < total_items;) {
+            const unsigned int nxt = prefetch_ticket(a.ctl, 1);
+            const uint4 ow = a.item_owner[it];  // (buffer, item within it, first unit)
+            const uint32_t b = ow.x;
             const BatchBuf B = a.bufs[b];
-            if (uniform_failed(B.status))
-                continue;  // this buffer's codebook failed
-            if (b != have) {
-                const uint32_t max_len = a.cbs[b].max_len;
-                fast = max_len <= (uint32_t)enc::kFastMaxLen;
-                group = enc::emit_group(max_len);
-                enc::build_table(a.cbs + b, tbl, fast);
-                __syncthreads();
-                have = b;
+            if (!uniform_failed(B.status)) {  // else this buffer's codebook failed
+                if (b != have) {
+                    const uint32_t max_len = a.cbs[b].max_len;
+                    fast = max_len <= (uint32_t)enc::kFastMaxLen;
+                    group = enc::emit_group(max_len);
+                    enc::build_table(a.cbs + b, tbl, fast);
+                    __syncthreads();
+                    have = b;
+                }
+                const uint64_t u0 = ow.z | ((uint64_t)ow.w << 32);
+                const enc::Job J =
+                    enc::make_job(B.in, B.in_bytes, a.cs, a.unit_off + u0 + b, B.out, B.out_cap);
+                const uint64_t u = (uint64_t)ow.y * kUnitsPerItem + warp;
+                bool overflow = false;
+                if (u < J.units)
+                    overflow = enc::encode_unit(J, u, tbl, fast, group, wob);
+                if (overflow)
+                    set_status(B.status, HUFF_ERR_CAPACITY);
             }
-            const uint64_t u0 = a.unit_base[b];
-            const enc::Job J =
-                enc::make_job(B.in, B.in_bytes, a.cs, a.unit_off + u0 + b, B.out, B.out_cap);
-            const uint64_t u = (uint64_t)(it - a.item_base[b]) * kUnitsPerItem + warp;
-            bool overflow = false;
-            if (u < J.units)
-                overflow = enc::encode_unit(J, u, tbl, fast, group, wob);
-            if (overflow)
-                set_status(B.status, HUFF_ERR_CAPACITY);
-            __syncthreads();  // the table may be rebuilt for the next item
+            it = cta_broadcast(nxt);  // also: the table may be rebuilt for the next item
         }
     }
 }
@@ -351,14 +412,11 @@ __global__ void __launch_bounds__(kBatchBlock, 2) k_batch_decompress(BatchArgs a
     bool ready = false;
     dec::StreamInfo si;
     uint32_t S = 1;
-    for (;;) {
-        const unsigned int it = take_ticket(a.ctl, 2);
-        if (it >= total_items)
-            break;
+    for (unsigned int it = take_ticket(a.ctl, 2); it < total_items;) {
+        const unsigned int nxt = prefetch_ticket(a.ctl, 2);
         const uint32_t b = find_owner(a.dec_items, a.count, it);
         const BatchBuf B = a.bufs[b];
         if (b != have) {
-            __syncthreads();
             ready = dec::prepare<kBatchBlock>(B.in, B.in_bytes, B.out, B.out_cap, B.out_bytes,
                                               B.status, it == a.dec_items[b] && tid == 0, sh,
                                               scratch, si);
@@ -366,18 +424,23 @@ __global__ void __launch_bounds__(kBatchBlock, 2) k_batch_decompress(BatchArgs a
                 S = dec::pick_split(si.chunks, a.min_lanes);
             have = b;
         }
-        if (!ready || uniform_failed(B.status))
-            continue;
-        const uint64_t tasks = (si.chunks + (32 / S) - 1) / (32 / S);
-        const uint64_t task = (uint64_t)(it - a.dec_items[b]) * kTasksPerItem + warp;
-        if (task < tasks && dec::decode_task(si, S, task, in_s, out_s)) {
-            if (lane == 0)
-                set_status(B.status, HUFF_ERR_CORRUPT_STREAM);
+        if (ready && !uniform_failed(B.status)) {
+            const uint64_t tasks = (si.chunks + (32 / S) - 1) / (32 / S);
+            const uint64_t task = (uint64_t)(it - a.dec_items[b]) * kTasksPerItem + warp;
+            if (task < tasks && dec::decode_task(si, S, task, in_s, out_s)) {
+                if (lane == 0)
+                    set_status(B.status, HUFF_ERR_CORRUPT_STREAM);
+            }
         }
+        it = cta_broadcast(nxt);  // also: the tables may be rebuilt for the next item
     }
 }
 
-constexpr int kCompressSmem = (enc::kTblWords + kBatchWarps * enc::kWarpObuf) * 4;
+// phase 1's two sets of histogram columns, or phase 3's code table and word
+// buffers, whichever is larger
+constexpr int kCompressSmem = (enc::kTblWords + kBatchWarps * enc::kWarpObuf) * 4 > 2 * 256 * 32 * 4
+                                  ? (enc::kTblWords + kBatchWarps * enc::kWarpObuf) * 4
+                                  : 2 * 256 * 32 * 4;
 
 }  // namespace
 
@@ -387,7 +450,8 @@ constexpr int kCompressSmem = (enc::kTblWords + kBatchWarps * enc::kWarpObuf) * 
 namespace huff {
 
 // Device block of one batch: control words, descriptors, prefix arrays and
-// (compress) per-unit histograms, unit offsets and codebooks.
+// (compress) per-unit histograms, unit offsets, codebooks and the owners of
+// units and encode items.
 void batch_layout(const huff_batch_desc_t *descs, uint32_t count, huff_op_t op, BatchLayout &L)
 {
     auto al = [](uint64_t x) { return (x + 255) & ~uint64_t(255); };
@@ -418,7 +482,7 @@ void batch_layout(const huff_batch_desc_t *descs, uint32_t count, huff_op_t op, 
     off = al(off + 8 * (count + 1));
     L.o_di = off;
     off = al(off + 8 * (count + 1));
-    L.o_uh = L.o_uo = L.o_cb = off;
+    L.o_uh = L.o_uo = L.o_cb = L.o_uw = L.o_iw = off;
     if (op == HUFF_BATCH_COMPRESS) {
         L.o_uh = off;
         off = al(off + 512 * total_units);
@@ -426,6 +490,10 @@ void batch_layout(const huff_batch_desc_t *descs, uint32_t count, huff_op_t op, 
         off = al(off + 8 * (total_units + count));
         L.o_cb = off;
         off = al(off + sizeof(huff_codebook_t) * count);
+        L.o_uw = off;
+        off = al(off + 16 * total_units);
+        L.o_iw = off;
+        off = al(off + 16 * L.item_base[count]);
     }
     L.bytes = off;
     // the host-side part copied to the device: descriptors and prefixes
@@ -447,6 +515,8 @@ BatchArgs batch_args(const BatchLayout &L, void *d_block, uint32_t cs, uint32_t 
     a.unit_hist = c ? reinterpret_cast<uint16_t *>(blk + L.o_uh) : nullptr;
     a.unit_off = c ? reinterpret_cast<unsigned long long *>(blk + L.o_uo) : nullptr;
     a.cbs = c ? reinterpret_cast<huff_codebook_t *>(blk + L.o_cb) : nullptr;
+    a.unit_owner = c ? reinterpret_cast<uint4 *>(blk + L.o_uw) : nullptr;
+    a.item_owner = c ? reinterpret_cast<uint4 *>(blk + L.o_iw) : nullptr;
     a.min_lanes = lanes;
     a.ctl = reinterpret_cast<unsigned int *>(blk + L.o_ctl);
     a.fail = reinterpret_cast<int32_t *>(blk + L.o_ctl + sizeof(unsigned int) * kCtlWords);

@@ -34,6 +34,10 @@ struct BatchArgs {
     uint16_t *unit_hist;            // compress: [units][256]
     unsigned long long *unit_off;   // compress: per buffer units_b + 1 entries at unit_base[b] + b
     huff_codebook_t *cbs;           // compress: [count]
+    uint4 *unit_owner;              // compress: [units] (its first input byte, low and high
+                                    //   words; its bytes; its buffer), set in phase 0
+    uint4 *item_owner;              // compress: [items] (buffer, item within it, its first
+                                    //   unit's index in unit_base order, low and high words)
     uint64_t *dec_items;            // decompress: [count + 1] items, then their prefix
     uint32_t min_lanes;             // decompress: lanes per buffer to aim for
     unsigned int *ctl;              // kCtlWords
@@ -47,7 +51,7 @@ struct BatchLayout {
     huff_op_t op;
     std::vector<BatchBuf> bufs;
     std::vector<uint64_t> unit_base, item_base;
-    uint64_t o_ctl, o_bufs, o_ub, o_ib, o_di, o_uh, o_uo, o_cb;
+    uint64_t o_ctl, o_bufs, o_ub, o_ib, o_di, o_uh, o_uo, o_cb, o_uw, o_iw;
     uint64_t bytes;         // device block size
     uint64_t upload_bytes;  // leading part filled from the host
 };

@@ -144,8 +144,10 @@ uint64_t out_need(const huff_server_t *S, int32_t op, uint64_t in_bytes, uint64_
 // Device block bytes of a round over `count` requests of `units` total.
 uint64_t round_block_bytes(uint32_t count, uint64_t units)
 {
-    return 4096 + 64ull * count + 16ull * (count + 1) * 3 + 520ull * units + 16ull * count +
-           sizeof(huff_codebook_t) * count;
+    // descriptors and prefixes; per unit its histogram, offset and owner; per
+    // encode item (at most units / 8 + count) its owner; codebooks
+    return 4096 + 64ull * count + 16ull * (count + 1) * 3 + 536ull * units + 16ull * count +
+           16ull * (units / huff::kUnitsPerItem + count) + 512 + sizeof(huff_codebook_t) * count;
 }
 
 // Try to start a round of `op` on slot r; returns true if it launched.
