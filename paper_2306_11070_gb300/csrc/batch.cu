@@ -144,6 +144,32 @@ __device__ __forceinline__ unsigned int prefetch_ticket(unsigned int *ctl, int p
     return threadIdx.x == 0 ? atomicAdd(ctl + kCtlTicket0 + phase, 1u) : 0u;
 }
 
+// The barrier of one half: named barrier 1 or 2 over its kHalf threads
+// (immediate ids, so the kernel reserves three barriers, not all sixteen).
+struct HalfSync {
+    int half;
+    __device__ __forceinline__ void operator()() const
+    {
+        static_assert(kHalf == 128, "the barrier counts below are kHalf");
+        if (half)
+            asm volatile("bar.sync 2, 128;" ::: "memory");
+        else
+            asm volatile("bar.sync 1, 128;" ::: "memory");
+    }
+};
+
+// Thread 0 of the half's value of t, for every thread of the half (a
+// barrier of the half first, so it also ends the half's work before).
+__device__ __forceinline__ unsigned int half_broadcast(unsigned int t, HalfSync hs)
+{
+    __shared__ unsigned int s_h[2];
+    hs();
+    if ((threadIdx.x & (kHalf - 1)) == 0)
+        s_h[hs.half] = t;
+    hs();
+    return s_h[hs.half];
+}
+
 // ------------------------------------------------------------------ compress
 __global__ void __launch_bounds__(kBatchBlock, 2) k_batch_compress(BatchArgs a)
 {
@@ -301,58 +327,66 @@ __global__ void __launch_bounds__(kBatchBlock, 2) k_batch_compress(BatchArgs a)
         return;
     }
 
-    // phase 3: encode
+    // phase 3: encode, each half of the CTA on its own items with its own
+    // code table (its named barrier; no CTA barrier from here on)
     {
-        uint32_t *tbl = reinterpret_cast<uint32_t *>(smem_raw);
-        uint32_t *wob = tbl + enc::kTblWords + warp * enc::kWarpObuf;
+        const int half = warp / kHalfWarps, htid = tid & (kHalf - 1), hwarp = warp % kHalfWarps;
+        const HalfSync hs{half};
+        uint32_t *tbl = reinterpret_cast<uint32_t *>(smem_raw) + half * enc::kTblWords;
+        uint32_t *wob = reinterpret_cast<uint32_t *>(smem_raw) + 2 * enc::kTblWords + warp * enc::kWarpObuf;
         uint32_t have = 0xffffffffu;  // buffer whose table is loaded
         bool fast = true;
         int group = 1;
-        for (unsigned int it = take_ticket(a.ctl, 1); it < total_items;) {
-            const unsigned int nxt = prefetch_ticket(a.ctl, 1);
+        const unsigned int t0 = htid == 0 ? atomicAdd(a.ctl + kCtlTicket0 + 1, 1u) : 0u;
+        for (unsigned int it = half_broadcast(t0, hs); it < total_items;) {
+            // the next ticket is taken now and broadcast when this item ends
+            const unsigned int nxt = htid == 0 ? atomicAdd(a.ctl + kCtlTicket0 + 1, 1u) : 0u;
             const uint4 ow = a.item_owner[it];  // (buffer, item within it, first unit)
             const uint32_t b = ow.x;
             const BatchBuf B = a.bufs[b];
-            if (!uniform_failed(B.status)) {  // else this buffer's codebook failed
+            const bool failed =  // this buffer's codebook failed
+                half_broadcast(htid == 0 ? (unsigned int)chain_failed(B.status) : 0u, hs) != 0;
+            if (!failed) {
                 if (b != have) {
                     const uint32_t max_len = a.cbs[b].max_len;
                     fast = max_len <= (uint32_t)enc::kFastMaxLen;
                     group = enc::emit_group(max_len);
-                    enc::build_table(a.cbs + b, tbl, fast);
-                    __syncthreads();
+                    enc::build_table(a.cbs + b, tbl, fast, htid, kHalf);
+                    hs();
                     have = b;
                 }
                 const uint64_t u0 = ow.z | ((uint64_t)ow.w << 32);
                 const enc::Job J =
                     enc::make_job(B.in, B.in_bytes, a.cs, a.unit_off + u0 + b, B.out, B.out_cap);
-                const uint64_t u = (uint64_t)ow.y * kUnitsPerItem + warp;
+                const uint64_t u = (uint64_t)ow.y * kUnitsPerItem + hwarp;
                 bool overflow = false;
                 if (u < J.units)
                     overflow = enc::encode_unit(J, u, tbl, fast, group, wob);
                 if (overflow)
                     set_status(B.status, HUFF_ERR_CAPACITY);
             }
-            it = cta_broadcast(nxt);  // also: the table may be rebuilt for the next item
+            it = half_broadcast(nxt, hs);  // also: the table may be rebuilt for the next item
         }
     }
 }
 
 // ------------------------------------------------------------------ decompress
-// One copy of the lookup table per CTA (tables are rebuilt per buffer, and
-// most buffers of a batch are small); dynamic shared memory as in decode.cu:
-// the tables, then from the next 4 KiB boundary a 4 KiB output block and a
-// 4 KiB input block per warp.
+// Each half of a CTA (4 warps, its own named barrier) decodes items of its
+// own buffer: an item is one task per warp of the half, so a small buffer
+// leaves fewer lanes idle than with items of the whole CTA.  One copy of the
+// lookup tables per half (tables are rebuilt per buffer, and most buffers of
+// a batch are small); dynamic shared memory as in decode.cu: the two halves'
+// tables, then from the next 4 KiB boundary a 4 KiB output block per warp,
+// then a 4 KiB input block per warp (a half builds its tables with its own
+// warps' input blocks as scratch).
 constexpr int kBatchCopies = 1;
 constexpr size_t kDecompTables = (sizeof(dec::DecodeShared<kBatchCopies>) + 15) & ~size_t(15);
-constexpr size_t kDecompressSmem = kDecompTables + 4096 + (size_t)kBatchWarps * 2 * 4096;
+constexpr size_t kDecompressSmem = 2 * kDecompTables + 4096 + (size_t)kBatchWarps * 2 * 4096;
 
 __global__ void __launch_bounds__(kBatchBlock, 2) k_batch_decompress(BatchArgs a)
 {
     extern __shared__ __align__(16) unsigned char dsm[];
-    dec::DecodeShared<kBatchCopies> &sh = *reinterpret_cast<dec::DecodeShared<kBatchCopies> *>(dsm);
-    const uint32_t rings = (smem_u32(dsm) + (uint32_t)kDecompTables + 4095u) & ~4095u;
-    uint16_t *scratch = reinterpret_cast<uint16_t *>(dsm + (rings - smem_u32(dsm)) +
-                                                     kBatchWarps * 4096);
+    const uint32_t rings = (smem_u32(dsm) + 2u * (uint32_t)kDecompTables + 4095u) & ~4095u;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
 
     // phase 1: statuses and work sizes from the headers
@@ -404,7 +438,14 @@ __global__ void __launch_bounds__(kBatchBlock, 2) k_batch_decompress(BatchArgs a
         return;
     }
 
-    // phase 3: decode items
+    // phase 3: decode items, each half of the CTA on its own (its named
+    // barrier; no CTA barrier from here on)
+    const int half = warp / kHalfWarps, htid = tid & (kHalf - 1), hwarp = warp % kHalfWarps;
+    const HalfSync hs{half};
+    dec::DecodeShared<kBatchCopies> &sh =
+        *reinterpret_cast<dec::DecodeShared<kBatchCopies> *>(dsm + half * kDecompTables);
+    uint16_t *scratch = reinterpret_cast<uint16_t *>(
+        dsm + (rings - smem_u32(dsm)) + (kBatchWarps + half * kHalfWarps) * 4096);
     const uint32_t out_s = rings + warp * 4096 + lane * 4;
     const uint32_t in_s = rings + (kBatchWarps + warp) * 4096 + lane * 16;
     const uint64_t total_items = a.dec_items[a.count];
@@ -412,34 +453,38 @@ __global__ void __launch_bounds__(kBatchBlock, 2) k_batch_decompress(BatchArgs a
     bool ready = false;
     dec::StreamInfo si;
     uint32_t S = 1;
-    for (unsigned int it = take_ticket(a.ctl, 2); it < total_items;) {
-        const unsigned int nxt = prefetch_ticket(a.ctl, 2);
+    const unsigned int t0 = htid == 0 ? atomicAdd(a.ctl + kCtlTicket0 + 2, 1u) : 0u;
+    for (unsigned int it = half_broadcast(t0, hs); it < total_items;) {
+        // the next ticket is taken now and broadcast when this item ends
+        const unsigned int nxt = htid == 0 ? atomicAdd(a.ctl + kCtlTicket0 + 2, 1u) : 0u;
         const uint32_t b = find_owner(a.dec_items, a.count, it);
         const BatchBuf B = a.bufs[b];
         if (b != have) {
-            ready = dec::prepare<kBatchBlock>(B.in, B.in_bytes, B.out, B.out_cap, B.out_bytes,
-                                              B.status, it == a.dec_items[b] && tid == 0, sh,
-                                              scratch, si);
+            ready = dec::prepare<kHalf>(B.in, B.in_bytes, B.out, B.out_cap, B.out_bytes, B.status,
+                                        it == a.dec_items[b] && htid == 0, sh, scratch, si, htid,
+                                        hs);
             if (ready)
                 S = dec::pick_split(si.chunks, a.min_lanes);
             have = b;
         }
-        if (ready && !uniform_failed(B.status)) {
+        const bool failed =
+            half_broadcast(htid == 0 ? (unsigned int)chain_failed(B.status) : 0u, hs) != 0;
+        if (ready && !failed) {
             const uint64_t tasks = (si.chunks + (32 / S) - 1) / (32 / S);
-            const uint64_t task = (uint64_t)(it - a.dec_items[b]) * kTasksPerItem + warp;
+            const uint64_t task = (uint64_t)(it - a.dec_items[b]) * kTasksPerItem + hwarp;
             if (task < tasks && dec::decode_task(si, S, task, in_s, out_s)) {
                 if (lane == 0)
                     set_status(B.status, HUFF_ERR_CORRUPT_STREAM);
             }
         }
-        it = cta_broadcast(nxt);  // also: the tables may be rebuilt for the next item
+        it = half_broadcast(nxt, hs);  // also: the tables may be rebuilt for the next item
     }
 }
 
-// phase 1's two sets of histogram columns, or phase 3's code table and word
-// buffers, whichever is larger
-constexpr int kCompressSmem = (enc::kTblWords + kBatchWarps * enc::kWarpObuf) * 4 > 2 * 256 * 32 * 4
-                                  ? (enc::kTblWords + kBatchWarps * enc::kWarpObuf) * 4
+// phase 1's two sets of histogram columns, or phase 3's two code tables and
+// word buffers, whichever is larger
+constexpr int kCompressSmem = (2 * enc::kTblWords + kBatchWarps * enc::kWarpObuf) * 4 > 2 * 256 * 32 * 4
+                                  ? (2 * enc::kTblWords + kBatchWarps * enc::kWarpObuf) * 4
                                   : 2 * 256 * 32 * 4;
 
 }  // namespace

@@ -10,8 +10,13 @@ namespace huff {
 
 constexpr int kBatchBlock = 256;
 constexpr int kBatchWarps = kBatchBlock / 32;
-constexpr int kUnitsPerItem = kBatchWarps;  // encode: one unit per warp
-constexpr int kTasksPerItem = kBatchWarps;  // decode: one task per warp
+// The encode and decode phases run each half of a CTA on its own items
+// (its own code or lookup table), so that small buffers leave fewer warps
+// idle than with items of the whole CTA.
+constexpr int kHalf = kBatchBlock / 2;
+constexpr int kHalfWarps = kBatchWarps / 2;
+constexpr int kUnitsPerItem = kHalfWarps;  // encode: one unit per warp of a half
+constexpr int kTasksPerItem = kHalfWarps;  // decode: one task per warp of a half
 
 // control words (device): barrier arrivals and generation, then tickets
 enum { kCtlArrive = 0, kCtlGen = 1, kCtlTicket0 = 2, kCtlWords = 8 };

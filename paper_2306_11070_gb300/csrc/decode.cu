@@ -108,7 +108,7 @@ __global__ void __launch_bounds__(kDecBlock, 1) k_decode(DecodeArgs a)
     }
     StreamInfo si;
     if (!prepare<kDecBlock>(a.stream, a.bytes, a.out, a.cap, a.d_n, a.status,
-                            blockIdx.x == 0 && threadIdx.x == 0, sh, scratch, si))
+                            blockIdx.x == 0 && threadIdx.x == 0, sh, scratch, si, threadIdx.x, CtaSync()))
         return;
     const uint32_t S = pick_split(si.chunks, a.min_chains);
     const uint64_t tasks = (si.chunks + (32 / S) - 1) / (32 / S);

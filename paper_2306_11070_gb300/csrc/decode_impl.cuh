@@ -521,13 +521,19 @@ __device__ __forceinline__ void settle_segment(const Tables &T, const uint8_t *p
 // and the header errors).  `scratch` is shared memory for kLutSize u16 that
 // is free while the tables are built.  Returns true when there are chunks to
 // decode.
-template <int NT, int C>
+// The CTA barrier, as the barrier of prepare's thread group.
+struct CtaSync {
+    __device__ __forceinline__ void operator()() const { __syncthreads(); }
+};
+
+// Validate a stream's header and build its tables, by a group of NT threads
+// (tid = 0..NT-1) whose barrier is sync().
+template <int NT, int C, class Sync>
 __device__ __forceinline__ bool prepare(const uint8_t *stream_in, uint64_t bytes, uint8_t *out,
                                         uint64_t cap, unsigned long long *d_n, int32_t *status,
                                         bool reporter, DecodeShared<C> &sh, uint16_t *scratch,
-                                        StreamInfo &si)
+                                        StreamInfo &si, int tid, Sync sync)
 {
-    const int tid = threadIdx.x;
     const uint8_t *stream = stream_in;
     if (bytes < kHeaderBytes) {
         if (reporter)
@@ -558,7 +564,7 @@ __device__ __forceinline__ bool prepare(const uint8_t *stream_in, uint64_t bytes
         sh.s_nsym = 0;
         sh.s_bad = 0;
     }
-    __syncthreads();
+    sync();
     for (int b = tid; b < 256; b += NT) {
         const uint32_t L = stream[b];
         sh.len_s[b] = (uint8_t)L;
@@ -571,7 +577,7 @@ __device__ __forceinline__ bool prepare(const uint8_t *stream_in, uint64_t bytes
             atomicAdd(&sh.count[L], 1u);
         }
     }
-    __syncthreads();
+    sync();
     const uint32_t max_len = (uint32_t)sh.s_max;
     const int nsym = sh.s_nsym;
     const bool bad_header = sh.s_bad || max_len != max_field || (n > 0 && nsym == 0) ||
@@ -602,7 +608,7 @@ __device__ __forceinline__ bool prepare(const uint8_t *stream_in, uint64_t bytes
             idx += sh.count[L];
         }
     }
-    __syncthreads();
+    sync();
     for (int b = tid; b < 256; b += NT) {
         const uint32_t L = sh.len_s[b];
         if (L) {
@@ -612,7 +618,7 @@ __device__ __forceinline__ bool prepare(const uint8_t *stream_in, uint64_t bytes
             sh.sorted[sh.start[L] + r] = (uint8_t)b;
         }
     }
-    __syncthreads();
+    sync();
     // pass 1: the first code of every 12-bit window, sym | L << 8 (0: none)
     const uint32_t lut_len = max_len < (uint32_t)kLutBits ? max_len : (uint32_t)kLutBits;
     for (int v = tid; v < kLutSize; v += NT) {
@@ -626,7 +632,7 @@ __device__ __forceinline__ bool prepare(const uint8_t *stream_in, uint64_t bytes
         }
         scratch[v] = (uint16_t)ent;
     }
-    __syncthreads();
+    sync();
     // pass 2: append the second code when it also fits in the window
     for (int v = tid; v < kLutSize; v += NT) {
         const uint32_t e0 = scratch[v];
@@ -647,7 +653,7 @@ __device__ __forceinline__ bool prepare(const uint8_t *stream_in, uint64_t bytes
             sh.lut[v * C + c] = ent;
         sh.len0[v] = (uint8_t)first_len;
     }
-    __syncthreads();
+    sync();
 
     const uint64_t pay_words = (bytes - kHeaderBytes - 8 * chunks) / 4;
     const uint64_t pbits = 32 * pay_words;

@@ -97,19 +97,21 @@ __device__ __forceinline__ uint32_t tbl_at(uint32_t a)
     return v;
 }
 
-// Per-lane replicated code table (all threads of the CTA take part).  Fast
-// entry = (code << (32 - len)) | len: the code left-aligned, its length in
-// the low bits, zeros between them (len <= 22 leaves bits 5..9 clear).
-__device__ __forceinline__ void build_table(const huff_codebook_t *cb, uint32_t *tbl, bool fast)
+// Per-lane replicated code table, built by threads tid = 0..nt-1 (by default
+// all threads of the CTA).  Fast entry = (code << (32 - len)) | len: the code
+// left-aligned, its length in the low bits, zeros between them (len <= 22
+// leaves bits 5..9 clear).
+__device__ __forceinline__ void build_table(const huff_codebook_t *cb, uint32_t *tbl, bool fast,
+                                            int tid = threadIdx.x, int nt = blockDim.x)
 {
     if (fast) {
-        for (int i = threadIdx.x; i < kTblWords; i += blockDim.x) {
+        for (int i = tid; i < kTblWords; i += nt) {
             const int b = i >> 5;
             const uint32_t L = cb->len[b];
             tbl[i] = L ? (cb->code[b] << (32 - L)) | L : 0u;
         }
     } else {
-        for (int i = threadIdx.x; i < 256 * 16; i += blockDim.x) {
+        for (int i = tid; i < 256 * 16; i += nt) {
             const int b = i >> 4;
             tbl[i] = cb->code[b];
             tbl[256 * 16 + i] = cb->len[b];
