@@ -176,6 +176,7 @@ __global__ void __launch_bounds__(kBatchBlock, 2) k_batch_compress(BatchArgs a)
     extern __shared__ uint4 smem_raw[];
     __shared__ unsigned long long s_hist[256];
     __shared__ uint32_t s_len[256];
+    __shared__ uint32_t s_bits[kBatchBlock];
     __shared__ unsigned long long s_scan[kBatchWarps];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const uint64_t total_units = a.unit_base[a.count];
@@ -282,16 +283,35 @@ __global__ void __launch_bounds__(kBatchBlock, 2) k_batch_compress(BatchArgs a)
             s_len[tid] = a.cbs[b].len[tid];
             __syncthreads();
             unsigned long long *off = a.unit_off + u0 + b;
-            // unit bit counts, scanned 256 at a time with a running carry
+            // unit bit counts, 256 units at a time: unit i of a tile goes to
+            // warp i mod 8 (one coalesced 512-byte row: lane l dots bins
+            // 8l..8l+7 with their code lengths, the warp sums), through
+            // shared memory to thread i, and the tile is scanned with a
+            // running carry
+            uint32_t L8[8];
+#pragma unroll
+            for (int j = 0; j < 8; ++j)
+                L8[j] = s_len[8 * lane + j];
             unsigned long long carry = 0;
             for (uint64_t t0 = 0; t0 < nu; t0 += kBatchBlock) {
                 const uint64_t u = t0 + tid;
-                uint32_t bits = 0;
-                if (u < nu) {
-                    const uint16_t *uh = a.unit_hist + (u0 + u) * 256;
-                    for (int k = 0; k < 256; ++k)
-                        bits += (uint32_t)uh[k] * s_len[k];
+#pragma unroll 4
+                for (int k = 0; k < kBatchBlock / kBatchWarps; ++k) {
+                    const uint32_t i = (uint32_t)k * kBatchWarps + (uint32_t)warp;
+                    if (t0 + i < nu) {  // warp-uniform
+                        const uint4 q = __ldcg(reinterpret_cast<const uint4 *>(
+                                                   a.unit_hist + (u0 + t0 + i) * 256) + lane);
+                        const uint32_t d = (q.x & 0xffffu) * L8[0] + (q.x >> 16) * L8[1] +
+                                           (q.y & 0xffffu) * L8[2] + (q.y >> 16) * L8[3] +
+                                           (q.z & 0xffffu) * L8[4] + (q.z >> 16) * L8[5] +
+                                           (q.w & 0xffffu) * L8[6] + (q.w >> 16) * L8[7];
+                        const uint32_t t = __reduce_add_sync(0xffffffffu, d);
+                        if (lane == 0)
+                            s_bits[i] = t;
+                    }
                 }
+                __syncthreads();
+                const uint32_t bits = u < nu ? s_bits[tid] : 0u;
                 unsigned long long x = bits;
 #pragma unroll
                 for (int d = 1; d < 32; d <<= 1) {
