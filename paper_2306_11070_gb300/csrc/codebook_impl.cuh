@@ -10,6 +10,7 @@ namespace cbk {
 
 struct CodebookShared {
     unsigned long long w[256];
+    unsigned long long key[256];               // weight * 256 + byte, all ones if absent
     unsigned long long pm[2][512];             // package-merge: the previous and current list
     uint16_t pos[kMaxCodeLen + 1][256];        // package-merge: position of each leaf per list
     int pm_take[kMaxCodeLen + 1];              // package-merge: leaves taken from each list
@@ -111,7 +112,11 @@ __device__ __forceinline__ void build_codebook(const unsigned long long *__restr
         return;
     const int t = threadIdx.x;
     const unsigned long long wt = hist[t];
+    // (weight, byte) as one key where every weight is below 2^56 (any byte
+    // count is)
+    const unsigned long long kt = wt ? (wt << 8) | (unsigned long long)t : ~0ull;
     sh.w[t] = wt;
+    sh.key[t] = kt;
     sh.len_s[t] = 0;
     if (t <= (int)kMaxCodeLen)
         sh.bl[t] = 0;
@@ -119,13 +124,21 @@ __device__ __forceinline__ void build_codebook(const unsigned long long *__restr
         sh.s_max = 0;
     const int present = wt > 0;
     const int m = __syncthreads_count(present);
+    const bool huge = __syncthreads_or((wt >> 56) != 0);  // weights the key cannot hold
 
-    // 1. rank of byte t among present bytes, ordered by (weight, byte)
+    // 1. rank of byte t among present bytes, ordered by (weight, byte): the
+    //    keys below its own (an absent byte's key is above every other)
     if (present) {
         int rank = 0;
-        for (int j = 0; j < 256; ++j) {
-            const unsigned long long wj = sh.w[j];
-            rank += (wj > 0) & ((wj < wt) | ((wj == wt) & (j < t)));
+        if (!huge) {
+#pragma unroll 8
+            for (int j = 0; j < 256; ++j)
+                rank += sh.key[j] < kt;
+        } else {
+            for (int j = 0; j < 256; ++j) {
+                const unsigned long long wj = sh.w[j];
+                rank += (wj > 0) & ((wj < wt) | ((wj == wt) & (j < t)));
+            }
         }
         sh.leaf_sym[rank] = (uint8_t)t;
         sh.nw[rank] = wt;
@@ -135,43 +148,49 @@ __device__ __forceinline__ void build_codebook(const unsigned long long *__restr
     if (m >= 2) {
         // 2. two-queue merge
         if (t == 0) {
-            // the fronts of both queues are kept in registers: a leaf's weight
-            // is loaded once, and a merged node's weight usually never is
+            // the first two entries of each queue are kept in registers (all
+            // ones past a queue's end), so that a take never waits for a
+            // shared load: a leaf's weight is loaded two takes before it can
+            // be needed, and a merged node's weight usually never is.  A tie
+            // takes the leaf (the smaller id).
+            constexpr unsigned long long kNone = ~0ull;
             int li = 0, ii = m, ni = m;
-            unsigned long long lw = sh.nw[0], iw = 0;
+            unsigned long long l0 = sh.nw[0], l1 = sh.nw[1], i0 = kNone, i1 = kNone;  // m >= 2
             for (int step = 0; step < m - 1; ++step) {
-                int a, b;
-                unsigned long long wa, wb;
-                if (li < m && (ii >= ni || lw <= iw)) {
-                    a = li++;
-                    wa = lw;
-                    lw = li < m ? sh.nw[li] : 0ull;
-                } else {
-                    a = ii++;
-                    wa = iw;
-                    iw = ii < ni ? sh.nw[ii] : 0ull;
+                int ab[2];
+                unsigned long long wab[2];
+#pragma unroll
+                for (int k = 0; k < 2; ++k) {
+                    if (l0 <= i0) {
+                        ab[k] = li;
+                        wab[k] = l0;
+                        l0 = l1;
+                        l1 = li + 2 < m ? sh.nw[li + 2] : kNone;
+                        ++li;
+                    } else {
+                        ab[k] = ii;
+                        wab[k] = i0;
+                        i0 = i1;
+                        i1 = ii + 2 < ni ? sh.nw[ii + 2] : kNone;
+                        ++ii;
+                    }
                 }
-                if (li < m && (ii >= ni || lw <= iw)) {
-                    b = li++;
-                    wb = lw;
-                    lw = li < m ? sh.nw[li] : 0ull;
-                } else {
-                    b = ii++;
-                    wb = iw;
-                    iw = ii < ni ? sh.nw[ii] : 0ull;
-                }
-                const unsigned long long w2 = wa + wb;
+                const unsigned long long w2 = wab[0] + wab[1];
                 sh.nw[ni] = w2;
-                sh.par[a] = (int16_t)ni;
-                sh.par[b] = (int16_t)ni;
+                sh.par[ab[0]] = (int16_t)ni;
+                sh.par[ab[1]] = (int16_t)ni;
+                // the new node joins the merged queue at ni
                 if (ii == ni)
-                    iw = w2;  // the merged queue was empty: the new node is its front
+                    i0 = w2;
+                else if (ii + 1 == ni)
+                    i1 = w2;
                 ++ni;
             }
             sh.par[2 * m - 2] = (int16_t)(2 * m - 2);  // the root points at itself
         }
         __syncthreads();
-        // 3. depth = distance to the root, by pointer jumping (9 rounds cover 511 nodes)
+        // 3. depth = distance to the root, by pointer jumping (9 rounds cover
+        //    511 nodes; done early once every ancestor is the root)
         const int nn = 2 * m - 1, root = 2 * m - 2;
         for (int k = t; k < nn; k += 256) {
             sh.dep[k] = (k == root) ? 0 : 1;
@@ -189,15 +208,18 @@ __device__ __forceinline__ void build_codebook(const unsigned long long *__restr
                 }
             }
             __syncthreads();
+            bool at_root = true;
 #pragma unroll
             for (int j = 0; j < 2; ++j) {
                 const int k = t + j * 256;
                 if (k < nn) {
                     sh.dep[k] = nd[j];
                     sh.anc[k] = na[j];
+                    at_root &= na[j] == root;
                 }
             }
-            __syncthreads();
+            if (__syncthreads_and(at_root))
+                break;
         }
         // the Huffman lengths, unless a limit below 32 is exceeded
         if (t < m)

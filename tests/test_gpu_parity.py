@@ -123,6 +123,29 @@ def test_codebook_random_histograms():
         assert nsym == int((h > 0).sum()) and mx == int(oln.max())
 
 
+def test_codebook_weights_of_2_56_and_more():
+    """Weights the packed (weight, byte) key cannot hold take the two-part
+    comparison: equal results, ties included (sums stay below 2^64)."""
+    rng = np.random.default_rng(11)
+    for t in range(60):
+        k = int(rng.integers(2, 33))
+        syms = rng.choice(256, size=k, replace=False)
+        if t % 3 == 0:
+            w = rng.integers(1 << 56, 1 << 58, size=k, dtype=np.uint64)
+        elif t % 3 == 1:  # ties among huge weights
+            w = (np.uint64(1) << np.uint64(56)) * rng.integers(1, 4, size=k).astype(np.uint64)
+        else:  # one huge weight among small ones
+            w = rng.integers(1, 1000, size=k).astype(np.uint64)
+            w[0] = np.uint64(1) << np.uint64(57)
+        h = np.zeros(256, dtype=np.uint64)
+        h[syms] = w
+        (ln, code, nsym, mx), st = _gpu_cb_from_hist(h)
+        ost, oln = oracle.code_lengths(h)
+        assert st == ost == oracle.OK
+        assert np.array_equal(ln, oln)
+        assert np.array_equal(code, oracle.canonical_codes(oln))
+
+
 def test_codebook_fibonacci_boundary():
     f = [1, 1]
     while len(f) < 34:
