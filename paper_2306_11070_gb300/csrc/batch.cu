@@ -126,9 +126,7 @@ __device__ __forceinline__ unsigned int take_ticket(unsigned int *ctl, int phase
 }
 
 // Thread 0's value of t, for every thread of the CTA (a CTA barrier first,
-// so it also ends the work of the item before).  The ticket loops below take
-// their next ticket in thread 0 when an item starts and broadcast it when
-// the item ends, so the atomic's round trip overlaps the item's work.
+// so it also ends the work of the item before).
 __device__ __forceinline__ unsigned int cta_broadcast(unsigned int t)
 {
     __shared__ unsigned int s_b;
@@ -139,9 +137,25 @@ __device__ __forceinline__ unsigned int cta_broadcast(unsigned int t)
     return s_b;
 }
 
-__device__ __forceinline__ unsigned int prefetch_ticket(unsigned int *ctl, int phase)
+// Tickets of the work loops below.  While more than a wave of items (one
+// per worker: a CTA or a half) lies beyond the current one, the leader takes
+// its next ticket when an item starts, so that the atomic's round trip
+// overlaps the item's work; near the end (and in batches of about one wave)
+// it takes it when the item ends, so that no worker holds an item that an
+// idle one could run.
+constexpr unsigned int kNoTicket = 0xffffffffu;
+
+__device__ __forceinline__ unsigned int early_ticket(bool leader, unsigned int *ctl, int phase,
+                                                     unsigned int it, uint64_t total,
+                                                     uint64_t workers)
 {
-    return threadIdx.x == 0 ? atomicAdd(ctl + kCtlTicket0 + phase, 1u) : 0u;
+    return leader && it + workers < total ? atomicAdd(ctl + kCtlTicket0 + phase, 1u) : kNoTicket;
+}
+
+__device__ __forceinline__ unsigned int late_ticket(bool leader, unsigned int *ctl, int phase,
+                                                    unsigned int nxt)
+{
+    return leader && nxt == kNoTicket ? atomicAdd(ctl + kCtlTicket0 + phase, 1u) : nxt;
 }
 
 // The barrier of one half: named barrier 1 or 2 over its kHalf threads
@@ -221,35 +235,28 @@ __global__ void __launch_bounds__(kBatchBlock, 2) k_batch_compress(BatchArgs a)
         uint32_t prev0 = 0u, prev1 = 0u;  // folds of each set at its previous unit
         uint32_t set = 0;
         uint4 v[hst::kVecPerThread];
-        // a unit is counted while the next two units' bytes and the owner
-        // entry of the one after them are in flight
+        // a unit is counted while the next one's bytes and the owner entry of
+        // the one after are in flight
         const uint64_t G = gridDim.x;
         uint64_t g = blockIdx.x;
         const uint4 none = make_uint4(0u, 0u, 0u, 0u);
         uint4 o0 = g < total_units ? a.unit_owner[g] : none;
         uint4 o1 = g + G < total_units ? a.unit_owner[g + G] : none;
-        uint4 o2 = g + 2 * G < total_units ? a.unit_owner[g + 2 * G] : none;
-        uint4 v2[hst::kVecPerThread];
         if (g < total_units)
             hst::load_unit(unit_ptr(o0), o0.z, 0, v);
-        if (g + G < total_units)
-            hst::load_unit(unit_ptr(o1), o1.z, 0, v2);
         __syncthreads();
         for (; g < total_units; g += G) {
             uint4 cur[hst::kVecPerThread];
 #pragma unroll
-            for (int j = 0; j < hst::kVecPerThread; ++j) {
+            for (int j = 0; j < hst::kVecPerThread; ++j)
                 cur[j] = v[j];
-                v[j] = v2[j];
-            }
             const uint4 co = o0;
+            const uint64_t gn = g + G;
+            if (gn < total_units)
+                hst::load_unit(unit_ptr(o1), o1.z, 0, v);
             o0 = o1;
-            o1 = o2;
-            if (g + 2 * G < total_units) {
-                hst::load_unit(unit_ptr(o1), o1.z, 0, v2);
-                if (g + 3 * G < total_units)
-                    o2 = a.unit_owner[g + 3 * G];
-            }
+            if (gn + G < total_units)
+                o1 = a.unit_owner[gn + G];
             hst::count_unit(unit_ptr(co), co.z, 0, cur, col0 + set * (256 * 32 * 4));
             __syncthreads();
             const uint32_t s = hst::fold_bin(cnt + set * (256 * 32), tid);
@@ -270,7 +277,7 @@ __global__ void __launch_bounds__(kBatchBlock, 2) k_batch_compress(BatchArgs a)
     {
         cbk::CodebookShared &csh = *reinterpret_cast<cbk::CodebookShared *>(smem_raw);
         for (unsigned int b = take_ticket(a.ctl, 0); b < a.count;) {
-            const unsigned int nxt = prefetch_ticket(a.ctl, 0);
+            const unsigned int nxt = early_ticket(tid == 0, a.ctl, 0, b, a.count, gridDim.x);
             const BatchBuf B = a.bufs[b];
             const uint64_t u0 = a.unit_base[b], nu = a.unit_base[b + 1] - u0;
             unsigned long long h = 0;
@@ -339,7 +346,7 @@ __global__ void __launch_bounds__(kBatchBlock, 2) k_batch_compress(BatchArgs a)
             const enc::Job J = enc::make_job(B.in, B.in_bytes, a.cs, off, B.out, B.out_cap);
             if (!uniform_failed(B.status))
                 enc::write_header(J, a.cbs + b, B.out_bytes, B.status);
-            b = cta_broadcast(nxt);
+            b = cta_broadcast(late_ticket(tid == 0, a.ctl, 0, nxt));
         }
     }
     if (!grid_barrier(a.ctl, a.fail, a.barrier_extra)) {
@@ -359,8 +366,8 @@ __global__ void __launch_bounds__(kBatchBlock, 2) k_batch_compress(BatchArgs a)
         int group = 1;
         const unsigned int t0 = htid == 0 ? atomicAdd(a.ctl + kCtlTicket0 + 1, 1u) : 0u;
         for (unsigned int it = half_broadcast(t0, hs); it < total_items;) {
-            // the next ticket is taken now and broadcast when this item ends
-            const unsigned int nxt = htid == 0 ? atomicAdd(a.ctl + kCtlTicket0 + 1, 1u) : 0u;
+            const unsigned int nxt =
+                early_ticket(htid == 0, a.ctl, 1, it, total_items, 2ull * gridDim.x);
             const uint4 ow = a.item_owner[it];  // (buffer, item within it, first unit)
             const uint32_t b = ow.x;
             const BatchBuf B = a.bufs[b];
@@ -385,7 +392,8 @@ __global__ void __launch_bounds__(kBatchBlock, 2) k_batch_compress(BatchArgs a)
                 if (overflow)
                     set_status(B.status, HUFF_ERR_CAPACITY);
             }
-            it = half_broadcast(nxt, hs);  // also: the table may be rebuilt for the next item
+            // also: the table may be rebuilt for the next item
+            it = half_broadcast(late_ticket(htid == 0, a.ctl, 1, nxt), hs);
         }
     }
 }
@@ -475,8 +483,8 @@ __global__ void __launch_bounds__(kBatchBlock, 2) k_batch_decompress(BatchArgs a
     uint32_t S = 1;
     const unsigned int t0 = htid == 0 ? atomicAdd(a.ctl + kCtlTicket0 + 2, 1u) : 0u;
     for (unsigned int it = half_broadcast(t0, hs); it < total_items;) {
-        // the next ticket is taken now and broadcast when this item ends
-        const unsigned int nxt = htid == 0 ? atomicAdd(a.ctl + kCtlTicket0 + 2, 1u) : 0u;
+        const unsigned int nxt =
+            early_ticket(htid == 0, a.ctl, 2, it, total_items, 2ull * gridDim.x);
         const uint32_t b = find_owner(a.dec_items, a.count, it);
         const BatchBuf B = a.bufs[b];
         if (b != have) {
@@ -497,7 +505,8 @@ __global__ void __launch_bounds__(kBatchBlock, 2) k_batch_decompress(BatchArgs a
                     set_status(B.status, HUFF_ERR_CORRUPT_STREAM);
             }
         }
-        it = half_broadcast(nxt, hs);  // also: the tables may be rebuilt for the next item
+        // also: the tables may be rebuilt for the next item
+        it = half_broadcast(late_ticket(htid == 0, a.ctl, 2, nxt), hs);
     }
 }
 
