@@ -161,29 +161,29 @@ __device__ __forceinline__ void build_codebook(const unsigned long long *__restr
                 unsigned long long wab[2];
 #pragma unroll
                 for (int k = 0; k < 2; ++k) {
-                    if (l0 <= i0) {
-                        ab[k] = li;
-                        wab[k] = l0;
-                        l0 = l1;
-                        l1 = li + 2 < m ? sh.nw[li + 2] : kNone;
-                        ++li;
-                    } else {
-                        ab[k] = ii;
-                        wab[k] = i0;
-                        i0 = i1;
-                        i1 = ii + 2 < ni ? sh.nw[ii + 2] : kNone;
-                        ++ii;
-                    }
+                    // branch free: both refills are loaded (at in-range
+                    // indices) and the take selects
+                    const bool lf = l0 <= i0;
+                    const unsigned long long nl = sh.nw[li + 2 < 510 ? li + 2 : 510];
+                    const unsigned long long nq = sh.nw[ii + 2 < 510 ? ii + 2 : 510];
+                    ab[k] = lf ? li : ii;
+                    wab[k] = lf ? l0 : i0;
+                    const unsigned long long l1n = li + 2 < m ? nl : kNone;
+                    const unsigned long long i1n = ii + 2 < ni ? nq : kNone;
+                    l0 = lf ? l1 : l0;
+                    l1 = lf ? l1n : l1;
+                    i0 = lf ? i0 : i1;
+                    i1 = lf ? i1 : i1n;
+                    li += lf;
+                    ii += !lf;
                 }
                 const unsigned long long w2 = wab[0] + wab[1];
                 sh.nw[ni] = w2;
                 sh.par[ab[0]] = (int16_t)ni;
                 sh.par[ab[1]] = (int16_t)ni;
                 // the new node joins the merged queue at ni
-                if (ii == ni)
-                    i0 = w2;
-                else if (ii + 1 == ni)
-                    i1 = w2;
+                i0 = ii == ni ? w2 : i0;
+                i1 = ii + 1 == ni ? w2 : i1;
                 ++ni;
             }
             sh.par[2 * m - 2] = (int16_t)(2 * m - 2);  // the root points at itself
