@@ -97,18 +97,25 @@ __device__ __forceinline__ uint32_t tbl_at(uint32_t a)
     return v;
 }
 
-// Per-lane replicated code table, built by threads tid = 0..nt-1 (by default
-// all threads of the CTA).  Fast entry = (code << (32 - len)) | len: the code
-// left-aligned, its length in the low bits, zeros between them (len <= 22
-// leaves bits 5..9 clear).
+// Per-lane replicated code table (16-byte aligned), built by threads tid =
+// 0..nt-1 (by default all threads of the CTA).  Fast entry = (code << (32 -
+// len)) | len: the code left-aligned, its length in the low bits, zeros
+// between them (len <= 22 leaves bits 5..9 clear).  A thread per byte reads
+// its length and code once and fills the byte's 32 lane copies with eight
+// 16-byte stores, rotated by the byte so that the stores of a warp spread
+// over all eight 16-byte bank groups.
 __device__ __forceinline__ void build_table(const huff_codebook_t *cb, uint32_t *tbl, bool fast,
                                             int tid = threadIdx.x, int nt = blockDim.x)
 {
     if (fast) {
-        for (int i = tid; i < kTblWords; i += nt) {
-            const int b = i >> 5;
+        for (int b = tid; b < 256; b += nt) {
             const uint32_t L = cb->len[b];
-            tbl[i] = L ? (cb->code[b] << (32 - L)) | L : 0u;
+            const uint32_t e = L ? (cb->code[b] << (32 - L)) | L : 0u;
+            const uint4 v = make_uint4(e, e, e, e);
+            uint4 *row = reinterpret_cast<uint4 *>(tbl + b * 32);
+#pragma unroll
+            for (int j = 0; j < 8; ++j)
+                row[(j + b) & 7] = v;
         }
     } else {
         for (int i = tid; i < 256 * 16; i += nt) {
