@@ -473,9 +473,11 @@ def measure_next_rows(hg, synth, torch, oracle=None):
     torch.cuda.empty_cache()
     n2, seg = 256 << 20, 1 << 20
     x2 = torch.from_numpy(synth.text(n2, 1)).cuda()
-    tc = t_ms(lambda: hg.huff_segmented_compress(x2, seg), reps=3, warm=1)
+    # each call plans its batch on the host and synchronises: ten calls after
+    # three warm-up calls, so that the host's allocator has settled
+    tc = t_ms(lambda: hg.huff_segmented_compress(x2, seg), reps=10, warm=3)
     c, st = hg.huff_segmented_compress(x2, seg)
-    td = t_ms(lambda: hg.huff_segmented_decompress(c), reps=3, warm=1)
+    td = t_ms(lambda: hg.huff_segmented_decompress(c), reps=10, warm=3)
     back, m, st2 = hg.huff_segmented_decompress(c)
     torch.cuda.synchronize()
     seg_row = {"workload": "synthetic text 256 MiB (seed 1), 1 MiB segments, own codebook each",

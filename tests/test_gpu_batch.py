@@ -155,6 +155,48 @@ def test_batch_many_small_buffers_one_chunk_each():
     dplan.close()
 
 
+@pytest.mark.parametrize("ctas", [0, 1])
+def test_batch_few_buffers_and_many_items_per_worker(ctas):
+    """Batches far below one wave of items (1-3 buffers) and one buffer with
+    many items per worker (6 MiB at one CTA per SM): the ticket loops take
+    their next ticket late in the first case and early in the second; every
+    stream and every decoded byte must match the oracle."""
+    cases = [[synth.text(70000, 41)],
+             [synth.text(5, 42), synth.uniform(40000, 43)],
+             [synth.geometric(33000, 44), synth.text(1, 45), synth.zipf_ascii(250000, 46)],
+             [synth.text(6 << 20, 47)]]
+    for xs in cases:
+        params = hg.huff_batch_default_params()
+        params.chunk_symbols = 4096
+        params.ctas_per_sm = ctas
+        plan, ins, outs = _compress_batch(xs, 4096, params)
+        plan.run()
+        torch.cuda.synchronize()
+        st = plan.status.cpu().numpy()
+        nb = plan.out_bytes.cpu().numpy()
+        assert (st == 0).all()
+        streams = []
+        for i, x in enumerate(xs):
+            ost, ref = oracle.compress(x, 4096)
+            got = outs[i][:nb[i]]
+            assert ost == 0 and np.array_equal(got.cpu().numpy(), ref), i
+            streams.append(got.clone())
+        for lanes in (1, 64):
+            dec = [torch.zeros(max(x.size, 16), dtype=torch.uint8, device="cuda") for x in xs]
+            dp = hg.huff_batch_default_params()
+            dp.ctas_per_sm = ctas
+            dp.decode_lanes = lanes
+            dplan = hg.BatchPlan(streams, dec, hg.HUFF_BATCH_DECOMPRESS, dp)
+            dplan.run()
+            torch.cuda.synchronize()
+            assert (dplan.status.cpu().numpy() == 0).all()
+            assert (dplan.out_bytes.cpu().numpy() == [x.size for x in xs]).all()
+            for i, x in enumerate(xs):
+                assert np.array_equal(dec[i][:x.size].cpu().numpy(), x), (lanes, i)
+            dplan.close()
+        plan.close()
+
+
 def test_barrier_timeout_reports_status_and_context_survives():
     # The test hook makes every grid barrier wait for one CTA more than the
     # grid holds: the bounded spins run out (no fault, no hang), every buffer
