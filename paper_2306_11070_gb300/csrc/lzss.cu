@@ -686,6 +686,58 @@ struct OutBits {
     }
 };
 
+// Tokens far from both ends of a segment, for the shared-memory ring
+// (windows of 32..2048 bits) with the stored-prefix window and literal blocks
+// of at most 31 bits: at least 64 code bits and 32 output bits remain, so no
+// bounds check applies, the window never reaches before the output (the
+// prefix filled it) and a token is at most 32 bits of the reader's top 32.
+// Branch free where the lanes of a warp (each on its own segment) would
+// diverge: both the match and the literal are formed and the token
+// selects.  False (and the caller's status) only for a length field above
+// the longest match.
+__device__ __forceinline__ bool decode_fast(CodeReader &rd, OutBits<true> &ob, const LzParams &P,
+                                            uint32_t nbits)
+{
+    while (rd.pos + 64 <= rd.nbits && ob.pos + 32 <= nbits) {
+        const uint32_t t = (uint32_t)(rd.buf >> 32);  // >= 33 bits are valid
+        const uint32_t flag = t >> 31;
+        const uint32_t body = t << 1;  // the token after its flag, left-aligned
+        const uint32_t d = (body >> (32 - P.ob)) + 1;
+        const uint32_t len = (P.lb ? (body << P.ob) >> (32 - P.lb) : 0u) + P.lmin;
+        if (flag && len > P.lmax)
+            return false;
+        const uint32_t used = flag ? 1u + P.ob + P.lb : 1u + P.blk;
+        const uint32_t nout = flag ? len : P.blk;
+        // the match's 32 source bits at ob.pos - d (at most W back, so inside
+        // the output and the ring; read whether or not the token is a match)
+        const uint32_t src = ob.pos - d;
+        const uint32_t q = src >> 5, cur = ob.pos >> 5;
+        const uint32_t wa = ob.ring[q & (kDecRing - 1)], wb = ob.ring[(q + 1) & (kDecRing - 1)];
+        const uint32_t a = q == cur ? ob.pend : wa;
+        const uint32_t b = q + 1 == cur ? ob.pend : (q + 1 > cur ? 0u : wb);
+        uint32_t v = __funnelshift_l(b, a, src & 31u);
+        // a source that runs into the bits being produced repeats with period d
+        uint32_t vp = v & ~(0xffffffffu >> (d & 31u));
+#pragma unroll
+        for (int i = 0; i < 5; ++i) {
+            const uint32_t sh = d << i;
+            vp |= sh < len ? vp >> (sh & 31u) : 0u;
+        }
+        v = flag ? (d < len ? vp : v) : body;
+        // consume the token: one refill keeps >= 33 bits
+        rd.buf <<= used;
+        rd.have -= used;
+        rd.pos += used;
+        if (rd.have <= 32) {
+            rd.buf |= (uint64_t)rd.nxt << (32 - rd.have);
+            rd.have += 32;
+            rd.nxt = rd.load(rd.next++);
+        }
+        ob.put(v, nout);
+    }
+    return true;
+}
+
 // Decode one segment's tokens; false if the code is corrupt.
 template <bool kRing>
 __device__ __forceinline__ bool decode_segment(CodeReader &rd, OutBits<kRing> &ob, const LzParams &P,
@@ -699,6 +751,10 @@ __device__ __forceinline__ bool decode_segment(CodeReader &rd, OutBits<kRing> &o
                 return false;
             ob.put(rd.get(k) << (32 - k), k);
         }
+    }
+    if constexpr (kRing) {
+        if (P.dict == 2 && P.blk <= 31 && !decode_fast(rd, ob, P, nbits))
+            return false;
     }
     while (ob.pos < nbits) {
         if (rd.pos >= rd.nbits)
