@@ -73,7 +73,14 @@ def test_container_matches_oracle_paper_params(gen, n):
                                     (16, 4, 12, 8, 1), (64, 6, 9, 5, 1), (64, 12, 24, 8, 2),
                                     (256, 1, 32, 32, 1), (4096, 16, 32, 8, 2), (32, 3, 3, 1, 2),
                                     (2048, 8, 20, 8, 1), (16384, 12, 24, 8, 1),
-                                    (65536, 20, 32, 16, 1)])
+                                    (65536, 20, 32, 16, 1),
+                                    # the decoder's branch-free step (windows of 32..2048
+                                    # bits, stored prefix, literal blocks up to 31 bits):
+                                    # 31-bit literals and 32-bit matches, a length field
+                                    # of no bits, one-bit matches, short windows
+                                    (256, 4, 32, 31, 2), (2048, 1, 1, 16, 2),
+                                    (128, 2, 9, 3, 2), (512, 20, 32, 31, 2),
+                                    (32, 1, 32, 32, 2)])
 @pytest.mark.parametrize("gen", ["bitstream", "text", "periodic"])
 def test_container_matches_oracle_other_params(params, gen):
     _roundtrip_vs_oracle(_gen(gen, 3000, sum(params)), 1024, params)
@@ -171,6 +178,39 @@ def test_statuses_match_oracle():
     y, n, st = hg.huff_lzss_decompress(torch.from_numpy(c).cuda(), out_cap=100)
     torch.cuda.synchronize()
     assert int(st.item()) == hg.HUFF_ERR_CAPACITY
+
+
+def test_length_field_above_longest_match_mid_segment():
+    """A match token far from both ends of a segment (the decoder's
+    branch-free step) whose length field is all ones: with 1024/12/24/8 the
+    4-bit field then means 27 > 24 bits, so the stream is corrupt for the
+    oracle and the GPU alike."""
+    x = synth.bitstream(16384, 12)
+    params = hg.LZSS_PAPER
+    W, lmin, lmax, blk, _ = params
+    ob, lb = 10, 4
+    ost, c = oracle.lzss_segmented_compress(x, 4096, params)
+    assert ost == oracle.OK
+    start = (48 + 4 * 4 + 15) // 16 * 16  # segment 0's code
+    bits = np.unpackbits(c[start:start + 4096])
+    pos, hit = W, None  # tokens begin after the stored prefix
+    while pos < 20000:
+        if bits[pos]:
+            if pos >= 4000:
+                hit = pos
+                break
+            pos += 1 + ob + lb
+        else:
+            pos += 1 + blk
+    assert hit is not None
+    bad = c.copy()
+    for j in range(hit + 1 + ob, hit + 1 + ob + lb):
+        bad[start + j // 8] |= np.uint8(0x80 >> (j % 8))
+    ost, _, _ = oracle.lzss_segmented_decompress(bad)
+    assert ost == oracle.ERR_CORRUPT
+    y, n, st = hg.huff_lzss_decompress(torch.from_numpy(bad).cuda(), out_cap=x.size)
+    torch.cuda.synchronize()
+    assert int(st.item()) == hg.HUFF_ERR_CORRUPT_STREAM
 
 
 def test_capacity_and_arguments():
