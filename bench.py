@@ -32,7 +32,7 @@ sys.path.insert(0, ROOT)
 
 METRIC = "Huffman enc/dec GB/s & % HBM roofline; batched vs plain; served p50/p99 ms"
 WORKLOAD = "text_1g"
-E2E_PASSES = 5  # end-to-end passes of e2e_steps steps; the median is reported
+E2E_PASSES = 9  # end-to-end passes of e2e_steps steps; the median is reported
 E2E_SETS = 2  # buffer sets the end-to-end pipeline rotates through (3 or 4: slower, 78-102 GB/s)
 WORKLOAD_DESC = ("synthetic Zipf-word text (50,000-word vocabulary, Zipf(1.0), 5% punctuation, "
                  "newline at 80 chars), 1 GiB, seed 1, 16384-symbol chunks")
