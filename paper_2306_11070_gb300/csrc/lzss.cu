@@ -58,6 +58,8 @@ constexpr uint64_t kMaxSegment = 1ull << 24;
 constexpr int kLzDecThreads = 32;              // decompress: one warp per CTA, a segment per thread
 constexpr uint32_t kDecRing = 128;             // output words kept per thread (a power of two)
 constexpr uint32_t kDecRingMaxWindow = 2048;   // windows whose words fit the ring with 4 to spare
+constexpr uint32_t kLzInCells = 8;             // decompress: 16-byte cells of code staged per thread
+constexpr uint32_t kLzInFlight = kLzInCells - 1;  // copies left in flight when a word is read
 
 struct LzParams {
     uint32_t W, lmin, lmax, blk, dict;
@@ -686,6 +688,51 @@ struct OutBits {
     }
 };
 
+// The code words of the fast loop below come through a per-thread ring of
+// kLzInCells 16-byte cells in shared memory ([cell][thread], 512-byte rows),
+// filled by cp.async copies kept ahead of the reader: the 32 lanes of a warp
+// refill at different tokens, and a refill that waited on a global load
+// would wait on the one another lane issued a token before (the scoreboard
+// is the warp's), which left most of the load latency exposed.
+__device__ __forceinline__ void lz_cp_async16(uint32_t dst, const void *src)
+{
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
+}
+__device__ __forceinline__ void lz_cp_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void lz_cp_wait()
+{
+    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+struct CodeRing {
+    uint32_t col;      // shared address of this thread's cell in row 0
+    uint32_t fetched;  // cells requested so far (cell c holds code words 4c..4c+3)
+    uint32_t ncells;   // cells of the segment's code (its 16-byte padded length)
+    // request cells until the ring holds the kLzInCells from word w's on
+    __device__ __forceinline__ void top_up(const uint32_t *w, uint32_t word)
+    {
+        while (fetched < (word >> 2) + kLzInCells && fetched < ncells) {
+            lz_cp_async16(col + (fetched & (kLzInCells - 1)) * (kLzDecThreads * 16), w + 4 * fetched);
+            lz_cp_commit();
+            ++fetched;
+        }
+    }
+    // code word `word` right after top_up(w, word): unless the code's last
+    // cell has been requested, exactly kLzInFlight cells were requested after
+    // word's (one copy group each), so waiting for all but that many to land
+    // includes word's; after the last cell every copy is waited for.  A slot
+    // is requested again only once the reader has left its cell.
+    __device__ __forceinline__ uint32_t word_at(uint32_t word) const
+    {
+        if (fetched >= ncells)
+            lz_cp_wait<0>();
+        else
+            lz_cp_wait<kLzInFlight>();
+        return lds(col + ((word >> 2) & (kLzInCells - 1)) * (kLzDecThreads * 16) + (word & 3u) * 4);
+    }
+};
+
 // Tokens far from both ends of a segment, for the shared-memory ring
 // (windows of 32..2048 bits) with the stored-prefix window and literal blocks
 // of at most 31 bits: at least 64 code bits and 32 output bits remain, so no
@@ -696,16 +743,24 @@ struct OutBits {
 // selects.  False (and the caller's status) only for a length field above
 // the longest match.
 __device__ __forceinline__ bool decode_fast(CodeReader &rd, OutBits<true> &ob, const LzParams &P,
-                                            uint32_t nbits)
+                                            uint32_t nbits, uint32_t in_col)
 {
+    CodeRing rg;
+    rg.col = in_col;
+    rg.fetched = rd.next >> 2;
+    rg.ncells = rd.nw >> 2;
+    rg.top_up(rd.w, rd.next);
+    bool ok = true;
     while (rd.pos + 64 <= rd.nbits && ob.pos + 32 <= nbits) {
         const uint32_t t = (uint32_t)(rd.buf >> 32);  // >= 33 bits are valid
         const uint32_t flag = t >> 31;
         const uint32_t body = t << 1;  // the token after its flag, left-aligned
         const uint32_t d = (body >> (32 - P.ob)) + 1;
         const uint32_t len = (P.lb ? (body << P.ob) >> (32 - P.lb) : 0u) + P.lmin;
-        if (flag && len > P.lmax)
-            return false;
+        if (flag && len > P.lmax) {
+            ok = false;
+            break;
+        }
         const uint32_t used = flag ? 1u + P.ob + P.lb : 1u + P.blk;
         const uint32_t nout = flag ? len : P.blk;
         // the match's 32 source bits at ob.pos - d (at most W back, so inside
@@ -724,24 +779,32 @@ __device__ __forceinline__ bool decode_fast(CodeReader &rd, OutBits<true> &ob, c
             vp |= sh < len ? vp >> (sh & 31u) : 0u;
         }
         v = flag ? (d < len ? vp : v) : body;
-        // consume the token: one refill keeps >= 33 bits
+        // consume the token: one refill keeps >= 33 bits; the next word
+        // comes from the ring (zero past the padded code, as rd.load gives)
         rd.buf <<= used;
         rd.have -= used;
         rd.pos += used;
         if (rd.have <= 32) {
             rd.buf |= (uint64_t)rd.nxt << (32 - rd.have);
             rd.have += 32;
-            rd.nxt = rd.load(rd.next++);
+            uint32_t nw = 0u;
+            if (rd.next < rd.nw) {
+                rg.top_up(rd.w, rd.next);
+                nw = bswap32(rg.word_at(rd.next));
+            }
+            rd.nxt = nw;
+            ++rd.next;
         }
         ob.put(v, nout);
     }
-    return true;
+    lz_cp_wait<0>();  // no copy in flight into the ring once the loop is left
+    return ok;
 }
 
 // Decode one segment's tokens; false if the code is corrupt.
 template <bool kRing>
 __device__ __forceinline__ bool decode_segment(CodeReader &rd, OutBits<kRing> &ob, const LzParams &P,
-                                               uint32_t nbits)
+                                               uint32_t nbits, uint32_t in_col = 0)
 {
     if (P.dict == 2) {
         const uint32_t raw = nbits < P.W ? nbits : P.W;
@@ -753,7 +816,7 @@ __device__ __forceinline__ bool decode_segment(CodeReader &rd, OutBits<kRing> &o
         }
     }
     if constexpr (kRing) {
-        if (P.dict == 2 && P.blk <= 31 && !decode_fast(rd, ob, P, nbits))
+        if (P.dict == 2 && P.blk <= 31 && !decode_fast(rd, ob, P, nbits, in_col))
             return false;
     }
     while (ob.pos < nbits) {
@@ -796,8 +859,10 @@ __global__ void __launch_bounds__(kLzDecThreads) k_lzss_decode(const uint8_t *__
     // ring of thread t at t * (kDecRing + 1): the odd stride spreads the
     // threads' equal ring positions over the banks
     __shared__ uint32_t rings[kLzDecThreads * (kDecRing + 1)];
+    __shared__ __align__(16) uint4 in_ring[kLzInCells * kLzDecThreads];  // [cell][thread]
     if (!*ok || chain_failed(status))
         return;
+    const uint32_t in_col = smem_u32(in_ring) + threadIdx.x * 16;
     const uint64_t n = *reinterpret_cast<const uint64_t *>(c);
     const uint64_t seg = *reinterpret_cast<const uint64_t *>(c + 8);
     const uint32_t *f = reinterpret_cast<const uint32_t *>(c + 16);
@@ -819,7 +884,7 @@ __global__ void __launch_bounds__(kLzDecThreads) k_lzss_decode(const uint8_t *__
             ob.pend = 0;
             ob.npend = 0;
             ob.pos = 0;
-            good = decode_segment(rd, ob, P, (uint32_t)(8 * m));
+            good = decode_segment(rd, ob, P, (uint32_t)(8 * m), in_col);
             if (good)
                 ob.finish();
         } else {
