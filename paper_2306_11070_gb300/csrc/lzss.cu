@@ -216,6 +216,11 @@ __host__ __device__ __forceinline__ bool ring_ok(const LzParams &P)
     return P.W >= 64 && P.W <= kRingMaxWindow;
 }
 
+// 2^16 from the constant bank: search_run forms its key by one multiply-add
+// on the FMA pipe (a visible power of two would become a shift and an add on
+// the ALU pipe, which the candidate loop already fills)
+static __constant__ uint32_t kKeyScale = 65536u;
+
 // The best key over this lane's candidates from a straight run of window
 // words: w points at the word after the one where candidate 0's source
 // begins; candidate k's source begins k words lower.
@@ -232,7 +237,8 @@ __device__ __forceinline__ int32_t search_run(const uint32_t *w, uint32_t nk, ui
             const uint32_t low = w[-(k + 1)];
             const uint32_t src = __funnelshift_l(hiw, low, sh);
             hiw = low;
-            const int32_t key = (int32_t)(__clz((src ^ X) | cap) << 16) - 32 * k;
+            const int32_t key = (int32_t)imad((uint32_t)__clz((src ^ X) | cap), kKeyScale,
+                                              (uint32_t)(-32 * k));
             best = key > best ? key : best;
         }
     } else {
@@ -240,7 +246,8 @@ __device__ __forceinline__ int32_t search_run(const uint32_t *w, uint32_t nk, ui
             const uint32_t low = w[-(int)(k + 1)];
             const uint32_t src = __funnelshift_l(hiw, low, sh);
             hiw = low;
-            const int32_t key = (int32_t)(__clz((src ^ X) | cap) << 16) - 32 * (int32_t)k;
+            const int32_t key = (int32_t)imad((uint32_t)__clz((src ^ X) | cap), kKeyScale,
+                                              0u - 32u * k);
             best = key > best ? key : best;
         }
     }
